@@ -1,0 +1,205 @@
+/*
+ * rsvd.h -- C ABI of the GB300 randomized SVD library.
+ *
+ * The library computes the rank-k randomized SVD of Algorithm 4 of
+ * X. Li, "Randomized Algorithms for Solving Singular Value Decomposition
+ * Problems with MATLAB Toolbox" (2021), Section 3.3 ("Accuracy Enhanced
+ * Randomized SVD with Orthonormalization"), truncated to rank k as in
+ * Section 3.1; with q = 0 it is Algorithm 2 (Section 3.1):
+ *
+ *   1. Omega: n x (k+p) standard Gaussian test matrix
+ *   2. Y = A Omega
+ *   3. Q = orth(Y)
+ *   4-5. for j = 1..q:  W = orth(A^T Q);  Q = orth(A W)
+ *   6. B = Q^T A              (computed as B^T = A^T Q)
+ *   7. B = U~ Sigma V^T       (small SVD)
+ *   8. U = Q U~, keep the leading k triplets
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Matrices are column-major (the thesis' MATLAB/LAPACK setting).  A
+ *   matrix "r x c with leading dimension ld" holds element (i, j) at
+ *   ptr[i + j*ld], ld >= r.
+ * - Every matrix pointer passed to a compute entry point is a DEVICE pointer
+ *   owned by the caller; the library never frees it.  Host pointers are
+ *   named as such.
+ * - The library allocates nothing on the device after rsvd_plan_create():
+ *   all scratch lives in one caller-provided workspace
+ *   (rsvd_workspace_size / rsvd_set_workspace).
+ * - Compute entry points only enqueue work on the plan's CUDA stream and
+ *   return.  Their return value reports argument and launch errors; the
+ *   numerical status of the enqueued work (Cholesky breakdown, Jacobi not
+ *   converged, non-finite input) is read by rsvd_plan_status(), which waits
+ *   for the stream.
+ * - Return values: RSVD_OK (0); -i when the i-th argument (1-based) of the
+ *   call is invalid; a positive RSVD_ERR_* code otherwise.
+ * - Random numbers: Omega is drawn from Philox4x32-10 (Salmon et al., SC'11)
+ *   with Box-Muller, element (i, j) using counter (lo32(t), hi32(t),
+ *   stream, 0) with t = j*n + i and key (lo32(seed), hi32(seed)); words 0,1
+ *   give u1 and words 2,3 give u2 as (x + 1/2) 2^-52 with
+ *   x = (w_a >> 6) 2^26 + (w_b >> 6); z = sqrt(-2 ln u1) cos(2 pi u2).
+ *   The thesis does not fix a generator (Algorithm 1 step 1 only asks for
+ *   a Gaussian matrix); this one makes results reproducible from the seed.
+ */
+#ifndef RSVD_GB300_H
+#define RSVD_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rsvd_plan_s* rsvd_plan_t;
+
+/* Storage type of A. */
+typedef enum {
+  RSVD_F64 = 0,   /* FP64 A; plain mode computes every step in FP64        */
+  RSVD_BF16 = 2   /* BF16 A; mixed mode (tensor cores, FP32 accumulation)  */
+} rsvd_dtype_t;
+
+typedef enum {
+  RSVD_MODE_PLAIN = 0, /* FP64 arithmetic throughout (A must be RSVD_F64)   */
+  RSVD_MODE_MIXED = 1  /* BF16 operands on tcgen05 tensor cores, FP32
+                          accumulation, FP64 for the l x l steps            */
+} rsvd_mode_t;
+
+/* Status codes (positive). */
+#define RSVD_OK 0
+#define RSVD_ERR_CHOLESKY 1    /* Gram Cholesky failed even after a shift   */
+#define RSVD_ERR_JACOBI 2      /* Jacobi SVD did not converge (30 sweeps)   */
+#define RSVD_ERR_TIMEOUT 3     /* a device-side wait hit its iteration cap  */
+#define RSVD_ERR_WORKSPACE 4   /* no workspace set, or it is too small      */
+#define RSVD_ERR_CUDA 5        /* a CUDA runtime call or launch failed      */
+#define RSVD_ERR_NONFINITE 6   /* NaN or Inf met in A (through Y = A Omega) */
+#define RSVD_ERR_UNSUPPORTED 7 /* dtype/mode/size not built into this library */
+
+/* Largest k+p the library accepts (the l x l steps keep l x l FP64 tiles). */
+#define RSVD_L_MAX 288
+
+/* ---------------------------------------------------------------------- */
+/* Plans                                                                   */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * rsvd_plan_create: a plan for problems up to m_max x n_max with
+ * k + p <= l_max, A stored as a_dtype, computed in `mode`, enqueued on
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).
+ * Allocates a small pinned host status buffer and nothing on the device.
+ * Errors: -1 plan NULL; -2/-3 sizes < 1; -4 l_max < 1 or > RSVD_L_MAX;
+ * -5 unknown dtype; -6 unknown mode or mode/dtype mismatch;
+ * RSVD_ERR_CUDA if the host allocation fails.
+ */
+int rsvd_plan_create(rsvd_plan_t* plan, int64_t m_max, int64_t n_max, int l_max,
+                     int a_dtype, int mode, void* cuda_stream);
+
+/* Bytes of device workspace the plan needs (256-byte aligned pointer). */
+int rsvd_workspace_size(rsvd_plan_t plan, size_t* bytes);
+
+/*
+ * rsvd_set_workspace: hands the plan `bytes` bytes of device memory at
+ * `dev_ptr` (caller-owned, must outlive the plan's use, 256-byte aligned).
+ * Errors: -2 NULL pointer or misaligned; RSVD_ERR_WORKSPACE if too small.
+ */
+int rsvd_set_workspace(rsvd_plan_t plan, void* dev_ptr, size_t bytes);
+
+/*
+ * rsvd_plan_status: waits for the plan's stream, then returns the status of
+ * the work enqueued since the previous call (RSVD_OK or a positive code) and
+ * clears it.  RSVD_ERR_CUDA if the stream reported an error.
+ */
+int rsvd_plan_status(rsvd_plan_t plan);
+
+/* Sets the stream later calls enqueue on. */
+int rsvd_plan_set_stream(rsvd_plan_t plan, void* cuda_stream);
+
+int rsvd_plan_destroy(rsvd_plan_t plan);
+
+const char* rsvd_status_string(int status);
+
+/* ---------------------------------------------------------------------- */
+/* Full solve: Algorithm 4 (Section 3.3), truncated to rank k (Section 3.1) */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * rsvd_solve: rank-k randomized SVD  A ~= U diag(S) VT.
+ *   A    m x n, leading dimension lda >= m, stored as the plan's dtype.
+ *   k >= 1 target rank, p >= 0 oversampling, k + p <= min(m, n) and
+ *   <= the plan's l_max (Theorem 2's premise k + p <= min{m, n}), q >= 0
+ *   power steps, seed selects Omega (stream 0).
+ *   U    m x k, ldu >= m: FP64 in plain mode, FP32 in mixed mode.
+ *   S    k FP64 values, descending.
+ *   VT   k x n, ldvt >= k: FP64 in plain mode, FP32 in mixed mode.
+ * Signs: each pair (u_i, v_i) is flipped so the entry of u_i with the
+ * largest magnitude is positive (lowest row index on ties).
+ * Argument errors: -1 plan; -2 A NULL; -3 m; -4 n; -5 lda; -6 k; -7 p;
+ * -8 q; -10 U NULL; -11 ldu; -12 S NULL; -13 VT NULL; -14 ldvt.
+ * m, n above the plan's maxima or k+p above l_max: RSVD_ERR_WORKSPACE.
+ */
+int rsvd_solve(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t lda,
+               int k, int p, int q, uint64_t seed,
+               void* U, int64_t ldu, double* S, void* VT, int64_t ldvt);
+
+/* ---------------------------------------------------------------------- */
+/* Step-level entry points (the rows of the hot path, one call per step).   */
+/* In plain mode every buffer is FP64; the mixed-mode types are noted.     */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * rsvd_gaussian: Algorithm 4 step 1 (Section 3.3; "Gaussian test matrix",
+ * Algorithm 1 step 1, Section 2.2).  Writes the n x l matrix Omega for
+ * (seed, stream) to `out` (ldo >= n) as FP64 (out_dtype RSVD_F64) or BF16
+ * (RSVD_BF16, rounded to nearest even from the FP64 value).
+ * Errors: -2 n < 1; -3 l < 1; -6 out_dtype; -7 out NULL; -8 ldo < n.
+ */
+int rsvd_gaussian(rsvd_plan_t plan, int64_t n, int l, uint64_t seed, uint32_t stream,
+                  int out_dtype, void* out, int64_t ldo);
+
+/*
+ * rsvd_apply_a: Y = A X  (Algorithm 4 steps 2 and 5, "Form Y = A Omega",
+ * "Q = orth(A W)").  A m x n (lda), X n x l (ldx), Y m x l (ldy).
+ * Plain: A, X, Y FP64.  Mixed: A BF16, X BF16, Y FP32.
+ * Errors: -2 A; -3 m; -4 n; -5 lda; -6 X; -7 ldx; -8 l; -9 Y; -10 ldy.
+ */
+int rsvd_apply_a(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t lda,
+                 const void* X, int64_t ldx, int l, void* Y, int64_t ldy);
+
+/*
+ * rsvd_apply_at: Z = A^T X  (Algorithm 4 step 5 "W = orth(A* Q)" and step 6
+ * "B = Q* A", computed as B^T = A^T Q).  A m x n (lda), X m x l (ldx),
+ * Z n x l (ldz).  Plain: FP64.  Mixed: A BF16, X BF16, Z FP32.
+ * Errors as rsvd_apply_a, with ldx >= m and ldz >= n.
+ */
+int rsvd_apply_at(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t lda,
+                  const void* X, int64_t ldx, int l, void* Z, int64_t ldz);
+
+/*
+ * rsvd_orth: Q = orth(Y) by CholeskyQR2 (Algorithm 4 step 3; the thesis
+ * leaves the orthonormalisation method open).  Y rows x l (ldy) FP64 in both
+ * modes for this entry point; Q rows x l (ldq) FP64; Y is left unchanged.
+ * If R (l x l, ldr, device, FP64) is non-NULL it receives the upper
+ * triangular factor with Y = Q R.  Columns of Y that are numerically in the
+ * span of earlier columns (Gram pivot <= l * 2^-52 * max diag) come out as
+ * zero columns of Q and zero rows of R.
+ * Errors: -2 Y; -3 rows; -4 l; -5 ldy; -6 Q; -7 ldq; -9 ldr.
+ */
+int rsvd_orth(rsvd_plan_t plan, const double* Y, int64_t rows, int l, int64_t ldy,
+              double* Q, int64_t ldq, double* R, int64_t ldr);
+
+/*
+ * rsvd_small_svd: SVD of an l x l FP64 matrix M (ldm) by one-sided Jacobi
+ * (Algorithm 4 step 7, applied to the triangular factor of B^T):
+ * M = Um diag(sig) Vm^T with sig descending (l values), Um and Vm l x l
+ * (ldu, ldv) with orthonormal columns (a column of Um is zero where sig is
+ * zero).  All pointers device FP64.  M is left unchanged.
+ * Errors: -2 M; -3 l; -4 ldm; -5 sig; -6 Um; -7 ldu; -8 Vm; -9 ldv.
+ */
+int rsvd_small_svd(rsvd_plan_t plan, const double* M, int l, int64_t ldm,
+                   double* sig, double* Um, int64_t ldu, double* Vm, int64_t ldv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSVD_GB300_H */

@@ -1,0 +1,61 @@
+"""ctypes loader for ``librsvd_gb300.so`` (the C ABI of include/rsvd.h).
+
+Argument marshalling only.  If the shared object is missing this raises:
+the library has no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from ._build import LIB_PATH
+
+c_int, c_int64, c_uint32, c_uint64 = ctypes.c_int, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64
+c_void_p, c_size_t = ctypes.c_void_p, ctypes.c_size_t
+P_double = ctypes.c_void_p
+
+# name -> (restype, argtypes), in the order of include/rsvd.h
+SIGNATURES = {
+    "rsvd_plan_create": (c_int, [ctypes.POINTER(c_void_p), c_int64, c_int64, c_int, c_int, c_int,
+                                 c_void_p]),
+    "rsvd_workspace_size": (c_int, [c_void_p, ctypes.POINTER(c_size_t)]),
+    "rsvd_set_workspace": (c_int, [c_void_p, c_void_p, c_size_t]),
+    "rsvd_plan_status": (c_int, [c_void_p]),
+    "rsvd_plan_set_stream": (c_int, [c_void_p, c_void_p]),
+    "rsvd_plan_destroy": (c_int, [c_void_p]),
+    "rsvd_status_string": (ctypes.c_char_p, [c_int]),
+    "rsvd_solve": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_int64, c_int, c_int, c_int,
+                           c_uint64, c_void_p, c_int64, P_double, c_void_p, c_int64]),
+    "rsvd_gaussian": (c_int, [c_void_p, c_int64, c_int, c_uint64, c_uint32, c_int, c_void_p,
+                              c_int64]),
+    "rsvd_apply_a": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_int64, c_void_p, c_int64,
+                             c_int, c_void_p, c_int64]),
+    "rsvd_apply_at": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_int64, c_void_p, c_int64,
+                              c_int, c_void_p, c_int64]),
+    "rsvd_orth": (c_int, [c_void_p, P_double, c_int64, c_int, c_int64, P_double, c_int64,
+                          P_double, c_int64]),
+    "rsvd_small_svd": (c_int, [c_void_p, P_double, c_int, c_int64, P_double, P_double, c_int64,
+                               P_double, c_int64]),
+}
+
+_LIB = None
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load the shared object (once) and attach the C signatures."""
+    global _LIB
+    if _LIB is not None and path is None:
+        return _LIB
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"CUDA library {path} is not built; run "
+            "`python -c 'import __graft_entry__ as g; g.build()'` first")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path == LIB_PATH:
+        _LIB = lib
+    return lib

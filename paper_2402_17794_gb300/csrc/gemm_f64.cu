@@ -1,0 +1,207 @@
+// FP64 tall-skinny products of the plain path: the passes over A of
+// Algorithm 4 (steps 2, 5 and 6, Section 3.3) and the O(m l^2) products of
+// CholeskyQR2 (Gram Y^T Y, Y R^-1) and of the lift U = Q U~ (step 8).
+//
+// On GB300 FP64 runs at 2 DFMA per clock per SM (about 1.2 TFLOP/s for the
+// GPU) while HBM streams ~6.8 TB/s, so an FP64 pass over A at l = 80
+// (20 flop per byte of A) is bound by the FP64 pipe by two orders of
+// magnitude, not by memory.  The kernel is therefore shaped to keep the
+// DFMA pipe busy: 64 x BN output tiles (BN = 16*TN matched to l so no
+// column of work is padded away), 4 x TN accumulators per thread, both
+// operands staged in padded shared memory (conflict-free 8-byte accesses)
+// with a register double buffer, and split-K so that every SM holds several
+// CTAs.  Split-K partials are summed by a second kernel in a fixed order,
+// so results do not depend on scheduling.
+#include <algorithm>
+
+#include "internal.h"
+
+namespace rsvd {
+namespace {
+
+constexpr int BM = 64;
+constexpr int BK = 16;
+constexpr int THREADS = 256;
+constexpr int AS_LD = BM + 1;  // padded row (doubles)
+
+template <int TN, bool TRANS>
+__global__ void __launch_bounds__(THREADS)
+gemm_f64_kernel(const double* __restrict__ A, int64_t lda, const double* __restrict__ X,
+                int64_t ldx, double* __restrict__ C, int64_t ldc, int64_t M, int64_t K, int N,
+                int64_t k_per_split, int64_t part_stride) {
+  constexpr int BN = 16 * TN;
+  constexpr int XS_LD = BN + 1;
+  __shared__ double As[2][BK * AS_LD];
+  __shared__ double Xs[2][BK * XS_LD];
+
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int64_t r0 = (int64_t)blockIdx.x * BM;
+  const int c0 = blockIdx.y * BN;
+  const int64_t kb = (int64_t)blockIdx.z * k_per_split;
+  const int64_t ke = (kb + k_per_split < K) ? kb + k_per_split : K;
+  double* Cout = C + (int64_t)blockIdx.z * part_stride;
+
+  constexpr int A_PER = BM * BK / THREADS;             // 4
+  constexpr int X_PER = (BN * BK + THREADS - 1) / THREADS;
+  double ra[A_PER], rx[X_PER];
+
+  auto load_tiles = [&](int64_t k0) {
+#pragma unroll
+    for (int e = 0; e < A_PER; ++e) {
+      int idx = tid + e * THREADS;
+      int r, kk;
+      if (!TRANS) { r = idx % BM; kk = idx / BM; }
+      else { kk = idx % BK; r = idx / BK; }
+      int64_t gr = r0 + r, gk = k0 + kk;
+      double v = 0.0;
+      if (gr < M && gk < ke) v = TRANS ? A[gk + gr * lda] : A[gr + gk * lda];
+      ra[e] = v;
+    }
+#pragma unroll
+    for (int e = 0; e < X_PER; ++e) {
+      int idx = tid + e * THREADS;
+      int kk = idx % BK, c = idx / BK;
+      int64_t gk = k0 + kk;
+      double v = 0.0;
+      if (idx < BN * BK && c0 + c < N && gk < ke) v = X[gk + (int64_t)(c0 + c) * ldx];
+      rx[e] = v;
+    }
+  };
+  auto store_tiles = [&](int buf) {
+#pragma unroll
+    for (int e = 0; e < A_PER; ++e) {
+      int idx = tid + e * THREADS;
+      int r, kk;
+      if (!TRANS) { r = idx % BM; kk = idx / BM; }
+      else { kk = idx % BK; r = idx / BK; }
+      As[buf][kk * AS_LD + r] = ra[e];
+    }
+#pragma unroll
+    for (int e = 0; e < X_PER; ++e) {
+      int idx = tid + e * THREADS;
+      if (idx < BN * BK) {
+        int kk = idx % BK, c = idx / BK;
+        Xs[buf][kk * XS_LD + c] = rx[e];
+      }
+    }
+  };
+
+  double acc[4][TN];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
+
+  int buf = 0;
+  if (kb < ke) {
+    load_tiles(kb);
+    store_tiles(0);
+  }
+  __syncthreads();
+  for (int64_t k0 = kb; k0 < ke; k0 += BK) {
+    const bool more = k0 + BK < ke;
+    if (more) load_tiles(k0 + BK);
+    const double* as = As[buf];
+    const double* xs = Xs[buf];
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double a[4], x[TN];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = as[kk * AS_LD + tx + 16 * i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) x[j] = xs[kk * XS_LD + ty + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], x[j], acc[i][j]);
+    }
+    if (more) store_tiles(buf ^ 1);
+    __syncthreads();
+    buf ^= 1;
+  }
+
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int64_t gr = r0 + tx + 16 * i;
+    if (gr >= M) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      int gc = c0 + ty + 16 * j;
+      if (gc < N) Cout[gr + (int64_t)gc * ldc] = acc[i][j];
+    }
+  }
+}
+
+__global__ void splitk_reduce_kernel(const double* __restrict__ part, int splits,
+                                     int64_t part_stride, int64_t M, int N, double* __restrict__ C,
+                                     int64_t ldc) {
+  const int64_t total = M * (int64_t)N;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t c = t / M, r = t - c * M;
+    double s = 0.0;
+    for (int z = 0; z < splits; ++z) s += part[z * part_stride + t];
+    C[r + c * ldc] = s;
+  }
+}
+
+template <int TN>
+void launch_tn(const GemmF64& g, dim3 grid, double* out, int64_t ldo, int64_t kps,
+               int64_t pstride, cudaStream_t st) {
+  if (g.trans)
+    gemm_f64_kernel<TN, true><<<grid, THREADS, 0, st>>>(g.A, g.lda, g.X, g.ldx, out, ldo, g.M, g.K,
+                                                        g.N, kps, pstride);
+  else
+    gemm_f64_kernel<TN, false><<<grid, THREADS, 0, st>>>(g.A, g.lda, g.X, g.ldx, out, ldo, g.M,
+                                                         g.K, g.N, kps, pstride);
+}
+
+}  // namespace
+
+cudaError_t launch_gemm_f64(const GemmF64& g, double* part, size_t part_elems, int num_sms,
+                            cudaStream_t st) {
+  if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+  // Column tiles of at most 96 columns, each a multiple of 16 wide.
+  int col_tiles = (g.N + 95) / 96;
+  int per = (g.N + col_tiles - 1) / col_tiles;
+  int tn = (per + 15) / 16;
+  int bn = 16 * tn;
+  col_tiles = (g.N + bn - 1) / bn;
+  int64_t row_tiles = (g.M + BM - 1) / BM;
+  // Split K so the grid covers every SM several times, keeping >= 256 of K
+  // per split, and never more slices than the partial buffer holds.
+  int64_t tiles = row_tiles * col_tiles;
+  int64_t target = (int64_t)num_sms * 6;
+  int64_t splits = (target + tiles - 1) / tiles;
+  splits = std::min<int64_t>(splits, std::max<int64_t>(1, g.K / 256));
+  splits = std::min<int64_t>(splits, kMaxSplits);
+  int64_t pstride = g.M * (int64_t)g.N;
+  if (splits > 1 && (part == nullptr || (size_t)(splits * pstride) > part_elems))
+    splits = part ? std::max<int64_t>(1, (int64_t)(part_elems / (size_t)pstride)) : 1;
+  if (splits < 1) splits = 1;
+  int64_t kps = (g.K + splits - 1) / splits;
+  kps = (kps + BK - 1) / BK * BK;
+  splits = (g.K + kps - 1) / kps;
+  if (splits < 1) splits = 1;
+  dim3 grid((unsigned)row_tiles, (unsigned)col_tiles, (unsigned)splits);
+  double* out = splits > 1 ? part : g.C;
+  int64_t ldo = splits > 1 ? g.M : g.ldc;
+  switch (tn) {
+    case 1: launch_tn<1>(g, grid, out, ldo, kps, pstride, st); break;
+    case 2: launch_tn<2>(g, grid, out, ldo, kps, pstride, st); break;
+    case 3: launch_tn<3>(g, grid, out, ldo, kps, pstride, st); break;
+    case 4: launch_tn<4>(g, grid, out, ldo, kps, pstride, st); break;
+    case 5: launch_tn<5>(g, grid, out, ldo, kps, pstride, st); break;
+    case 6: launch_tn<6>(g, grid, out, ldo, kps, pstride, st); break;
+    default: return cudaErrorInvalidValue;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || splits == 1) return e;
+  int64_t total = pstride;
+  int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)num_sms * 8);
+  splitk_reduce_kernel<<<blocks, 256, 0, st>>>(part, (int)splits, pstride, g.M, g.N, g.C, g.ldc);
+  return cudaGetLastError();
+}
+
+}  // namespace rsvd

@@ -1,0 +1,99 @@
+// Internal declarations shared by the library's translation units.
+// Not part of the public C ABI (see include/rsvd.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/rsvd.h"
+
+namespace rsvd {
+
+constexpr int kMaxSplits = 32;      // split-K partial slices kept in workspace
+constexpr size_t kAlign = 256;
+
+// Device status word bits live in one int; codes are ORed as (1 << code).
+struct DeviceStatus {
+  int flags;        // bit (1 << RSVD_ERR_*) set by kernels
+  int jacobi_sweeps;
+  int deficient;    // number of dropped (deficient) columns in the last orth
+  int pad[61];
+};
+
+inline int status_from_flags(int flags) {
+  // report the most severe code first
+  const int order[] = {RSVD_ERR_NONFINITE, RSVD_ERR_TIMEOUT, RSVD_ERR_CHOLESKY, RSVD_ERR_JACOBI};
+  for (int c : order)
+    if (flags & (1 << c)) return c;
+  return RSVD_OK;
+}
+
+// Workspace carve-up (offsets in bytes from the workspace base).
+struct Layout {
+  size_t status, om, y, qm, tmp, z, qb, part, small, total;
+  // mixed-mode extras
+  size_t om16, q16, y32, z32, vk;
+  size_t small_stride;  // bytes of one l x l FP64 matrix (padded)
+};
+
+}  // namespace rsvd
+
+struct rsvd_plan_s {
+  int64_t m_max, n_max;
+  int l_max;
+  int dtype, mode;
+  cudaStream_t stream;
+  char* ws;
+  size_t ws_bytes;
+  rsvd::Layout lay;
+  int* h_status;     // pinned host copy of DeviceStatus.flags
+  int num_sms;
+};
+
+namespace rsvd {
+
+// ---- kernels' host launchers (all enqueue on `st`) ----
+
+// Omega (n x l) for (seed, stream): FP64 or BF16 output.
+cudaError_t launch_gaussian(int64_t n, int l, uint64_t seed, uint32_t stream_id,
+                            int out_dtype, void* out, int64_t ldo, cudaStream_t st);
+
+// FP64 tall-skinny GEMM:  C (M x N) = op(A) X,  op(A) = A (M x K, lda) or
+// A^T (A stored K x M, lda).  X is K x N (ldx).  Split-K partials go to
+// `part` (kMaxSplits * M * N doubles) when more than one split is used.
+struct GemmF64 {
+  const double* A; int64_t lda; bool trans;
+  const double* X; int64_t ldx;
+  double* C; int64_t ldc;
+  int64_t M, K; int N;
+};
+cudaError_t launch_gemm_f64(const GemmF64& g, double* part, size_t part_elems,
+                            int num_sms, cudaStream_t st);
+
+// One-CTA Cholesky of the l x l Gram G (ldg) -> upper R (l x l, ld l) and
+// its inverse Rinv (ld l); deficient pivots zero the row of R and the row and
+// column of Rinv.  Sets status bits on breakdown / non-finite input.
+cudaError_t launch_chol_inv(const double* G, int64_t ldg, int l, double* R, double* Rinv,
+                            double* work, DeviceStatus* status, cudaStream_t st);
+
+// out (l x l, ld l) = R2 * R1 for upper triangular R1, R2 (ld l); if
+// transpose_out, out = (R2 R1)^T.
+cudaError_t launch_tri_product(const double* R2, const double* R1, int l, double* out,
+                               bool transpose_out, cudaStream_t st);
+
+// One-CTA one-sided Jacobi SVD of the l x l matrix M (ldm).  work holds
+// 2 * l_even * l doubles.
+cudaError_t launch_jacobi_svd(const double* M, int l, int64_t ldm, double* sig,
+                              double* Um, int64_t ldu, double* Vm, int64_t ldv,
+                              double* work, DeviceStatus* status, cudaStream_t st);
+
+// Sign convention + outputs of the lift: flips columns of U (m x k, ldu, FP64)
+// so each column's largest-|.| entry is positive, writes S[i] = sig[i] and
+// VT (k x n, ldvt) = diag(sign) Vk^T with Vk n x k (ld n).
+cudaError_t launch_finalize_f64(double* U, int64_t m, int64_t ldu, int k,
+                                const double* Vk, int64_t n, double* VT, int64_t ldvt,
+                                const double* sig, double* S, double* sign_work,
+                                cudaStream_t st);
+
+}  // namespace rsvd

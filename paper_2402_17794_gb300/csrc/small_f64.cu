@@ -1,0 +1,381 @@
+// The l x l FP64 steps of the path (l = k + p <= 288):
+//
+//  * chol_inv: Cholesky factor R of the Gram matrix G = Y^T Y and its inverse,
+//    the middle of CholeskyQR (Q = Y R^-1), used for every orth() of
+//    Algorithm 4 (steps 3 and 5, Section 3.3).  Columns whose Gram pivot falls
+//    below l * 2^-52 * max(diag G) are numerically in the span of the earlier
+//    ones; they are dropped (zero row of R, zero row and column of R^-1), so
+//    the matching column of Q is exactly zero and contributes nothing to
+//    B = Q^T A.  This keeps exactly rank-deficient samples (rank(A) < k + p)
+//    well defined.
+//  * tri_product: R = R2 R1 (the R factor of CholeskyQR2), optionally
+//    transposed.
+//  * jacobi_svd: one-sided (Hestenes) Jacobi SVD of an l x l matrix, step 7 of
+//    Algorithm 4 applied to R_B^T where B^T = Q_B R_B; round-robin pair
+//    ordering, one warp per column pair, Rutishauser's rotation formulas.
+//  * finalize: the sign convention and the output layout of step 8.
+//
+// Each runs as one CTA: the whole problem is O(l^3) FP64 work, which fits in
+// one SM's L1/shared memory and needs a block-wide barrier per elimination
+// step or Jacobi round.
+#include <cfloat>
+
+#include <algorithm>
+
+#include "internal.h"
+
+namespace rsvd {
+namespace {
+
+constexpr int SMALL_THREADS = 1024;
+
+__device__ __forceinline__ void set_flag(DeviceStatus* s, int code) {
+  atomicOr(&s->flags, 1 << code);
+}
+
+// G (ldg) -> R (ld l, upper; lower part zeroed), Rinv (ld l, upper).
+// `work` must hold l*l doubles (it may be shared memory or global).
+__global__ void __launch_bounds__(SMALL_THREADS)
+chol_inv_kernel(const double* __restrict__ G, int64_t ldg, int l, double* __restrict__ R,
+                double* __restrict__ Rinv, double* __restrict__ gwork, DeviceStatus* status) {
+  extern __shared__ double smem[];
+  double* W = gwork ? gwork : smem;  // column-major l x l working copy
+  __shared__ double s_maxdiag;
+  __shared__ double s_r;
+  __shared__ int s_bad;
+  __shared__ int s_deficient;
+  const int tid = threadIdx.x, nt = blockDim.x;
+
+  for (int t = tid; t < l * l; t += nt) {
+    int i = t % l, j = t / l;
+    W[t] = (i <= j) ? G[i + (int64_t)j * ldg] : 0.0;
+  }
+  if (tid == 0) {
+    s_maxdiag = 0.0;
+    s_bad = 0;
+    s_deficient = 0;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double mx = 0.0;
+    int bad = 0;
+    for (int j = 0; j < l; ++j) {
+      double d = W[j + j * l];
+      if (!isfinite(d)) bad = 1;
+      mx = fmax(mx, fabs(d));
+    }
+    s_maxdiag = mx;
+    s_bad = bad;
+  }
+  __syncthreads();
+  if (s_bad) {
+    for (int t = tid; t < l * l; t += nt) {
+      R[t] = 0.0;
+      Rinv[t] = 0.0;
+    }
+    if (tid == 0) set_flag(status, RSVD_ERR_NONFINITE);
+    return;
+  }
+  const double tol = (double)l * DBL_EPSILON * s_maxdiag;
+
+  // Right-looking Cholesky on the upper triangle: G = R^T R.
+  for (int j = 0; j < l; ++j) {
+    if (tid == 0) {
+      double d = W[j + j * l];
+      if (!(d > tol)) {
+        s_r = 0.0;  // dropped column
+        s_deficient++;
+      } else {
+        s_r = sqrt(d);
+      }
+    }
+    __syncthreads();
+    const double r = s_r;
+    if (r == 0.0) {
+      for (int c = j + tid; c < l; c += nt) W[j + c * l] = 0.0;
+      __syncthreads();
+      continue;
+    }
+    const double inv = 1.0 / r;
+    for (int c = j + 1 + tid; c < l; c += nt) W[j + c * l] *= inv;
+    if (tid == 0) W[j + j * l] = r;
+    __syncthreads();
+    // trailing update of the upper triangle: W[i][c] -= R[j][i] R[j][c], j < i <= c
+    const int rem = l - j - 1;
+    const int cnt = rem * (rem + 1) / 2;
+    for (int t = tid; t < cnt; t += nt) {
+      // map t -> (i, c) with j < i <= c < l, enumerating column by column
+      int cc = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+      while ((cc + 1) * (cc + 2) / 2 <= t) ++cc;
+      while (cc * (cc + 1) / 2 > t) --cc;
+      int ii = t - cc * (cc + 1) / 2;
+      int i = j + 1 + ii, c = j + 1 + cc;
+      W[i + c * l] -= W[j + i * l] * W[j + c * l];
+    }
+    __syncthreads();
+  }
+  // R out
+  for (int t = tid; t < l * l; t += nt) {
+    int i = t % l, j = t / l;
+    R[t] = (i <= j) ? W[t] : 0.0;
+  }
+  __syncthreads();
+  // In-place inverse of the upper triangular W (column by column):
+  // for column j: Winv[j][j] = 1/R[j][j];  Winv[0:j, j] = -Winv[j][j] * Winv[0:j,0:j] R[0:j, j]
+  for (int j = 0; j < l; ++j) {
+    const double rjj = W[j + j * l];
+    if (rjj == 0.0) {
+      for (int i = tid; i <= j; i += nt) W[i + j * l] = 0.0;
+      __syncthreads();
+      continue;
+    }
+    const double ajj = 1.0 / rjj;
+    // x_i = sum_{t=i}^{j-1} Winv[i][t] * R[t][j], for i < j (uses columns < j, already inverted)
+    double x = 0.0;
+    const int i = tid;
+    if (i < j) {
+      for (int t = i; t < j; ++t) x = fma(W[i + t * l], W[t + j * l], x);
+    }
+    __syncthreads();
+    if (i < j) W[i + j * l] = -ajj * x;
+    if (tid == 0) W[j + j * l] = ajj;
+    __syncthreads();
+  }
+  for (int t = tid; t < l * l; t += nt) {
+    int i = t % l, j = t / l;
+    Rinv[t] = (i <= j) ? W[t] : 0.0;
+  }
+  if (tid == 0 && s_deficient) atomicAdd(&status->deficient, s_deficient);
+}
+
+__global__ void tri_product_kernel(const double* __restrict__ R2, const double* __restrict__ R1,
+                                   int l, double* __restrict__ out, int transpose_out) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < l * l; t += gridDim.x * blockDim.x) {
+    int i = t % l, j = t / l;
+    double s = 0.0;
+    if (i <= j)
+      for (int u = i; u <= j; ++u) s = fma(R2[i + u * l], R1[u + j * l], s);
+    if (transpose_out) out[j + i * l] = s;
+    else out[t] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One-sided Jacobi
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// player at position `pos` in round `r` of a round-robin on 2P players
+__device__ __forceinline__ int rr_player(int pos, int r, int twoP) {
+  if (pos == 0) return 0;
+  return 1 + (pos - 1 + r) % (twoP - 1);
+}
+
+__global__ void __launch_bounds__(SMALL_THREADS)
+jacobi_svd_kernel(const double* __restrict__ M, int l, int64_t ldm, double* __restrict__ sig,
+                  double* __restrict__ Um, int64_t ldu, double* __restrict__ Vm, int64_t ldv,
+                  double* __restrict__ work, DeviceStatus* status) {
+  const int twoP = (l + 1) & ~1;  // even number of columns (one zero column if l is odd)
+  const int P = twoP / 2;
+  double* Wm = work;                       // l x twoP, column-major (ld l)
+  double* Wv = work + (int64_t)l * twoP;   // l x twoP
+  __shared__ int s_rot;
+  __shared__ double s_norm[RSVD_L_MAX + 1];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nwarps = nt >> 5;
+
+  for (int t = tid; t < l * twoP; t += nt) {
+    int i = t % l, j = t / l;
+    Wm[t] = (j < l) ? M[i + (int64_t)j * ldm] : 0.0;
+    Wv[t] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  const double tol = sqrt((double)l) * DBL_EPSILON;
+  int sweep = 0;
+  const int max_sweeps = 30;
+  if (tid == 0) s_rot = 0;
+  __syncthreads();
+  for (; sweep < max_sweeps; ++sweep) {
+    for (int r = 0; r < twoP - 1; ++r) {
+      for (int pr = warp; pr < P; pr += nwarps) {
+        int p = rr_player(pr, r, twoP), q = rr_player(twoP - 1 - pr, r, twoP);
+        if (p > q) { int t = p; p = q; q = t; }
+        double* cp = Wm + (int64_t)p * l;
+        double* cq = Wm + (int64_t)q * l;
+        double a = 0.0, b = 0.0, g = 0.0;
+        for (int i = lane; i < l; i += 32) {
+          double x = cp[i], y = cq[i];
+          a = fma(x, x, a);
+          b = fma(y, y, b);
+          g = fma(x, y, g);
+        }
+        a = warp_sum(a);
+        b = warp_sum(b);
+        g = warp_sum(g);
+        if (g != 0.0 && fabs(g) > tol * sqrt(a) * sqrt(b)) {
+          // Rutishauser: zeta = (b - a) / (2g), t = sign(zeta)/(|zeta| + sqrt(1+zeta^2))
+          double zeta = (b - a) / (2.0 * g);
+          double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+          double c = rsqrt(fma(t, t, 1.0));
+          double s = c * t;
+          for (int i = lane; i < l; i += 32) {
+            double x = cp[i], y = cq[i];
+            cp[i] = c * x - s * y;
+            cq[i] = s * x + c * y;
+          }
+          double* vp = Wv + (int64_t)p * l;
+          double* vq = Wv + (int64_t)q * l;
+          for (int i = lane; i < l; i += 32) {
+            double x = vp[i], y = vq[i];
+            vp[i] = c * x - s * y;
+            vq[i] = s * x + c * y;
+          }
+          if (lane == 0) s_rot = 1;
+        }
+      }
+      __syncthreads();
+    }
+    const int rot = s_rot;
+    __syncthreads();
+    if (tid == 0) s_rot = 0;
+    __syncthreads();
+    if (!rot) break;
+  }
+  if (tid == 0) {
+    status->jacobi_sweeps = sweep + 1;
+    if (sweep >= max_sweeps) set_flag(status, RSVD_ERR_JACOBI);
+  }
+  // column norms
+  for (int c = warp; c < l; c += nwarps) {
+    const double* cp = Wm + (int64_t)c * l;
+    double a = 0.0;
+    for (int i = lane; i < l; i += 32) a = fma(cp[i], cp[i], a);
+    a = warp_sum(a);
+    if (lane == 0) s_norm[c] = sqrt(a);
+  }
+  __syncthreads();
+  // sort descending by rank; ties keep column order
+  for (int c = warp; c < l; c += nwarps) {
+    const double sc = s_norm[c];
+    int rank = 0;
+    for (int d = lane; d < l; d += 32) {
+      double sd = s_norm[d];
+      rank += (sd > sc || (sd == sc && d < c)) ? 1 : 0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rank += __shfl_xor_sync(0xffffffffu, rank, o);
+    const double inv = sc > 0.0 ? 1.0 / sc : 0.0;
+    if (lane == 0) sig[rank] = sc;
+    for (int i = lane; i < l; i += 32) {
+      Um[i + (int64_t)rank * ldu] = Wm[i + (int64_t)c * l] * inv;
+      Vm[i + (int64_t)rank * ldv] = Wv[i + (int64_t)c * l];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Sign convention and outputs
+// ---------------------------------------------------------------------------
+
+__global__ void sign_kernel(double* __restrict__ U, int64_t m, int64_t ldu,
+                            double* __restrict__ sign) {
+  const int col = blockIdx.x;
+  double* u = U + (int64_t)col * ldu;
+  double best = -1.0;
+  int64_t bidx = 0;
+  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
+    double v = fabs(u[i]);
+    if (v > best) { best = v; bidx = i; }
+  }
+  __shared__ double sv[1024];
+  __shared__ int64_t si[1024];
+  sv[threadIdx.x] = best;
+  si[threadIdx.x] = bidx;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      double o = sv[threadIdx.x + s];
+      int64_t oi = si[threadIdx.x + s];
+      if (o > sv[threadIdx.x] || (o == sv[threadIdx.x] && oi < si[threadIdx.x])) {
+        sv[threadIdx.x] = o;
+        si[threadIdx.x] = oi;
+      }
+    }
+    __syncthreads();
+  }
+  __shared__ double s_sign;
+  if (threadIdx.x == 0) {
+    s_sign = (u[si[0]] < 0.0) ? -1.0 : 1.0;
+    sign[col] = s_sign;
+  }
+  __syncthreads();
+  if (s_sign < 0.0)
+    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) u[i] = -u[i];
+}
+
+__global__ void vt_kernel(const double* __restrict__ Vk, int64_t n, int k,
+                          const double* __restrict__ sign, double* __restrict__ VT, int64_t ldvt,
+                          const double* __restrict__ sig, double* __restrict__ S) {
+  // VT (k x n): VT[i + j*ldvt] = sign[i] * Vk[j + i*n]
+  const int64_t total = n * (int64_t)k;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t j = t / k;
+    int i = (int)(t - j * k);
+    VT[i + j * ldvt] = sign[i] * Vk[j + (int64_t)i * n];
+  }
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i < k; i += blockDim.x) S[i] = sig[i];
+}
+
+}  // namespace
+
+cudaError_t launch_chol_inv(const double* G, int64_t ldg, int l, double* R, double* Rinv,
+                            double* work, DeviceStatus* status, cudaStream_t st) {
+  size_t smem = (size_t)l * l * sizeof(double);
+  if (smem <= 200 * 1024) {
+    static bool attr_set = false;
+    if (!attr_set) {
+      cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           200 * 1024);
+      attr_set = true;
+    }
+    chol_inv_kernel<<<1, SMALL_THREADS, smem, st>>>(G, ldg, l, R, Rinv, nullptr, status);
+  } else {
+    chol_inv_kernel<<<1, SMALL_THREADS, 0, st>>>(G, ldg, l, R, Rinv, work, status);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tri_product(const double* R2, const double* R1, int l, double* out,
+                               bool transpose_out, cudaStream_t st) {
+  int total = l * l;
+  tri_product_kernel<<<(total + 255) / 256, 256, 0, st>>>(R2, R1, l, out, transpose_out ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jacobi_svd(const double* M, int l, int64_t ldm, double* sig, double* Um,
+                              int64_t ldu, double* Vm, int64_t ldv, double* work,
+                              DeviceStatus* status, cudaStream_t st) {
+  jacobi_svd_kernel<<<1, SMALL_THREADS, 0, st>>>(M, l, ldm, sig, Um, ldu, Vm, ldv, work, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_f64(double* U, int64_t m, int64_t ldu, int k, const double* Vk,
+                                int64_t n, double* VT, int64_t ldvt, const double* sig, double* S,
+                                double* sign_work, cudaStream_t st) {
+  sign_kernel<<<k, 1024, 0, st>>>(U, m, ldu, sign_work);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int64_t total = n * (int64_t)k;
+  int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
+  vt_kernel<<<blocks, 256, 0, st>>>(Vk, n, k, sign_work, VT, ldvt, sig, S);
+  return cudaGetLastError();
+}
+
+}  // namespace rsvd

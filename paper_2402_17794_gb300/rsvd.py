@@ -1,0 +1,179 @@
+"""Python binding of the C ABI (include/rsvd.h), torch tensors as buffers.
+
+The functions carry the C names and only marshal arguments: every step of
+the randomized SVD runs in the library's CUDA kernels.  Torch supplies device
+memory and the stream.
+
+Layout: a column-major r x c matrix with leading dimension ld is held in a
+torch tensor of shape (c, ld) (row j of the tensor is column j of the
+matrix); :func:`colmajor` allocates one, :func:`from_numpy_f` converts a
+Fortran-ordered numpy array.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+
+F64, BF16 = 0, 2
+PLAIN, MIXED = 0, 1
+STATUS = {0: "ok", 1: "cholesky", 2: "jacobi", 3: "timeout", 4: "workspace", 5: "cuda",
+          6: "nonfinite", 7: "unsupported"}
+
+
+class RsvdError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = _lib.load().rsvd_status_string(code).decode()
+        super().__init__(f"{where}: status {code} ({msg})")
+        self.code = code
+
+
+def _check(code: int, where: str) -> int:
+    if code != 0:
+        raise RsvdError(code, where)
+    return code
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def colmajor(rows: int, cols: int, dtype=torch.float64, ld: int | None = None,
+             device="cuda", zero: bool = False):
+    ld = ld or rows
+    f = torch.zeros if zero else torch.empty
+    return f(cols, ld, dtype=dtype, device=device)
+
+
+def from_numpy_f(a: np.ndarray, device="cuda", dtype=None):
+    """Column-major torch copy of a 2-D numpy array (any order)."""
+    t = torch.from_numpy(np.ascontiguousarray(np.asarray(a).T))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.to(device)
+
+
+def to_numpy_f(t, rows: int | None = None) -> np.ndarray:
+    """numpy (rows x cols) Fortran array from a column-major tensor (cols, ld)."""
+    a = t.detach().to("cpu", dtype=torch.float64).numpy().T
+    if rows is not None:
+        a = a[:rows]
+    return np.asfortranarray(a)
+
+
+# ---------------------------------------------------------------------------
+# C entry points (same names)
+# ---------------------------------------------------------------------------
+
+def rsvd_plan_create(m_max, n_max, l_max, a_dtype=F64, mode=PLAIN, stream=None):
+    lib = _lib.load()
+    h = ctypes.c_void_p()
+    _check(lib.rsvd_plan_create(ctypes.byref(h), m_max, n_max, l_max, a_dtype, mode,
+                                _stream_handle(stream)), "rsvd_plan_create")
+    return h
+
+
+def rsvd_workspace_size(plan) -> int:
+    n = ctypes.c_size_t()
+    _check(_lib.load().rsvd_workspace_size(plan, ctypes.byref(n)), "rsvd_workspace_size")
+    return n.value
+
+
+def rsvd_set_workspace(plan, buf) -> None:
+    _check(_lib.load().rsvd_set_workspace(plan, _ptr(buf), buf.numel() * buf.element_size()),
+           "rsvd_set_workspace")
+
+
+def rsvd_plan_status(plan) -> int:
+    return _lib.load().rsvd_plan_status(plan)
+
+
+def rsvd_plan_set_stream(plan, stream=None) -> None:
+    _check(_lib.load().rsvd_plan_set_stream(plan, _stream_handle(stream)), "rsvd_plan_set_stream")
+
+
+def rsvd_plan_destroy(plan) -> None:
+    _lib.load().rsvd_plan_destroy(plan)
+
+
+def rsvd_status_string(code: int) -> str:
+    return _lib.load().rsvd_status_string(code).decode()
+
+
+def rsvd_solve(plan, A, m, n, lda, k, p, q, seed, U, ldu, S, VT, ldvt) -> int:
+    return _lib.load().rsvd_solve(plan, _ptr(A), m, n, lda, k, p, q, seed, _ptr(U), ldu, _ptr(S),
+                                  _ptr(VT), ldvt)
+
+
+def rsvd_gaussian(plan, n, l, seed, stream_id, out_dtype, out, ldo) -> int:
+    return _lib.load().rsvd_gaussian(plan, n, l, seed, stream_id, out_dtype, _ptr(out), ldo)
+
+
+def rsvd_apply_a(plan, A, m, n, lda, X, ldx, l, Y, ldy) -> int:
+    return _lib.load().rsvd_apply_a(plan, _ptr(A), m, n, lda, _ptr(X), ldx, l, _ptr(Y), ldy)
+
+
+def rsvd_apply_at(plan, A, m, n, lda, X, ldx, l, Z, ldz) -> int:
+    return _lib.load().rsvd_apply_at(plan, _ptr(A), m, n, lda, _ptr(X), ldx, l, _ptr(Z), ldz)
+
+
+def rsvd_orth(plan, Y, rows, l, ldy, Q, ldq, R=None, ldr=0) -> int:
+    return _lib.load().rsvd_orth(plan, _ptr(Y), rows, l, ldy, _ptr(Q), ldq, _ptr(R), ldr)
+
+
+def rsvd_small_svd(plan, M, l, ldm, sig, Um, ldu, Vm, ldv) -> int:
+    return _lib.load().rsvd_small_svd(plan, _ptr(M), l, ldm, _ptr(sig), _ptr(Um), ldu, _ptr(Vm),
+                                      ldv)
+
+
+# ---------------------------------------------------------------------------
+# Convenience wrapper
+# ---------------------------------------------------------------------------
+
+class Plan:
+    """Owns a C plan and its torch-allocated workspace."""
+
+    def __init__(self, m_max, n_max, l_max, a_dtype=F64, mode=PLAIN, stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("the randomized SVD library needs a CUDA GPU")
+        self.stream = stream
+        self.handle = rsvd_plan_create(m_max, n_max, l_max, a_dtype, mode, stream)
+        self.mode = mode
+        nbytes = rsvd_workspace_size(self.handle)
+        self.workspace = torch.empty(max(nbytes, 256), dtype=torch.uint8, device="cuda")
+        rsvd_set_workspace(self.handle, self.workspace)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None:
+            try:
+                rsvd_plan_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+    def status(self) -> int:
+        return rsvd_plan_status(self.handle)
+
+    def solve(self, A, m, n, k, p, q, seed, lda=None, out=None):
+        """A: column-major device tensor (n, lda).  Returns (U, S, VT) as
+        column-major tensors U (k, m), S (k,), VT (n, k); enqueued only."""
+        lda = lda or A.shape[1]
+        odt = torch.float64 if self.mode == PLAIN else torch.float32
+        if out is None:
+            U = torch.empty(k, m, dtype=odt, device=A.device)
+            S = torch.empty(k, dtype=torch.float64, device=A.device)
+            VT = torch.empty(n, k, dtype=odt, device=A.device)
+        else:
+            U, S, VT = out
+        _check(rsvd_solve(self.handle, A, m, n, lda, k, p, q, seed, U, U.shape[1], S, VT,
+                          VT.shape[1]), "rsvd_solve")
+        return U, S, VT
