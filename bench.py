@@ -1,0 +1,461 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 randomized SVD (Algorithm 4 of the thesis, Section 3.3).
+
+One step = one full rank-k randomized SVD (all steps of the hot path: Omega,
+the 2q+2 passes over A, every CholeskyQR2, the Jacobi SVD of the l x l
+factor, the lift and the output layout) on a seeded synthetic matrix that is
+already resident in HBM.
+
+Default workload (one GPU): A 16384 x 8192 FP64 = U diag(sigma) V^T with Haar
+factors and sigma_i = i^-1.5, k = 64, p = 16, q = 2, Omega 8192 x 80.  A is
+1.07 GB, larger than the 129 MB L2, so no flush is needed between steps.
+
+Printed: one JSON line (rank 0) with solves/s, the A-pass bandwidth, the
+roofline of the dominant kernel, the end-to-end rate through the C ABI with
+host buffers, the CPU oracle's rate on this host, clocks sampled during the
+timed region and the number of this library's kernel launches per step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank solves its own replica of the workload
+(the path has no data exchange between problems); the job rate is the sum
+of the ranks' solves over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "RSVD A-pass HBM TB/s & solves/s, mixed vs FP64 plain @σ err≤1e-3; p99 ms"
+
+WORKLOADS = {
+    "plain-fp64": dict(
+        desc="plain RSVD FP64 on GPU: A 16384x8192 FP64, Haar factors, sigma_i=i^-1.5; "
+             "k=64, p=16, q=2; Gaussian Omega 8192x80",
+        m=16384, n=8192, k=64, p=16, q=2, spectrum=("poly", 1.5), seed_a=0, seed=2,
+        dtype="f64"),
+}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, device_uuid: str | None):
+        self.uuid = device_uuid
+        self.proc = None
+        self.out = os.path.join("/tmp", f"rsvd_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={','.join(self.FIELDS)}",
+               "--format=csv,noheader,nounits", "-lms", "100"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.fh = open(self.out, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.out) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) == len(self.FIELDS):
+                    rows.append(parts)
+        os.unlink(self.out)
+        if not rows and self.uuid:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _sigma(w):
+    from paper_2402_17794_gb300 import synthetic as syn
+    kind, arg = w["spectrum"]
+    r = min(w["m"], w["n"])
+    if kind == "poly":
+        return syn.spectrum("poly", r, alpha=arg)
+    raise ValueError(kind)
+
+
+def _make_input(w, rank):
+    import torch
+    from paper_2402_17794_gb300 import synthetic as syn
+    return syn.lowrank_matrix_torch(w["m"], w["n"], _sigma(w), seed=w["seed_a"] + 1000 * rank,
+                                    device="cuda", dtype=torch.float64)
+
+
+def _oracle_rate(A_host, w, budget_s: float):
+    """Times the CPU oracle (as it stands) on this host: full solves until the
+    budget is spent (at least one)."""
+    import numpy as np
+
+    import oracle
+    A = np.asfortranarray(A_host)
+    n_done, t0 = 0, time.perf_counter()
+    while True:
+        oracle.rsvd(A, w["k"], w["p"], w["q"], w["seed"] + n_done)
+        n_done += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or n_done >= 50:
+            break
+    return n_done, el
+
+
+def _cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count()
+
+
+def run_ours(args):
+    import torch
+
+    import __graft_entry__
+    from paper_2402_17794_gb300 import rsvd as R
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    __graft_entry__.build()
+    w = WORKLOADS[args.workload]
+    m, n, k, p, q, seed = w["m"], w["n"], w["k"], w["p"], w["q"], w["seed"]
+    l = k + p
+    passes = 2 * q + 2
+    a_bytes = m * n * 8
+    dA = _make_input(w, rank)
+    stream = torch.cuda.current_stream()
+    plan = R.Plan(m, n, l)
+    U = torch.empty(k, m, dtype=torch.float64, device="cuda")
+    S = torch.empty(k, dtype=torch.float64, device="cuda")
+    VT = torch.empty(n, k, dtype=torch.float64, device="cuda")
+
+    def step(i):
+        R._check(R.rsvd_solve(plan.handle, dA, m, n, m, k, p, q, seed, U, m, S, VT, k),
+                 "rsvd_solve")
+
+    for i in range(args.warmup):
+        step(i)
+    st = plan.status()
+    if st != 0:
+        raise RuntimeError(f"warm-up solve failed: {R.rsvd_status_string(st)}")
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid)
+    sampler.start()
+    _barrier(world)
+    torch.cuda.synchronize()
+    l0 = R.rsvd_kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        step(i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = R.rsvd_kernel_launches() - l0
+    _barrier(world)
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    st = plan.status()
+    if st != 0:
+        raise RuntimeError(f"timed solve failed: {R.rsvd_status_string(st)}")
+    sweeps, _ = R.rsvd_plan_diagnostics(plan.handle)
+    ms_max = _max_over_ranks(ms, world)
+    solves = args.steps * world
+    value = solves / (ms_max / 1e3)
+    ms_per_step = ms_max / args.steps
+
+    # --- the dominant kernels, timed alone through the step entry points ---
+    Om = R.colmajor(n, l)
+    Y = R.colmajor(m, l)
+    Z = R.colmajor(n, l)
+    R.rsvd_gaussian(plan.handle, n, l, seed, 0, R.F64, Om, n)
+    Qm = torch.linalg.qr(torch.randn(m, l, dtype=torch.float64, device="cuda"))[0].T.contiguous()
+
+    def time_call(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    t_an = time_call(lambda: R.rsvd_apply_a(plan.handle, dA, m, n, m, Om, n, l, Y, m))
+    t_at = time_call(lambda: R.rsvd_apply_at(plan.handle, dA, m, n, m, Qm, m, l, Z, n))
+    flops = 2.0 * m * n * l
+    peaks, peak_kind = _peaks()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    fp64_peak = 152 * 2 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s: 152 SMs x 2 DFMA/clk x 2 flop
+    dom_ms = max(t_an, t_at)
+    dom = "gemm_f64_kernel<5,true> (A^T X pass)" if t_at >= t_an else \
+        "gemm_f64_kernel<5,false> (A X pass)"
+    achieved = flops / (dom_ms / 1e3) / 1e12
+    traffic = _traffic_from_profile()
+    roofline = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 4),
+                "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
+                "frac": round(achieved / fp64_peak, 4),
+                "traffic": traffic,
+                "peak_source": f"derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x {sm_max:.0f} MHz",
+                "algorithmic_flops_per_launch": flops,
+                "ms_per_launch": round(dom_ms, 4)}
+    a_pass = {"ms_ax": round(t_an, 4), "ms_atx": round(t_at, 4),
+              "gbps_ax": round(a_bytes / (t_an / 1e3) / 1e9, 2),
+              "gbps_atx": round(a_bytes / (t_at / 1e3) / 1e9, 2),
+              "gbps_in_solve": round(passes * a_bytes / (ms_per_step / 1e3) / 1e9, 2),
+              "hbm_peak_gbs": peaks.get("hbm_gbs"), "passes_per_solve": passes}
+
+    # --- end to end through the C ABI with host buffers ---
+    A_h = torch.empty(dA.shape, dtype=dA.dtype, pin_memory=True)
+    A_h.copy_(dA)
+    U_h = torch.empty(U.shape, dtype=U.dtype, pin_memory=True)
+    S_h = torch.empty(S.shape, dtype=S.dtype, pin_memory=True)
+    VT_h = torch.empty(VT.shape, dtype=VT.dtype, pin_memory=True)
+    dA2 = torch.empty_like(dA)
+
+    def e2e_step(i):
+        dA2.copy_(A_h, non_blocking=True)
+        R._check(R.rsvd_solve(plan.handle, dA2, m, n, m, k, p, q, seed, U, m, S, VT, k),
+                 "rsvd_solve")
+        U_h.copy_(U, non_blocking=True)
+        S_h.copy_(S, non_blocking=True)
+        VT_h.copy_(VT, non_blocking=True)
+
+    e2e_steps = max(1, min(args.steps, 5))
+    e2e_step(0)
+    torch.cuda.synchronize()
+    _barrier(world)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for i in range(e2e_steps):
+        e2e_step(i)
+    b.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = _max_over_ranks(a.elapsed_time(b), world)
+    e2e = {"value": round(e2e_steps * world / (e2e_ms / 1e3), 4), "unit": "solves/s",
+           "h2d_bytes_per_step": a_bytes,
+           "d2h_bytes_per_step": (m * k + k + k * n) * 8}
+    st = plan.status()
+    if st != 0:
+        raise RuntimeError(f"e2e solve failed: {R.rsvd_status_string(st)}")
+
+    # --- CPU oracle on this host (rank 0, N = 1 only) ---
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        A_np = dA.cpu().numpy().T
+        done, el = _oracle_rate(A_np, w, args.cpu_budget)
+        cpu = {"value": round(done / el, 4), "unit": "solves/s", "cores": _cores(),
+               "kind": "oracle",
+               "sample": f"{done} full oracle solve(s) of the same workload in {el:.1f} s "
+                         f"(numpy FP64, LAPACK QR/SVD)"}
+
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded Haar factors, known spectrum)",
+        "config": {"workload": w["desc"], "m": m, "n": n, "k": k, "p": p, "q": q,
+                   "a_dtype": w["dtype"], "parallelism": f"replicas x{world}" if world > 1 else "1 gpu",
+                   "l2": "inputs larger than L2 (A is %.2f GB; L2 129 MB): no flush" % (a_bytes / 1e9)},
+        "a_pass": a_pass,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "gpu_launches_per_step": launches / args.steps,
+        "jacobi_sweeps": sweeps,
+        "clocks": clocks,
+        "peaks_source": peak_kind,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def _traffic_from_profile():
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, if that summary was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d.get("plain-fp64")
+    except (OSError, ValueError):
+        return None
+
+
+def run_reference(args):
+    """The CPU oracle timed as it stands on this host's cores, same workload."""
+    world, rank, local = _dist()
+    if rank != 0:
+        return
+    import numpy as np
+    import torch
+
+    w = WORKLOADS[args.workload]
+    m, n, k, p, q = w["m"], w["n"], w["k"], w["p"], w["q"]
+    if torch.cuda.is_available():
+        A = _make_input(w, 0).cpu().numpy().T
+    else:
+        from paper_2402_17794_gb300 import synthetic as syn
+        A = syn.lowrank_matrix(m, n, _sigma(w), seed=w["seed_a"])
+    A = np.asfortranarray(A)
+    import oracle
+    for i in range(args.warmup):
+        oracle.rsvd(A, k, p, q, w["seed"] + i)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        oracle.rsvd(A, k, p, q, w["seed"] + i)
+    el = time.perf_counter() - t0
+    value = args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "solves/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(el / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["desc"], "m": m, "n": n, "k": k, "p": p, "q": q,
+                   "a_dtype": w["dtype"]},
+        "cpu_baseline": {"value": round(value, 4), "unit": "solves/s", "cores": _cores(),
+                         "kind": "oracle",
+                         "sample": f"{args.steps} full oracle solves of the workload"},
+        "e2e": {"value": round(value, 4), "unit": "solves/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_profile_case(args):
+    """A reduced case of the same kernels for ncu captures (no timing):
+    A 8192 x 4096 FP64 (268 MB, larger than L2), l = 80; two passes of each
+    kind and one full solve."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from paper_2402_17794_gb300 import rsvd as R
+    from paper_2402_17794_gb300 import synthetic as syn
+
+    __graft_entry__.build()
+    m, n, k, p, q = 8192, 4096, 64, 16, 2
+    l = k + p
+    rng = np.random.default_rng(0)
+    dA = torch.from_numpy(rng.standard_normal((n, m))).cuda()
+    plan = R.Plan(m, n, l)
+    Om = R.colmajor(n, l)
+    Y = R.colmajor(m, l)
+    Z = R.colmajor(n, l)
+    R.rsvd_gaussian(plan.handle, n, l, 1, 0, R.F64, Om, n)
+    for _ in range(2):
+        R.rsvd_apply_a(plan.handle, dA, m, n, m, Om, n, l, Y, m)
+        R.rsvd_apply_at(plan.handle, dA, m, n, m, Y, m, l, Z, n)
+    plan.solve(dA, m, n, k, p, q, 3)
+    st = plan.status()
+    if st != 0:
+        raise RuntimeError(R.rsvd_status_string(st))
+    print("profile case done")
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="plain-fp64")
+    ap.add_argument("--cpu-budget", type=float, default=15.0,
+                    help="seconds of CPU oracle time for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run a reduced case of the same kernels for ncu (no timing)")
+    args = ap.parse_args()
+    if args.profile_case:
+        run_profile_case(args)
+        return
+    if args.warmup < 3 and args.impl == "ours":
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -111,12 +111,27 @@ int rsvd_set_workspace(rsvd_plan_t plan, void* dev_ptr, size_t bytes);
  */
 int rsvd_plan_status(rsvd_plan_t plan);
 
+/*
+ * rsvd_plan_diagnostics: waits for the plan's stream and reports, for the
+ * work enqueued so far, the sweeps the last Jacobi SVD took and the number of
+ * columns CholeskyQR dropped as numerically dependent (cumulative).  Either
+ * pointer (host) may be NULL.
+ */
+int rsvd_plan_diagnostics(rsvd_plan_t plan, int* jacobi_sweeps, int* dropped_columns);
+
 /* Sets the stream later calls enqueue on. */
 int rsvd_plan_set_stream(rsvd_plan_t plan, void* cuda_stream);
 
 int rsvd_plan_destroy(rsvd_plan_t plan);
 
 const char* rsvd_status_string(int status);
+
+/*
+ * rsvd_kernel_launches: number of CUDA kernels this library has launched in
+ * this process (all plans, all streams), counted on the host at each launch.
+ * A diagnostic for callers that account GPU work; it never blocks.
+ */
+uint64_t rsvd_kernel_launches(void);
 
 /* ---------------------------------------------------------------------- */
 /* Full solve: Algorithm 4 (Section 3.3), truncated to rank k (Section 3.1) */

@@ -22,8 +22,10 @@ SIGNATURES = {
     "rsvd_set_workspace": (c_int, [c_void_p, c_void_p, c_size_t]),
     "rsvd_plan_status": (c_int, [c_void_p]),
     "rsvd_plan_set_stream": (c_int, [c_void_p, c_void_p]),
+    "rsvd_plan_diagnostics": (c_int, [c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
     "rsvd_plan_destroy": (c_int, [c_void_p]),
     "rsvd_status_string": (ctypes.c_char_p, [c_int]),
+    "rsvd_kernel_launches": (c_uint64, []),
     "rsvd_solve": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_int64, c_int, c_int, c_int,
                            c_uint64, c_void_p, c_int64, P_double, c_void_p, c_int64]),
     "rsvd_gaussian": (c_int, [c_void_p, c_int64, c_int, c_uint64, c_uint32, c_int, c_void_p,

@@ -100,7 +100,8 @@ int gemm(rsvd_plan_t P, const double* A, int64_t lda, bool trans, const double* 
   return RSVD_OK;
 }
 
-// CholeskyQR2: Q = orth(Y); optionally Mt = (R2 R1)^T (ld l).
+// CholeskyQR2: Q = orth(Y) (skipped when Q is NULL); optionally
+// Rprod = R2 R1 or its transpose (ld l), the R factor of Y = Q R.
 int orth_f64(rsvd_plan_t P, const double* Y, int64_t rows, int l, int64_t ldy, double* Q,
              int64_t ldq, double* T, double* Rprod, bool transpose_R) {
   Small S = small_of(P);
@@ -113,7 +114,7 @@ int orth_f64(rsvd_plan_t P, const double* Y, int64_t rows, int l, int64_t ldy, d
   // pass 2
   if ((rc = gemm(P, T, rows, true, T, rows, S.G, l, l, rows, l))) return rc;
   CK(launch_chol_inv(S.G, l, l, S.R2, S.R2i, S.cholw, st, P->stream));
-  if ((rc = gemm(P, T, rows, false, S.R2i, l, Q, ldq, rows, l, l))) return rc;
+  if (Q && (rc = gemm(P, T, rows, false, S.R2i, l, Q, ldq, rows, l, l))) return rc;
   if (Rprod) CK(launch_tri_product(S.R2, S.R1, l, Rprod, transpose_R, P->stream));
   return RSVD_OK;
 }
@@ -141,14 +142,24 @@ int solve_plain(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t ld
     if ((rc = gemm(P, A, lda, false, om, n, y, m, m, n, l))) return rc;
     if ((rc = orth_f64(P, y, m, l, m, qm, m, tmp, nullptr, false))) return rc;
   }
-  // 6. B^T = A^T Q;  7. B^T = Q_B R_B, SVD of R_B^T by one-sided Jacobi
+  // 6. B^T = A^T Q.  7. B^T = Q_B R_B by CholeskyQR2 (only R_B is formed);
+  // one-sided Jacobi on R_B^T = U~ Sigma V_R^T gives sigma and U~ (the left
+  // singular vectors of B); the right ones follow as V = B^T U~ Sigma^-1.
   if ((rc = gemm(P, A, lda, true, qm, m, z, n, n, m, l))) return rc;
-  if ((rc = orth_f64(P, z, n, l, n, qb, n, tmp, S.Mt, true))) return rc;
-  CK(launch_jacobi_svd(S.Mt, l, l, S.sig, S.Um, l, S.Vm, l, S.jw, dstatus(P), P->stream));
-  // 8. U = Q U~ (first k columns), V = Q_B V_R (first k columns)
+  if ((rc = orth_f64(P, z, n, l, n, nullptr, n, tmp, S.Mt, true))) return rc;
+  double* us_inv = S.Vm;
+  CK(launch_jacobi_svd(S.Mt, l, l, S.sig, S.Um, l, nullptr, l, us_inv, S.jw, dstatus(P),
+                       P->stream));
+  // 8. U = Q U~ (first k columns), V_k = B^T U~_k Sigma_k^-1
   if ((rc = gemm(P, qm, m, false, S.Um, l, U, ldu, m, l, k))) return rc;
-  if ((rc = gemm(P, qb, n, false, S.Vm, l, z, n, n, l, k))) return rc;
-  CK(launch_finalize_f64(U, m, ldu, k, z, n, VT, ldvt, S.sig, Sout, S.sign, P->stream));
+  if ((rc = gemm(P, z, n, false, us_inv, l, tmp, n, n, l, k))) return rc;
+  // One CholeskyQR pass restores orthonormality of V_k to rounding (the
+  // product above carries relative errors ~ eps sigma_1/sigma_i); the
+  // triangular factor is I + O(eps sigma_1/sigma_k).
+  if ((rc = gemm(P, tmp, n, true, tmp, n, S.G, k, k, n, k))) return rc;
+  CK(launch_chol_inv(S.G, k, k, S.R1, S.R1i, S.cholw, dstatus(P), P->stream));
+  if ((rc = gemm(P, tmp, n, false, S.R1i, k, qb, n, n, k, k))) return rc;
+  CK(launch_finalize_f64(U, m, ldu, k, qb, n, VT, ldvt, S.sig, Sout, S.sign, P->stream));
   return RSVD_OK;
 }
 
@@ -227,6 +238,19 @@ int rsvd_plan_status(rsvd_plan_t plan) {
   int flags = plan->h_status[0];
   if (cudaMemsetAsync(&d->flags, 0, sizeof(int), plan->stream) != cudaSuccess) return RSVD_ERR_CUDA;
   return status_from_flags(flags);
+}
+
+int rsvd_plan_diagnostics(rsvd_plan_t plan, int* jacobi_sweeps, int* dropped_columns) {
+  if (!plan) return -1;
+  if (!plan->ws) return RSVD_ERR_WORKSPACE;
+  DeviceStatus* d = dstatus(plan);
+  if (cudaMemcpyAsync(plan->h_status, &d->flags, 4 * sizeof(int), cudaMemcpyDeviceToHost,
+                      plan->stream) != cudaSuccess)
+    return RSVD_ERR_CUDA;
+  if (cudaStreamSynchronize(plan->stream) != cudaSuccess) return RSVD_ERR_CUDA;
+  if (jacobi_sweeps) *jacobi_sweeps = plan->h_status[1];
+  if (dropped_columns) *dropped_columns = plan->h_status[2];
+  return RSVD_OK;
 }
 
 int rsvd_plan_destroy(rsvd_plan_t plan) {
@@ -363,8 +387,24 @@ int rsvd_small_svd(rsvd_plan_t plan, const double* M, int l, int64_t ldm, double
   if (ldv < l) return -9;
   if (!ready(plan)) return RSVD_ERR_WORKSPACE;
   Small S = small_of(plan);
-  CK(launch_jacobi_svd(M, l, ldm, sig, Um, ldu, Vm, ldv, S.jw, dstatus(plan), plan->stream));
+  CK(launch_jacobi_svd(M, l, ldm, sig, Um, ldu, Vm, ldv, nullptr, S.jw, dstatus(plan),
+                       plan->stream));
   return RSVD_OK;
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Launch accounting
+// ---------------------------------------------------------------------------
+#include <atomic>
+
+namespace {
+std::atomic<uint64_t> g_launches{0};
+}
+
+void rsvd::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+extern "C" uint64_t rsvd_kernel_launches(void) {
+  return g_launches.load(std::memory_order_relaxed);
+}

@@ -155,6 +155,7 @@ void launch_tn(const GemmF64& g, dim3 grid, double* out, int64_t ldo, int64_t kp
   else
     gemm_f64_kernel<TN, false><<<grid, THREADS, 0, st>>>(g.A, g.lda, g.X, g.ldx, out, ldo, g.M,
                                                          g.K, g.N, kps, pstride);
+  note_launch();
 }
 
 }  // namespace
@@ -201,6 +202,7 @@ cudaError_t launch_gemm_f64(const GemmF64& g, double* part, size_t part_elems, i
   int64_t total = pstride;
   int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)num_sms * 8);
   splitk_reduce_kernel<<<blocks, 256, 0, st>>>(part, (int)splits, pstride, g.M, g.N, g.C, g.ldc);
+  note_launch();
   return cudaGetLastError();
 }
 

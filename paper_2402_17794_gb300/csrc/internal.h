@@ -10,6 +10,10 @@
 
 namespace rsvd {
 
+// Host-side count of kernel launches made by this library (all launchers
+// call note_launch() once per <<<...>>>).
+void note_launch();
+
 constexpr int kMaxSplits = 32;      // split-K partial slices kept in workspace
 constexpr size_t kAlign = 256;
 
@@ -82,10 +86,11 @@ cudaError_t launch_chol_inv(const double* G, int64_t ldg, int l, double* R, doub
 cudaError_t launch_tri_product(const double* R2, const double* R1, int l, double* out,
                                bool transpose_out, cudaStream_t st);
 
-// One-CTA one-sided Jacobi SVD of the l x l matrix M (ldm).  work holds
-// 2 * l_even * l doubles.
+// One-CTA one-sided Jacobi SVD of the l x l matrix M (ldm): M = Um diag(sig) Vm^T.
+// Vm may be NULL (rotations not accumulated); UsInv (ld l), if non-NULL,
+// receives Um diag(1/sig).  work holds 2 * l_even * l doubles.
 cudaError_t launch_jacobi_svd(const double* M, int l, int64_t ldm, double* sig,
-                              double* Um, int64_t ldu, double* Vm, int64_t ldv,
+                              double* Um, int64_t ldu, double* Vm, int64_t ldv, double* UsInv,
                               double* work, DeviceStatus* status, cudaStream_t st);
 
 // Sign convention + outputs of the lift: flips columns of U (m x k, ldu, FP64)

@@ -79,9 +79,11 @@ cudaError_t launch_gaussian(int64_t n, int l, uint64_t seed, uint32_t stream_id,
   uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   if (out_dtype == RSVD_F64) {
     gaussian_kernel<double><<<blocks, threads, 0, st>>>(n, l, k0, k1, stream_id, (double*)out, ldo);
+    note_launch();
   } else if (out_dtype == RSVD_BF16) {
     gaussian_kernel<__nv_bfloat16><<<blocks, threads, 0, st>>>(n, l, k0, k1, stream_id,
                                                                (__nv_bfloat16*)out, ldo);
+    note_launch();
   } else {
     return cudaErrorInvalidValue;
   }

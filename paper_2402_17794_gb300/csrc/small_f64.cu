@@ -102,15 +102,12 @@ chol_inv_kernel(const double* __restrict__ G, int64_t ldg, int l, double* __rest
     __syncthreads();
     // trailing update of the upper triangle: W[i][c] -= R[j][i] R[j][c], j < i <= c
     const int rem = l - j - 1;
-    const int cnt = rem * (rem + 1) / 2;
-    for (int t = tid; t < cnt; t += nt) {
-      // map t -> (i, c) with j < i <= c < l, enumerating column by column
-      int cc = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
-      while ((cc + 1) * (cc + 2) / 2 <= t) ++cc;
-      while (cc * (cc + 1) / 2 > t) --cc;
-      int ii = t - cc * (cc + 1) / 2;
-      int i = j + 1 + ii, c = j + 1 + cc;
-      W[i + c * l] -= W[j + i * l] * W[j + c * l];
+    for (int t = tid; t < rem * rem; t += nt) {
+      const int ii = t % rem, cc = t / rem;
+      if (ii <= cc) {
+        const int i = j + 1 + ii, c = j + 1 + cc;
+        W[i + c * l] -= W[j + i * l] * W[j + c * l];
+      }
     }
     __syncthreads();
   }
@@ -176,66 +173,115 @@ __device__ __forceinline__ int rr_player(int pos, int r, int twoP) {
   return 1 + (pos - 1 + r) % (twoP - 1);
 }
 
+// Work layout: Wm (l x twoP) and, if V is accumulated, Wv (l x twoP), both
+// column-major with ld l; in dynamic shared memory when they fit, else in
+// `gwork`.  Each round of the round-robin ordering runs in three phases so
+// that the FP64 pipe (2 lanes per clock per SM) is spent on useful work:
+//   A. G threads per column pair form partial |c_p|^2, |c_q|^2, c_p.c_q over
+//      interleaved rows and reduce them with shuffles inside the group;
+//   B. one thread per pair turns (a, b, g) into a rotation (c, s);
+//   C. the G threads of each pair apply it to their rows.
 __global__ void __launch_bounds__(SMALL_THREADS)
 jacobi_svd_kernel(const double* __restrict__ M, int l, int64_t ldm, double* __restrict__ sig,
                   double* __restrict__ Um, int64_t ldu, double* __restrict__ Vm, int64_t ldv,
-                  double* __restrict__ work, DeviceStatus* status) {
+                  double* __restrict__ UsInv, double* __restrict__ gwork, int use_smem,
+                  DeviceStatus* status) {
+  extern __shared__ double jsm[];
   const int twoP = (l + 1) & ~1;  // even number of columns (one zero column if l is odd)
   const int P = twoP / 2;
-  double* Wm = work;                       // l x twoP, column-major (ld l)
-  double* Wv = work + (int64_t)l * twoP;   // l x twoP
+  const bool want_v = Vm != nullptr;
+  double* Wm = use_smem ? jsm : gwork;
+  double* Wv = Wm + (int64_t)l * twoP;
   __shared__ int s_rot;
   __shared__ double s_norm[RSVD_L_MAX + 1];
+  __shared__ double s_abg[(RSVD_L_MAX + 1) / 2][3];
+  __shared__ double s_cs[(RSVD_L_MAX + 1) / 2][2];
   const int tid = threadIdx.x, nt = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, nwarps = nt >> 5;
+  // threads per pair: power of two, at most 16 rows each
+  int G = 1;
+  while (G < 32 && (l + G - 1) / G > 16) G <<= 1;
+  const int items = P * G;
+  const int items_pad = (items + 31) & ~31;
 
   for (int t = tid; t < l * twoP; t += nt) {
     int i = t % l, j = t / l;
     Wm[t] = (j < l) ? M[i + (int64_t)j * ldm] : 0.0;
-    Wv[t] = (i == j) ? 1.0 : 0.0;
+    if (want_v) Wv[t] = (i == j) ? 1.0 : 0.0;
   }
+  if (tid == 0) s_rot = 0;
   __syncthreads();
   const double tol = sqrt((double)l) * DBL_EPSILON;
   int sweep = 0;
   const int max_sweeps = 30;
-  if (tid == 0) s_rot = 0;
-  __syncthreads();
   for (; sweep < max_sweeps; ++sweep) {
     for (int r = 0; r < twoP - 1; ++r) {
-      for (int pr = warp; pr < P; pr += nwarps) {
+      // A: partial dot products
+      for (int it = tid; it < items_pad; it += nt) {
+        const int pr = it / G, sub = it % G;
+        double a = 0.0, b = 0.0, g = 0.0;
+        if (it < items) {
+          int p = rr_player(pr, r, twoP), q = rr_player(twoP - 1 - pr, r, twoP);
+          if (p > q) { int t = p; p = q; q = t; }
+          const double* cp = Wm + (int64_t)p * l;
+          const double* cq = Wm + (int64_t)q * l;
+          for (int i = sub; i < l; i += G) {
+            double x = cp[i], y = cq[i];
+            a = fma(x, x, a);
+            b = fma(y, y, b);
+            g = fma(x, y, g);
+          }
+        }
+        for (int o = G >> 1; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          b += __shfl_xor_sync(0xffffffffu, b, o);
+          g += __shfl_xor_sync(0xffffffffu, g, o);
+        }
+        if (it < items && sub == 0) {
+          s_abg[pr][0] = a;
+          s_abg[pr][1] = b;
+          s_abg[pr][2] = g;
+        }
+      }
+      __syncthreads();
+      // B: rotation parameters (Rutishauser): zeta = (b - a) / (2g),
+      // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1+t^2), s = c t
+      for (int pr = tid; pr < P; pr += nt) {
+        const double a = s_abg[pr][0], b = s_abg[pr][1], g = s_abg[pr][2];
+        double c = 1.0, sn = 0.0;
+        if (g != 0.0 && fabs(g) > tol * sqrt(a) * sqrt(b)) {
+          const double zeta = (b - a) / (2.0 * g);
+          const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+          c = rsqrt(fma(t, t, 1.0));
+          sn = c * t;
+          s_rot = 1;
+        }
+        s_cs[pr][0] = c;
+        s_cs[pr][1] = sn;
+      }
+      __syncthreads();
+      // C: apply
+      for (int it = tid; it < items; it += nt) {
+        const int pr = it / G, sub = it % G;
+        const double c = s_cs[pr][0], sn = s_cs[pr][1];
+        if (sn == 0.0) continue;
         int p = rr_player(pr, r, twoP), q = rr_player(twoP - 1 - pr, r, twoP);
         if (p > q) { int t = p; p = q; q = t; }
         double* cp = Wm + (int64_t)p * l;
         double* cq = Wm + (int64_t)q * l;
-        double a = 0.0, b = 0.0, g = 0.0;
-        for (int i = lane; i < l; i += 32) {
+        for (int i = sub; i < l; i += G) {
           double x = cp[i], y = cq[i];
-          a = fma(x, x, a);
-          b = fma(y, y, b);
-          g = fma(x, y, g);
+          cp[i] = c * x - sn * y;
+          cq[i] = sn * x + c * y;
         }
-        a = warp_sum(a);
-        b = warp_sum(b);
-        g = warp_sum(g);
-        if (g != 0.0 && fabs(g) > tol * sqrt(a) * sqrt(b)) {
-          // Rutishauser: zeta = (b - a) / (2g), t = sign(zeta)/(|zeta| + sqrt(1+zeta^2))
-          double zeta = (b - a) / (2.0 * g);
-          double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
-          double c = rsqrt(fma(t, t, 1.0));
-          double s = c * t;
-          for (int i = lane; i < l; i += 32) {
-            double x = cp[i], y = cq[i];
-            cp[i] = c * x - s * y;
-            cq[i] = s * x + c * y;
-          }
+        if (want_v) {
           double* vp = Wv + (int64_t)p * l;
           double* vq = Wv + (int64_t)q * l;
-          for (int i = lane; i < l; i += 32) {
+          for (int i = sub; i < l; i += G) {
             double x = vp[i], y = vq[i];
-            vp[i] = c * x - s * y;
-            vq[i] = s * x + c * y;
+            vp[i] = c * x - sn * y;
+            vq[i] = sn * x + c * y;
           }
-          if (lane == 0) s_rot = 1;
         }
       }
       __syncthreads();
@@ -272,8 +318,10 @@ jacobi_svd_kernel(const double* __restrict__ M, int l, int64_t ldm, double* __re
     const double inv = sc > 0.0 ? 1.0 / sc : 0.0;
     if (lane == 0) sig[rank] = sc;
     for (int i = lane; i < l; i += 32) {
-      Um[i + (int64_t)rank * ldu] = Wm[i + (int64_t)c * l] * inv;
-      Vm[i + (int64_t)rank * ldv] = Wv[i + (int64_t)c * l];
+      const double u = Wm[i + (int64_t)c * l] * inv;
+      Um[i + (int64_t)rank * ldu] = u;
+      if (UsInv) UsInv[i + (int64_t)rank * l] = u * inv;
+      if (want_v) Vm[i + (int64_t)rank * ldv] = Wv[i + (int64_t)c * l];
     }
   }
 }
@@ -346,8 +394,10 @@ cudaError_t launch_chol_inv(const double* G, int64_t ldg, int l, double* R, doub
       attr_set = true;
     }
     chol_inv_kernel<<<1, SMALL_THREADS, smem, st>>>(G, ldg, l, R, Rinv, nullptr, status);
+    note_launch();
   } else {
     chol_inv_kernel<<<1, SMALL_THREADS, 0, st>>>(G, ldg, l, R, Rinv, work, status);
+    note_launch();
   }
   return cudaGetLastError();
 }
@@ -356,13 +406,25 @@ cudaError_t launch_tri_product(const double* R2, const double* R1, int l, double
                                bool transpose_out, cudaStream_t st) {
   int total = l * l;
   tri_product_kernel<<<(total + 255) / 256, 256, 0, st>>>(R2, R1, l, out, transpose_out ? 1 : 0);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_jacobi_svd(const double* M, int l, int64_t ldm, double* sig, double* Um,
-                              int64_t ldu, double* Vm, int64_t ldv, double* work,
+                              int64_t ldu, double* Vm, int64_t ldv, double* UsInv, double* work,
                               DeviceStatus* status, cudaStream_t st) {
-  jacobi_svd_kernel<<<1, SMALL_THREADS, 0, st>>>(M, l, ldm, sig, Um, ldu, Vm, ldv, work, status);
+  const int twoP = (l + 1) & ~1;
+  const size_t need = (size_t)(Vm ? 2 : 1) * l * twoP * sizeof(double);
+  const size_t cap = 200 * 1024;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(jacobi_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
+    attr_set = true;
+  }
+  const bool smem = need <= cap;
+  jacobi_svd_kernel<<<1, SMALL_THREADS, smem ? need : 0, st>>>(M, l, ldm, sig, Um, ldu, Vm, ldv,
+                                                               UsInv, work, smem ? 1 : 0, status);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -370,11 +432,13 @@ cudaError_t launch_finalize_f64(double* U, int64_t m, int64_t ldu, int k, const 
                                 int64_t n, double* VT, int64_t ldvt, const double* sig, double* S,
                                 double* sign_work, cudaStream_t st) {
   sign_kernel<<<k, 1024, 0, st>>>(U, m, ldu, sign_work);
+  note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   int64_t total = n * (int64_t)k;
   int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
   vt_kernel<<<blocks, 256, 0, st>>>(Vk, n, k, sign_work, VT, ldvt, sig, S);
+  note_launch();
   return cudaGetLastError();
 }
 

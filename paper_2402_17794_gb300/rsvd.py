@@ -96,6 +96,14 @@ def rsvd_plan_status(plan) -> int:
     return _lib.load().rsvd_plan_status(plan)
 
 
+def rsvd_plan_diagnostics(plan):
+    """(jacobi_sweeps, dropped_columns) of the work enqueued so far."""
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(_lib.load().rsvd_plan_diagnostics(plan, ctypes.byref(a), ctypes.byref(b)),
+           "rsvd_plan_diagnostics")
+    return a.value, b.value
+
+
 def rsvd_plan_set_stream(plan, stream=None) -> None:
     _check(_lib.load().rsvd_plan_set_stream(plan, _stream_handle(stream)), "rsvd_plan_set_stream")
 
@@ -106,6 +114,10 @@ def rsvd_plan_destroy(plan) -> None:
 
 def rsvd_status_string(code: int) -> str:
     return _lib.load().rsvd_status_string(code).decode()
+
+
+def rsvd_kernel_launches() -> int:
+    return int(_lib.load().rsvd_kernel_launches())
 
 
 def rsvd_solve(plan, A, m, n, lda, k, p, q, seed, U, ldu, S, VT, ldvt) -> int:
