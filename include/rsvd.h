@@ -53,16 +53,19 @@ extern "C" {
 
 typedef struct rsvd_plan_s* rsvd_plan_t;
 
-/* Storage type of A. */
+/* Element types.  A plan's A is RSVD_F64 (plain mode) or RSVD_BF16 (mixed
+ * mode); RSVD_F32 is an output type of rsvd_gaussian and the type of the
+ * mixed mode's FP32 buffers. */
 typedef enum {
   RSVD_F64 = 0,   /* FP64 A; plain mode computes every step in FP64        */
+  RSVD_F32 = 1,
   RSVD_BF16 = 2   /* BF16 A; mixed mode (tensor cores, FP32 accumulation)  */
 } rsvd_dtype_t;
 
 typedef enum {
   RSVD_MODE_PLAIN = 0, /* FP64 arithmetic throughout (A must be RSVD_F64)   */
   RSVD_MODE_MIXED = 1  /* BF16 operands on tcgen05 tensor cores, FP32
-                          accumulation, FP64 for the l x l steps            */
+                          accumulation, FP32 for the other steps            */
 } rsvd_mode_t;
 
 /* Status codes (positive). */
@@ -87,8 +90,8 @@ typedef enum {
  * k + p <= l_max, A stored as a_dtype, computed in `mode`, enqueued on
  * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).
  * Allocates a small pinned host status buffer and nothing on the device.
- * Errors: -1 plan NULL; -2/-3 sizes < 1; -4 l_max < 1 or > RSVD_L_MAX;
- * -5 unknown dtype; -6 unknown mode or mode/dtype mismatch;
+ * Errors: -1 plan NULL; -2/-3 sizes < 1; -4 l_max < 1 or > RSVD_L_MAX (256 in
+ * mixed mode); -5 unknown dtype; -6 unknown mode or mode/dtype mismatch;
  * RSVD_ERR_CUDA if the host allocation fails.
  */
 int rsvd_plan_create(rsvd_plan_t* plan, int64_t m_max, int64_t n_max, int l_max,
@@ -151,6 +154,10 @@ uint64_t rsvd_kernel_launches(void);
  * Argument errors: -1 plan; -2 A NULL; -3 m; -4 n; -5 lda; -6 k; -7 p;
  * -8 q; -10 U NULL; -11 ldu; -12 S NULL; -13 VT NULL; -14 ldvt.
  * m, n above the plan's maxima or k+p above l_max: RSVD_ERR_WORKSPACE.
+ * Mixed mode reads A with TMA: lda must be a multiple of 8 and A 16-byte
+ * aligned, else RSVD_ERR_UNSUPPORTED.  Mixed mode runs q power steps with a
+ * BF16 copy of the operand, then one more power step with the operand split
+ * in two BF16 slices, then B^T = A^T Q with Q split in three BF16 slices.
  */
 int rsvd_solve(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t lda,
                int k, int p, int q, uint64_t seed,
@@ -164,8 +171,8 @@ int rsvd_solve(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t ld
 /*
  * rsvd_gaussian: Algorithm 4 step 1 (Section 3.3; "Gaussian test matrix",
  * Algorithm 1 step 1, Section 2.2).  Writes the n x l matrix Omega for
- * (seed, stream) to `out` (ldo >= n) as FP64 (out_dtype RSVD_F64) or BF16
- * (RSVD_BF16, rounded to nearest even from the FP64 value).
+ * (seed, stream) to `out` (ldo >= n) as FP64 (out_dtype RSVD_F64), FP32
+ * (RSVD_F32) or BF16 (RSVD_BF16), rounded to nearest even from the FP64 value.
  * Errors: -2 n < 1; -3 l < 1; -6 out_dtype; -7 out NULL; -8 ldo < n.
  */
 int rsvd_gaussian(rsvd_plan_t plan, int64_t n, int l, uint64_t seed, uint32_t stream,
@@ -174,7 +181,9 @@ int rsvd_gaussian(rsvd_plan_t plan, int64_t n, int l, uint64_t seed, uint32_t st
 /*
  * rsvd_apply_a: Y = A X  (Algorithm 4 steps 2 and 5, "Form Y = A Omega",
  * "Q = orth(A W)").  A m x n (lda), X n x l (ldx), Y m x l (ldy).
- * Plain: A, X, Y FP64.  Mixed: A BF16, X BF16, Y FP32.
+ * Plain: A, X, Y FP64.  Mixed: A BF16, X BF16, Y FP32; mixed mode also needs
+ * lda and ldx multiples of 8 and A, X 16-byte aligned (TMA), else
+ * RSVD_ERR_UNSUPPORTED.
  * Errors: -2 A; -3 m; -4 n; -5 lda; -6 X; -7 ldx; -8 l; -9 Y; -10 ldy.
  */
 int rsvd_apply_a(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t lda,
@@ -191,27 +200,28 @@ int rsvd_apply_at(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t
 
 /*
  * rsvd_orth: Q = orth(Y) by CholeskyQR2 (Algorithm 4 step 3; the thesis
- * leaves the orthonormalisation method open).  Y rows x l (ldy) FP64 in both
- * modes for this entry point; Q rows x l (ldq) FP64; Y is left unchanged.
- * If R (l x l, ldr, device, FP64) is non-NULL it receives the upper
- * triangular factor with Y = Q R.  Columns of Y that are numerically in the
- * span of earlier columns (Gram pivot <= l * 2^-52 * max diag) come out as
- * zero columns of Q and zero rows of R.
+ * leaves the orthonormalisation method open).  Y rows x l (ldy), Q rows x l
+ * (ldq) and, if non-NULL, R (l x l, ldr) are FP64 in plain mode and FP32 in
+ * mixed mode; Y is left unchanged; R receives the upper triangular factor
+ * with Y = Q R.  Columns of Y that are numerically in the span of earlier
+ * columns (Gram pivot <= l * eps * max diag) come out as zero columns of Q
+ * and zero rows of R.
  * Errors: -2 Y; -3 rows; -4 l; -5 ldy; -6 Q; -7 ldq; -9 ldr.
  */
-int rsvd_orth(rsvd_plan_t plan, const double* Y, int64_t rows, int l, int64_t ldy,
-              double* Q, int64_t ldq, double* R, int64_t ldr);
+int rsvd_orth(rsvd_plan_t plan, const void* Y, int64_t rows, int l, int64_t ldy,
+              void* Q, int64_t ldq, void* R, int64_t ldr);
 
 /*
- * rsvd_small_svd: SVD of an l x l FP64 matrix M (ldm) by one-sided Jacobi
+ * rsvd_small_svd: SVD of an l x l matrix M (ldm) by one-sided Jacobi
  * (Algorithm 4 step 7, applied to the triangular factor of B^T):
  * M = Um diag(sig) Vm^T with sig descending (l values), Um and Vm l x l
  * (ldu, ldv) with orthonormal columns (a column of Um is zero where sig is
- * zero).  All pointers device FP64.  M is left unchanged.
+ * zero).  All pointers device; FP64 in plain mode, FP32 in mixed mode.  M is
+ * left unchanged.
  * Errors: -2 M; -3 l; -4 ldm; -5 sig; -6 Um; -7 ldu; -8 Vm; -9 ldv.
  */
-int rsvd_small_svd(rsvd_plan_t plan, const double* M, int l, int64_t ldm,
-                   double* sig, double* Um, int64_t ldu, double* Vm, int64_t ldv);
+int rsvd_small_svd(rsvd_plan_t plan, const void* M, int l, int64_t ldm,
+                   void* sig, void* Um, int64_t ldu, void* Vm, int64_t ldv);
 
 #ifdef __cplusplus
 }

@@ -1,6 +1,7 @@
-// FP64 tall-skinny products of the plain path: the passes over A of
-// Algorithm 4 (steps 2, 5 and 6, Section 3.3) and the O(m l^2) products of
-// CholeskyQR2 (Gram Y^T Y, Y R^-1) and of the lift U = Q U~ (step 8).
+// Tall-skinny products on the CUDA cores, FP64 or FP32: the passes over A
+// of the plain path (Algorithm 4, steps 2, 5 and 6, Section 3.3) and the
+// O(m l^2) products of CholeskyQR2 (Gram Y^T Y, Y R^-1) and of the lift
+// U = Q U~ (step 8) in both paths.
 //
 // On GB300 FP64 runs at 2 DFMA per clock per SM (about 1.2 TFLOP/s for the
 // GPU) while HBM streams ~6.8 TB/s, so an FP64 pass over A at l = 80
@@ -24,15 +25,15 @@ constexpr int BK = 16;
 constexpr int THREADS = 256;
 constexpr int AS_LD = BM + 1;  // padded row (doubles)
 
-template <int TN, bool TRANS>
+template <typename T, int TN, bool TRANS>
 __global__ void __launch_bounds__(THREADS)
-gemm_f64_kernel(const double* __restrict__ A, int64_t lda, const double* __restrict__ X,
-                int64_t ldx, double* __restrict__ C, int64_t ldc, int64_t M, int64_t K, int N,
+gemm_simt_kernel(const T* __restrict__ A, int64_t lda, const T* __restrict__ X,
+                 int64_t ldx, T* __restrict__ C, int64_t ldc, int64_t M, int64_t K, int N,
                 int64_t k_per_split, int64_t part_stride) {
   constexpr int BN = 16 * TN;
   constexpr int XS_LD = BN + 1;
-  __shared__ double As[2][BK * AS_LD];
-  __shared__ double Xs[2][BK * XS_LD];
+  __shared__ T As[2][BK * AS_LD];
+  __shared__ T Xs[2][BK * XS_LD];
 
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
@@ -40,11 +41,11 @@ gemm_f64_kernel(const double* __restrict__ A, int64_t lda, const double* __restr
   const int c0 = blockIdx.y * BN;
   const int64_t kb = (int64_t)blockIdx.z * k_per_split;
   const int64_t ke = (kb + k_per_split < K) ? kb + k_per_split : K;
-  double* Cout = C + (int64_t)blockIdx.z * part_stride;
+  T* Cout = C + (int64_t)blockIdx.z * part_stride;
 
   constexpr int A_PER = BM * BK / THREADS;             // 4
   constexpr int X_PER = (BN * BK + THREADS - 1) / THREADS;
-  double ra[A_PER], rx[X_PER];
+  T ra[A_PER], rx[X_PER];
 
   auto load_tiles = [&](int64_t k0) {
 #pragma unroll
@@ -54,7 +55,7 @@ gemm_f64_kernel(const double* __restrict__ A, int64_t lda, const double* __restr
       if (!TRANS) { r = idx % BM; kk = idx / BM; }
       else { kk = idx % BK; r = idx / BK; }
       int64_t gr = r0 + r, gk = k0 + kk;
-      double v = 0.0;
+      T v = T(0);
       if (gr < M && gk < ke) v = TRANS ? A[gk + gr * lda] : A[gr + gk * lda];
       ra[e] = v;
     }
@@ -63,7 +64,7 @@ gemm_f64_kernel(const double* __restrict__ A, int64_t lda, const double* __restr
       int idx = tid + e * THREADS;
       int kk = idx % BK, c = idx / BK;
       int64_t gk = k0 + kk;
-      double v = 0.0;
+      T v = T(0);
       if (idx < BN * BK && c0 + c < N && gk < ke) v = X[gk + (int64_t)(c0 + c) * ldx];
       rx[e] = v;
     }
@@ -87,11 +88,11 @@ gemm_f64_kernel(const double* __restrict__ A, int64_t lda, const double* __restr
     }
   };
 
-  double acc[4][TN];
+  T acc[4][TN];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
 
   int buf = 0;
   if (kb < ke) {
@@ -102,11 +103,11 @@ gemm_f64_kernel(const double* __restrict__ A, int64_t lda, const double* __restr
   for (int64_t k0 = kb; k0 < ke; k0 += BK) {
     const bool more = k0 + BK < ke;
     if (more) load_tiles(k0 + BK);
-    const double* as = As[buf];
-    const double* xs = Xs[buf];
+    const T* as = As[buf];
+    const T* xs = Xs[buf];
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      double a[4], x[TN];
+      T a[4], x[TN];
 #pragma unroll
       for (int i = 0; i < 4; ++i) a[i] = as[kk * AS_LD + tx + 16 * i];
 #pragma unroll
@@ -133,35 +134,37 @@ gemm_f64_kernel(const double* __restrict__ A, int64_t lda, const double* __restr
   }
 }
 
-__global__ void splitk_reduce_kernel(const double* __restrict__ part, int splits,
-                                     int64_t part_stride, int64_t M, int N, double* __restrict__ C,
+template <typename T>
+__global__ void splitk_reduce_kernel(const T* __restrict__ part, int splits,
+                                     int64_t part_stride, int64_t M, int N, T* __restrict__ C,
                                      int64_t ldc) {
   const int64_t total = M * (int64_t)N;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     int64_t c = t / M, r = t - c * M;
-    double s = 0.0;
+    T s = T(0);
     for (int z = 0; z < splits; ++z) s += part[z * part_stride + t];
     C[r + c * ldc] = s;
   }
 }
 
-template <int TN>
-void launch_tn(const GemmF64& g, dim3 grid, double* out, int64_t ldo, int64_t kps,
+template <typename T, int TN>
+void launch_tn(const GemmArgs<T>& g, dim3 grid, T* out, int64_t ldo, int64_t kps,
                int64_t pstride, cudaStream_t st) {
   if (g.trans)
-    gemm_f64_kernel<TN, true><<<grid, THREADS, 0, st>>>(g.A, g.lda, g.X, g.ldx, out, ldo, g.M, g.K,
-                                                        g.N, kps, pstride);
+    gemm_simt_kernel<T, TN, true><<<grid, THREADS, 0, st>>>(g.A, g.lda, g.X, g.ldx, out, ldo, g.M,
+                                                            g.K, g.N, kps, pstride);
   else
-    gemm_f64_kernel<TN, false><<<grid, THREADS, 0, st>>>(g.A, g.lda, g.X, g.ldx, out, ldo, g.M,
-                                                         g.K, g.N, kps, pstride);
+    gemm_simt_kernel<T, TN, false><<<grid, THREADS, 0, st>>>(g.A, g.lda, g.X, g.ldx, out, ldo,
+                                                             g.M, g.K, g.N, kps, pstride);
   note_launch();
 }
 
 }  // namespace
 
-cudaError_t launch_gemm_f64(const GemmF64& g, double* part, size_t part_elems, int num_sms,
-                            cudaStream_t st) {
+template <typename T>
+cudaError_t launch_gemm(const GemmArgs<T>& g, T* part, size_t part_elems, int num_sms,
+                        cudaStream_t st) {
   if (g.M <= 0 || g.N <= 0) return cudaSuccess;
   // Column tiles of at most 96 columns, each a multiple of 16 wide.
   int col_tiles = (g.N + 95) / 96;
@@ -186,24 +189,28 @@ cudaError_t launch_gemm_f64(const GemmF64& g, double* part, size_t part_elems, i
   splits = (g.K + kps - 1) / kps;
   if (splits < 1) splits = 1;
   dim3 grid((unsigned)row_tiles, (unsigned)col_tiles, (unsigned)splits);
-  double* out = splits > 1 ? part : g.C;
+  T* out = splits > 1 ? part : g.C;
   int64_t ldo = splits > 1 ? g.M : g.ldc;
   switch (tn) {
-    case 1: launch_tn<1>(g, grid, out, ldo, kps, pstride, st); break;
-    case 2: launch_tn<2>(g, grid, out, ldo, kps, pstride, st); break;
-    case 3: launch_tn<3>(g, grid, out, ldo, kps, pstride, st); break;
-    case 4: launch_tn<4>(g, grid, out, ldo, kps, pstride, st); break;
-    case 5: launch_tn<5>(g, grid, out, ldo, kps, pstride, st); break;
-    case 6: launch_tn<6>(g, grid, out, ldo, kps, pstride, st); break;
+    case 1: launch_tn<T, 1>(g, grid, out, ldo, kps, pstride, st); break;
+    case 2: launch_tn<T, 2>(g, grid, out, ldo, kps, pstride, st); break;
+    case 3: launch_tn<T, 3>(g, grid, out, ldo, kps, pstride, st); break;
+    case 4: launch_tn<T, 4>(g, grid, out, ldo, kps, pstride, st); break;
+    case 5: launch_tn<T, 5>(g, grid, out, ldo, kps, pstride, st); break;
+    case 6: launch_tn<T, 6>(g, grid, out, ldo, kps, pstride, st); break;
     default: return cudaErrorInvalidValue;
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || splits == 1) return e;
   int64_t total = pstride;
   int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)num_sms * 8);
-  splitk_reduce_kernel<<<blocks, 256, 0, st>>>(part, (int)splits, pstride, g.M, g.N, g.C, g.ldc);
+  splitk_reduce_kernel<T><<<blocks, 256, 0, st>>>(part, (int)splits, pstride, g.M, g.N, g.C, g.ldc);
   note_launch();
   return cudaGetLastError();
 }
+
+template cudaError_t launch_gemm<double>(const GemmArgs<double>&, double*, size_t, int,
+                                         cudaStream_t);
+template cudaError_t launch_gemm<float>(const GemmArgs<float>&, float*, size_t, int, cudaStream_t);
 
 }  // namespace rsvd

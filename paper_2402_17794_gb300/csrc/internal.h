@@ -36,8 +36,8 @@ inline int status_from_flags(int flags) {
 // Workspace carve-up (offsets in bytes from the workspace base).
 struct Layout {
   size_t status, om, y, qm, tmp, z, qb, part, small, total;
-  // mixed-mode extras
-  size_t om16, q16, y32, z32, vk;
+  // mixed-mode extras: BF16 operand slices (om16), tcgen05 partial slots (y32)
+  size_t om16, y32;
   size_t small_stride;  // bytes of one l x l FP64 matrix (padded)
 };
 
@@ -59,46 +59,51 @@ namespace rsvd {
 
 // ---- kernels' host launchers (all enqueue on `st`) ----
 
-// Omega (n x l) for (seed, stream): FP64 or BF16 output.
+// Omega (n x l) for (seed, stream): FP64, FP32 or BF16 output.
+constexpr int kOutF32 = RSVD_F32;
 cudaError_t launch_gaussian(int64_t n, int l, uint64_t seed, uint32_t stream_id,
                             int out_dtype, void* out, int64_t ldo, cudaStream_t st);
 
-// FP64 tall-skinny GEMM:  C (M x N) = op(A) X,  op(A) = A (M x K, lda) or
-// A^T (A stored K x M, lda).  X is K x N (ldx).  Split-K partials go to
-// `part` (kMaxSplits * M * N doubles) when more than one split is used.
-struct GemmF64 {
-  const double* A; int64_t lda; bool trans;
-  const double* X; int64_t ldx;
-  double* C; int64_t ldc;
+// Tall-skinny GEMM on the CUDA cores:  C (M x N) = op(A) X,  op(A) = A (M x K,
+// lda) or A^T (A stored K x M, lda).  X is K x N (ldx).  Split-K partials go
+// to `part` (up to part_elems elements) when more than one split is used.
+template <typename T>
+struct GemmArgs {
+  const T* A; int64_t lda; bool trans;
+  const T* X; int64_t ldx;
+  T* C; int64_t ldc;
   int64_t M, K; int N;
 };
-cudaError_t launch_gemm_f64(const GemmF64& g, double* part, size_t part_elems,
-                            int num_sms, cudaStream_t st);
+template <typename T>
+cudaError_t launch_gemm(const GemmArgs<T>& g, T* part, size_t part_elems, int num_sms,
+                        cudaStream_t st);
 
 // One-CTA Cholesky of the l x l Gram G (ldg) -> upper R (l x l, ld l) and
 // its inverse Rinv (ld l); deficient pivots zero the row of R and the row and
-// column of Rinv.  Sets status bits on breakdown / non-finite input.
-cudaError_t launch_chol_inv(const double* G, int64_t ldg, int l, double* R, double* Rinv,
-                            double* work, DeviceStatus* status, cudaStream_t st);
+// column of Rinv.  Sets status bits on non-finite input.  work: l*l elements.
+template <typename T>
+cudaError_t launch_chol_inv(const T* G, int64_t ldg, int l, T* R, T* Rinv, T* work,
+                            DeviceStatus* status, cudaStream_t st);
 
 // out (l x l, ld l) = R2 * R1 for upper triangular R1, R2 (ld l); if
 // transpose_out, out = (R2 R1)^T.
-cudaError_t launch_tri_product(const double* R2, const double* R1, int l, double* out,
-                               bool transpose_out, cudaStream_t st);
+template <typename T>
+cudaError_t launch_tri_product(const T* R2, const T* R1, int l, T* out, bool transpose_out,
+                               cudaStream_t st);
 
 // One-CTA one-sided Jacobi SVD of the l x l matrix M (ldm): M = Um diag(sig) Vm^T.
 // Vm may be NULL (rotations not accumulated); UsInv (ld l), if non-NULL,
-// receives Um diag(1/sig).  work holds 2 * l_even * l doubles.
-cudaError_t launch_jacobi_svd(const double* M, int l, int64_t ldm, double* sig,
-                              double* Um, int64_t ldu, double* Vm, int64_t ldv, double* UsInv,
-                              double* work, DeviceStatus* status, cudaStream_t st);
+// receives Um diag(1/sig).  work holds 2 * l_even * l elements.
+template <typename T>
+cudaError_t launch_jacobi_svd(const T* M, int l, int64_t ldm, T* sig, T* Um, int64_t ldu, T* Vm,
+                              int64_t ldv, T* UsInv, T* work, DeviceStatus* status,
+                              cudaStream_t st);
 
-// Sign convention + outputs of the lift: flips columns of U (m x k, ldu, FP64)
-// so each column's largest-|.| entry is positive, writes S[i] = sig[i] and
+// Sign convention + outputs of the lift: flips columns of U (m x k, ldu) so
+// each column's largest-|.| entry is positive, writes S[i] = sig[i] and
 // VT (k x n, ldvt) = diag(sign) Vk^T with Vk n x k (ld n).
-cudaError_t launch_finalize_f64(double* U, int64_t m, int64_t ldu, int k,
-                                const double* Vk, int64_t n, double* VT, int64_t ldvt,
-                                const double* sig, double* S, double* sign_work,
-                                cudaStream_t st);
+template <typename T>
+cudaError_t launch_finalize(T* U, int64_t m, int64_t ldu, int k, const T* Vk, int64_t n, T* VT,
+                            int64_t ldvt, const T* sig, double* S, T* sign_work, cudaStream_t st);
 
 }  // namespace rsvd

@@ -53,6 +53,8 @@ __device__ __forceinline__ T to_out(double z);
 template <>
 __device__ __forceinline__ double to_out<double>(double z) { return z; }
 template <>
+__device__ __forceinline__ float to_out<float>(double z) { return (float)z; }
+template <>
 __device__ __forceinline__ __nv_bfloat16 to_out<__nv_bfloat16>(double z) {
   return __double2bfloat16(z);
 }
@@ -79,6 +81,9 @@ cudaError_t launch_gaussian(int64_t n, int l, uint64_t seed, uint32_t stream_id,
   uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   if (out_dtype == RSVD_F64) {
     gaussian_kernel<double><<<blocks, threads, 0, st>>>(n, l, k0, k1, stream_id, (double*)out, ldo);
+    note_launch();
+  } else if (out_dtype == RSVD_F32) {
+    gaussian_kernel<float><<<blocks, threads, 0, st>>>(n, l, k0, k1, stream_id, (float*)out, ldo);
     note_launch();
   } else if (out_dtype == RSVD_BF16) {
     gaussian_kernel<__nv_bfloat16><<<blocks, threads, 0, st>>>(n, l, k0, k1, stream_id,

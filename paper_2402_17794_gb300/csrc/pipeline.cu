@@ -1,0 +1,307 @@
+// Host-side orchestration of Algorithm 4 (Section 3.3) for both paths.
+//
+// Plain path (FP64 A):   every step in FP64; passes over A on the CUDA cores.
+// Mixed path (BF16 A):   passes over A on the tcgen05 tensor cores with BF16
+//                        operands and FP32 accumulation; everything else in
+//                        FP32.  The q power steps use a single BF16 copy of
+//                        the operand; one extra power step follows with the
+//                        operand split in two BF16 slices (bf16x2, ~16 bits),
+//                        and the final B^T = A^T Q uses three slices
+//                        (bf16x3, ~24 bits, i.e. FP32-accurate since A is
+//                        exact in BF16).
+//
+// Steps shared by both paths (templated on the element type):
+//   orth       CholeskyQR2 (Gram on the CUDA cores, one-CTA Cholesky + inverse)
+//   finish     B^T = Q_B R_B (R only), one-sided Jacobi of R_B^T, U = Q U~,
+//              V = B^T U~ Sigma^-1 re-orthonormalised, signs and output layout.
+#include <algorithm>
+
+#include "pipeline.h"
+#include "umma.h"
+
+namespace rsvd {
+
+namespace {
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
+
+__global__ void split_bf16_kernel(const float* __restrict__ X, int64_t rows, int l, int64_t ldx,
+                                  int slices, int stride, __nv_bfloat16* __restrict__ out,
+                                  int64_t ldo) {
+  const int64_t total = rows * (int64_t)slices * stride;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cc = t / rows, r = t - cc * rows;
+    const int s = (int)(cc / stride), c = (int)(cc % stride);
+    float v = (c < l) ? X[r + (int64_t)c * ldx] : 0.f;
+    __nv_bfloat16 h = __float2bfloat16_rn(v);
+    for (int j = 0; j < s; ++j) {  // peel the leading slices off
+      v -= __bfloat162float(h);
+      h = __float2bfloat16_rn(v);
+    }
+    out[r + cc * ldo] = h;
+  }
+}
+
+int split_operand(rsvd_plan_t P, const float* X, int64_t rows, int l, int64_t ldx, int slices,
+                  int stride, __nv_bfloat16* out, int64_t ldo) {
+  const int64_t total = rows * (int64_t)slices * stride;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)P->num_sms * 8);
+  split_bf16_kernel<<<blocks, 256, 0, P->stream>>>(X, rows, l, ldx, slices, stride, out, ldo);
+  note_launch();
+  RSVD_CK(cudaGetLastError());
+  return RSVD_OK;
+}
+
+// One tcgen05 pass: out = A X (ax) or A^T X with X = `slices`-way BF16 split of
+// the FP32 operand (rows x l, ld rows).
+int mixed_pass(rsvd_plan_t P, bool ax, const void* A, int64_t m, int64_t n, int64_t lda,
+               const float* X, int l, int slices, float* out, int64_t ldo) {
+  MixedWork MW = mixed_work_of(P);
+  const int64_t rows = ax ? n : m;
+  const int64_t ldx = round8(rows);
+  const int l16 = (l + 15) / 16 * 16;
+  if ((size_t)ldx * slices * l16 > MW.xcat_elems) return RSVD_ERR_WORKSPACE;
+  int rc = split_operand(P, X, rows, l, rows, slices, l16, MW.xcat, ldx);
+  if (rc) return rc;
+  ApassCall c;
+  c.ax = ax;
+  c.A = A;
+  c.m = m;
+  c.n = n;
+  c.lda = lda;
+  c.X = MW.xcat;
+  c.ldx = ldx;
+  c.x_cols = slices * l16;
+  c.l = l;
+  c.slices = slices;
+  c.slice_stride = l16;
+  c.out = out;
+  c.ldo = ldo;
+  c.part = MW.apart;
+  c.part_floats = MW.apart_floats;
+  return launch_apass_bf16(c, P->num_sms, &dstatus(P)->flags, P->stream);
+}
+
+template <typename T>
+int finish(rsvd_plan_t P, const Work<T>& W, int64_t m, int64_t n, int l, int k, T* U, int64_t ldu,
+           double* S, T* VT, int64_t ldvt) {
+  int rc;
+  // B^T (in W.z) = Q_B R_B: only R_B is formed; Mt = R_B^T
+  if ((rc = orth<T>(P, W.z, n, l, n, nullptr, n, W.Mt, true))) return rc;
+  // one-sided Jacobi on R_B^T = U~ Sigma V_R^T; U~ are B's left singular vectors
+  T* us_inv = W.Vm;
+  RSVD_CK(launch_jacobi_svd<T>(W.Mt, l, l, W.sig, W.Um, l, nullptr, l, us_inv, W.jw, dstatus(P),
+                               P->stream));
+  // step 8: U = Q U~ (first k columns)
+  if ((rc = gemm<T>(P, W.qm, m, false, W.Um, l, U, ldu, m, l, k))) return rc;
+  // V_k = B^T U~_k Sigma_k^-1, then one CholeskyQR pass restores orthonormality
+  // to rounding (the product carries relative errors ~ eps sigma_1/sigma_i)
+  if ((rc = gemm<T>(P, W.z, n, false, us_inv, l, W.tmp, n, n, l, k))) return rc;
+  if ((rc = gemm<T>(P, W.tmp, n, true, W.tmp, n, W.G, k, k, n, k))) return rc;
+  RSVD_CK(launch_chol_inv<T>(W.G, k, k, W.R1, W.R1i, W.cholw, dstatus(P), P->stream));
+  if ((rc = gemm<T>(P, W.tmp, n, false, W.R1i, k, W.qb, n, n, k, k))) return rc;
+  RSVD_CK(launch_finalize<T>(U, m, ldu, k, W.qb, n, VT, ldvt, W.sig, S, W.sign, P->stream));
+  return RSVD_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Workspace
+// ---------------------------------------------------------------------------
+
+Layout make_layout(int64_t m, int64_t n, int l, int mode, int num_sms) {
+  Layout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += align_up(bytes);
+    return o;
+  };
+  const size_t e = mode == RSVD_MODE_PLAIN ? sizeof(double) : sizeof(float);
+  const int64_t mn = m > n ? m : n;
+  const int lpad = (l + 1) & ~1;
+  L.status = take(sizeof(DeviceStatus));
+  L.om = take((size_t)n * l * e);
+  L.y = take((size_t)m * l * e);
+  L.qm = take((size_t)m * l * e);
+  L.tmp = take((size_t)mn * l * e);
+  L.z = take((size_t)n * l * e);
+  L.qb = take((size_t)n * l * e);
+  L.part = take((size_t)kPartSplits * mn * l * e);
+  L.small_stride = align_up((size_t)l * l * e);
+  // G, R1, R1inv, R2, R2inv, Mt, Um, Vm, chol work, jacobi work (2 l x lpad), sig, sign
+  L.small = take(L.small_stride * 9 + align_up(2 * (size_t)l * lpad * e) + align_up(2 * (size_t)l * e));
+  if (mode == RSVD_MODE_MIXED) {
+    const int l16 = (l + 15) / 16 * 16;
+    L.om16 = take((size_t)round8(mn) * 3 * l16 * sizeof(__nv_bfloat16));
+    L.y32 = take(apass_partial_floats(num_sms, l) * sizeof(float));
+  }
+  L.total = off;
+  return L;
+}
+
+template <typename T>
+Work<T> work_of(rsvd_plan_t P) {
+  Work<T> W;
+  char* b = P->ws;
+  const Layout& L = P->lay;
+  W.om = (T*)(b + L.om);
+  W.y = (T*)(b + L.y);
+  W.qm = (T*)(b + L.qm);
+  W.tmp = (T*)(b + L.tmp);
+  W.z = (T*)(b + L.z);
+  W.qb = (T*)(b + L.qb);
+  W.part = (T*)(b + L.part);
+  const int64_t mn = P->m_max > P->n_max ? P->m_max : P->n_max;
+  W.part_elems = (size_t)kPartSplits * mn * P->l_max;
+  char* s = b + L.small;
+  const size_t st = L.small_stride;
+  W.G = (T*)(s + 0 * st);
+  W.R1 = (T*)(s + 1 * st);
+  W.R1i = (T*)(s + 2 * st);
+  W.R2 = (T*)(s + 3 * st);
+  W.R2i = (T*)(s + 4 * st);
+  W.Mt = (T*)(s + 5 * st);
+  W.Um = (T*)(s + 6 * st);
+  W.Vm = (T*)(s + 7 * st);
+  W.cholw = (T*)(s + 8 * st);
+  W.jw = (T*)(s + 9 * st);
+  const int l = P->l_max, lpad = (l + 1) & ~1;
+  W.sig = (T*)(s + 9 * st + align_up(2 * (size_t)l * lpad * sizeof(T)));
+  W.sign = W.sig + l;
+  return W;
+}
+template Work<double> work_of<double>(rsvd_plan_t);
+template Work<float> work_of<float>(rsvd_plan_t);
+
+MixedWork mixed_work_of(rsvd_plan_t P) {
+  MixedWork M;
+  const int64_t mn = P->m_max > P->n_max ? P->m_max : P->n_max;
+  const int l16 = (P->l_max + 15) / 16 * 16;
+  M.xcat = (__nv_bfloat16*)(P->ws + P->lay.om16);
+  M.xcat_elems = (size_t)round8(mn) * 3 * l16;
+  M.apart = (float*)(P->ws + P->lay.y32);
+  M.apart_floats = apass_partial_floats(P->num_sms, P->l_max);
+  return M;
+}
+
+DeviceStatus* dstatus(rsvd_plan_t P) { return (DeviceStatus*)(P->ws + P->lay.status); }
+
+bool plan_ready(rsvd_plan_t P) { return P && P->ws && P->ws_bytes >= P->lay.total; }
+
+// ---------------------------------------------------------------------------
+// Shared steps
+// ---------------------------------------------------------------------------
+
+template <typename T>
+int gemm(rsvd_plan_t P, const T* A, int64_t lda, bool trans, const T* X, int64_t ldx, T* C,
+         int64_t ldc, int64_t M, int64_t K, int N) {
+  GemmArgs<T> g{A, lda, trans, X, ldx, C, ldc, M, K, N};
+  Work<T> W = work_of<T>(P);
+  RSVD_CK(launch_gemm<T>(g, W.part, W.part_elems, P->num_sms, P->stream));
+  return RSVD_OK;
+}
+template int gemm<double>(rsvd_plan_t, const double*, int64_t, bool, const double*, int64_t,
+                          double*, int64_t, int64_t, int64_t, int);
+template int gemm<float>(rsvd_plan_t, const float*, int64_t, bool, const float*, int64_t, float*,
+                         int64_t, int64_t, int64_t, int);
+
+template <typename T>
+int orth(rsvd_plan_t P, const T* Y, int64_t rows, int l, int64_t ldy, T* Q, int64_t ldq, T* Rprod,
+         bool transpose_R) {
+  Work<T> W = work_of<T>(P);
+  DeviceStatus* st = dstatus(P);
+  int rc;
+  // pass 1: G = Y^T Y = R1^T R1, T1 = Y R1^-1
+  if ((rc = gemm<T>(P, Y, ldy, true, Y, ldy, W.G, l, l, rows, l))) return rc;
+  RSVD_CK(launch_chol_inv<T>(W.G, l, l, W.R1, W.R1i, W.cholw, st, P->stream));
+  if ((rc = gemm<T>(P, Y, ldy, false, W.R1i, l, W.tmp, rows, rows, l, l))) return rc;
+  // pass 2: G = T1^T T1 = R2^T R2, Q = T1 R2^-1
+  if ((rc = gemm<T>(P, W.tmp, rows, true, W.tmp, rows, W.G, l, l, rows, l))) return rc;
+  RSVD_CK(launch_chol_inv<T>(W.G, l, l, W.R2, W.R2i, W.cholw, st, P->stream));
+  if (Q && (rc = gemm<T>(P, W.tmp, rows, false, W.R2i, l, Q, ldq, rows, l, l))) return rc;
+  if (Rprod) RSVD_CK(launch_tri_product<T>(W.R2, W.R1, l, Rprod, transpose_R, P->stream));
+  return RSVD_OK;
+}
+template int orth<double>(rsvd_plan_t, const double*, int64_t, int, int64_t, double*, int64_t,
+                          double*, bool);
+template int orth<float>(rsvd_plan_t, const float*, int64_t, int, int64_t, float*, int64_t, float*,
+                         bool);
+
+// ---------------------------------------------------------------------------
+// Full solves
+// ---------------------------------------------------------------------------
+
+int solve_plain(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t lda, int k, int p,
+                int q, uint64_t seed, double* U, int64_t ldu, double* S, double* VT,
+                int64_t ldvt) {
+  const int l = k + p;
+  Work<double> W = work_of<double>(P);
+  int rc;
+  // 1. Omega;  2. Y = A Omega;  3. Q = orth(Y)
+  RSVD_CK(launch_gaussian(n, l, seed, 0u, RSVD_F64, W.om, n, P->stream));
+  if ((rc = gemm<double>(P, A, lda, false, W.om, n, W.y, m, m, n, l))) return rc;
+  if ((rc = orth<double>(P, W.y, m, l, m, W.qm, m, nullptr, false))) return rc;
+  // 4-5. power steps with orthonormalisation: W = orth(A^T Q), Q = orth(A W)
+  for (int j = 0; j < q; ++j) {
+    if ((rc = gemm<double>(P, A, lda, true, W.qm, m, W.z, n, n, m, l))) return rc;
+    if ((rc = orth<double>(P, W.z, n, l, n, W.om, n, nullptr, false))) return rc;
+    if ((rc = gemm<double>(P, A, lda, false, W.om, n, W.y, m, m, n, l))) return rc;
+    if ((rc = orth<double>(P, W.y, m, l, m, W.qm, m, nullptr, false))) return rc;
+  }
+  // 6. B^T = A^T Q;  7-8. small SVD and lift
+  if ((rc = gemm<double>(P, A, lda, true, W.qm, m, W.z, n, n, m, l))) return rc;
+  return finish<double>(P, W, m, n, l, k, U, ldu, S, VT, ldvt);
+}
+
+int solve_mixed(rsvd_plan_t P, const void* A, int64_t m, int64_t n, int64_t lda, int k, int p,
+                int q, uint64_t seed, float* U, int64_t ldu, double* S, float* VT,
+                int64_t ldvt) {
+  const int l = k + p;
+  Work<float> W = work_of<float>(P);
+  int rc;
+  // 1. Omega (FP32, rounded to BF16 for the pass);  2. Y = A Omega;  3. Q = orth(Y)
+  RSVD_CK(launch_gaussian(n, l, seed, 0u, kOutF32, W.om, n, P->stream));
+  if ((rc = mixed_pass(P, true, A, m, n, lda, W.om, l, 1, W.y, m))) return rc;
+  if ((rc = orth<float>(P, W.y, m, l, m, W.qm, m, nullptr, false))) return rc;
+  // 4-5. q power steps on a BF16 operand, then one refinement step on bf16x2
+  for (int j = 0; j <= q; ++j) {
+    const int slices = (j == q) ? 2 : 1;
+    if ((rc = mixed_pass(P, false, A, m, n, lda, W.qm, l, slices, W.z, n))) return rc;
+    if ((rc = orth<float>(P, W.z, n, l, n, W.om, n, nullptr, false))) return rc;
+    if ((rc = mixed_pass(P, true, A, m, n, lda, W.om, l, slices, W.y, m))) return rc;
+    if ((rc = orth<float>(P, W.y, m, l, m, W.qm, m, nullptr, false))) return rc;
+  }
+  // 6. B^T = A^T Q with Q split in three BF16 slices;  7-8. small SVD and lift
+  if ((rc = mixed_pass(P, false, A, m, n, lda, W.qm, l, 3, W.z, n))) return rc;
+  return finish<float>(P, W, m, n, l, k, U, ldu, S, VT, ldvt);
+}
+
+int mixed_apply(rsvd_plan_t P, const void* A, int64_t m, int64_t n, int64_t lda, const void* X,
+                int64_t ldx, int l, float* out, int64_t ldo, bool trans) {
+  MixedWork MW = mixed_work_of(P);
+  const int l16 = (l + 15) / 16 * 16;
+  ApassCall c;
+  c.ax = !trans;
+  c.A = A;
+  c.m = m;
+  c.n = n;
+  c.lda = lda;
+  c.X = X;
+  c.ldx = ldx;
+  c.x_cols = l;
+  c.l = l;
+  c.slices = 1;
+  c.slice_stride = l16;
+  c.out = out;
+  c.ldo = ldo;
+  c.part = MW.apart;
+  c.part_floats = MW.apart_floats;
+  return launch_apass_bf16(c, P->num_sms, &dstatus(P)->flags, P->stream);
+}
+
+}  // namespace rsvd

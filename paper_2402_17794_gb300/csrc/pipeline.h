@@ -1,0 +1,66 @@
+// Host-side orchestration of Algorithm 4 (Section 3.3): workspace views and
+// the steps shared by the plain (FP64) and mixed (BF16 A, FP32 elsewhere)
+// paths.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "internal.h"
+
+namespace rsvd {
+
+#define RSVD_CK(expr)                               \
+  do {                                              \
+    cudaError_t _e = (expr);                        \
+    if (_e != cudaSuccess) return RSVD_ERR_CUDA;    \
+  } while (0)
+
+constexpr int kPartSplits = 16;  // SIMT split-K partial slices held in workspace
+
+// Views of the workspace for the element type T of the path (double for the
+// plain path, float for the mixed path).
+template <typename T>
+struct Work {
+  T *om, *y, *qm, *tmp, *z, *qb;  // n x l, m x l, m x l, max(m,n) x l, n x l, n x l
+  T* part;                        // SIMT split-K partials
+  size_t part_elems;
+  T *G, *R1, *R1i, *R2, *R2i, *Mt, *Um, *Vm, *cholw, *jw, *sig, *sign;
+};
+
+// Mixed-path extras: the BF16 operand (up to three slices side by side) and
+// the partial slots of the tcgen05 passes.
+struct MixedWork {
+  __nv_bfloat16* xcat;
+  size_t xcat_elems;
+  float* apart;
+  size_t apart_floats;
+};
+
+Layout make_layout(int64_t m, int64_t n, int l, int mode, int num_sms);
+template <typename T>
+Work<T> work_of(rsvd_plan_t P);
+MixedWork mixed_work_of(rsvd_plan_t P);
+DeviceStatus* dstatus(rsvd_plan_t P);
+bool plan_ready(rsvd_plan_t P);
+
+template <typename T>
+int gemm(rsvd_plan_t P, const T* A, int64_t lda, bool trans, const T* X, int64_t ldx, T* C,
+         int64_t ldc, int64_t M, int64_t K, int N);
+
+// CholeskyQR2: Q = orth(Y) (Q may be NULL: only R is formed); Rprod, if
+// non-NULL, receives R2 R1 (or its transpose), the R factor of Y = Q R.
+template <typename T>
+int orth(rsvd_plan_t P, const T* Y, int64_t rows, int l, int64_t ldy, T* Q, int64_t ldq,
+         T* Rprod, bool transpose_R);
+
+int solve_plain(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t lda, int k, int p,
+                int q, uint64_t seed, double* U, int64_t ldu, double* S, double* VT,
+                int64_t ldvt);
+int solve_mixed(rsvd_plan_t P, const void* A, int64_t m, int64_t n, int64_t lda, int k, int p,
+                int q, uint64_t seed, float* U, int64_t ldu, double* S, float* VT, int64_t ldvt);
+
+// Step entry: one tcgen05 pass with a BF16 operand X (ldx) of `l` columns.
+int mixed_apply(rsvd_plan_t P, const void* A, int64_t m, int64_t n, int64_t lda, const void* X,
+                int64_t ldx, int l, float* out, int64_t ldo, bool trans);
+
+}  // namespace rsvd

@@ -1,9 +1,10 @@
-// The l x l FP64 steps of the path (l = k + p <= 288):
+// The l x l steps of the path (l = k + p <= 288), in FP64 (plain path) or
+// FP32 (mixed path):
 //
 //  * chol_inv: Cholesky factor R of the Gram matrix G = Y^T Y and its inverse,
 //    the middle of CholeskyQR (Q = Y R^-1), used for every orth() of
 //    Algorithm 4 (steps 3 and 5, Section 3.3).  Columns whose Gram pivot falls
-//    below l * 2^-52 * max(diag G) are numerically in the span of the earlier
+//    below l * eps * max(diag G) are numerically in the span of the earlier
 //    ones; they are dropped (zero row of R, zero row and column of R^-1), so
 //    the matching column of Q is exactly zero and contributes nothing to
 //    B = Q^T A.  This keeps exactly rank-deficient samples (rank(A) < k + p)
@@ -15,7 +16,7 @@
 //    ordering, one warp per column pair, Rutishauser's rotation formulas.
 //  * finalize: the sign convention and the output layout of step 8.
 //
-// Each runs as one CTA: the whole problem is O(l^3) FP64 work, which fits in
+// Each runs as one CTA: the whole problem is O(l^3) work, which fits in
 // one SM's L1/shared memory and needs a block-wide barrier per elimination
 // step or Jacobi round.
 #include <cfloat>
@@ -29,19 +30,39 @@ namespace {
 
 constexpr int SMALL_THREADS = 1024;
 
+template <typename T>
+struct Eps;
+// drop_factor: a Gram pivot below drop_factor * eps * max(diag G) marks a
+// dependent column.  FP64 uses l (exactly dependent columns leave pivots of a
+// few ulps times l); FP32 uses 1 -- its Gram already blurs pivots near
+// sqrt(eps) relative, and dropping there would discard directions the mixed
+// path still resolves; exactly dependent FP32 columns are instead kept as
+// directions orthogonal to range(Y) after the second CholeskyQR pass.
+template <>
+struct Eps<double> {
+  static constexpr double value = DBL_EPSILON;
+  __device__ static double drop_factor(int l) { return (double)l; }
+};
+template <>
+struct Eps<float> {
+  static constexpr float value = FLT_EPSILON;
+  __device__ static float drop_factor(int) { return 1.0f; }
+};
+
 __device__ __forceinline__ void set_flag(DeviceStatus* s, int code) {
   atomicOr(&s->flags, 1 << code);
 }
 
 // G (ldg) -> R (ld l, upper; lower part zeroed), Rinv (ld l, upper).
-// `work` must hold l*l doubles (it may be shared memory or global).
+// `work` must hold l*l Ts (it may be shared memory or global).
+template <typename T>
 __global__ void __launch_bounds__(SMALL_THREADS)
-chol_inv_kernel(const double* __restrict__ G, int64_t ldg, int l, double* __restrict__ R,
-                double* __restrict__ Rinv, double* __restrict__ gwork, DeviceStatus* status) {
-  extern __shared__ double smem[];
-  double* W = gwork ? gwork : smem;  // column-major l x l working copy
-  __shared__ double s_maxdiag;
-  __shared__ double s_r;
+chol_inv_kernel(const T* __restrict__ G, int64_t ldg, int l, T* __restrict__ R,
+                T* __restrict__ Rinv, T* __restrict__ gwork, DeviceStatus* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* W = gwork ? gwork : reinterpret_cast<T*>(smem_raw);  // column-major l x l working copy
+  __shared__ T s_maxdiag;
+  __shared__ T s_r;
   __shared__ int s_bad;
   __shared__ int s_deficient;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -57,10 +78,10 @@ chol_inv_kernel(const double* __restrict__ G, int64_t ldg, int l, double* __rest
   }
   __syncthreads();
   if (tid == 0) {
-    double mx = 0.0;
+    T mx = 0.0;
     int bad = 0;
     for (int j = 0; j < l; ++j) {
-      double d = W[j + j * l];
+      T d = W[j + j * l];
       if (!isfinite(d)) bad = 1;
       mx = fmax(mx, fabs(d));
     }
@@ -76,27 +97,27 @@ chol_inv_kernel(const double* __restrict__ G, int64_t ldg, int l, double* __rest
     if (tid == 0) set_flag(status, RSVD_ERR_NONFINITE);
     return;
   }
-  const double tol = (double)l * DBL_EPSILON * s_maxdiag;
+  const T tol = Eps<T>::drop_factor(l) * Eps<T>::value * s_maxdiag;
 
   // Right-looking Cholesky on the upper triangle: G = R^T R.
   for (int j = 0; j < l; ++j) {
     if (tid == 0) {
-      double d = W[j + j * l];
+      T d = W[j + j * l];
       if (!(d > tol)) {
-        s_r = 0.0;  // dropped column
+        s_r = T(0);  // dropped column
         s_deficient++;
       } else {
         s_r = sqrt(d);
       }
     }
     __syncthreads();
-    const double r = s_r;
+    const T r = s_r;
     if (r == 0.0) {
       for (int c = j + tid; c < l; c += nt) W[j + c * l] = 0.0;
       __syncthreads();
       continue;
     }
-    const double inv = 1.0 / r;
+    const T inv = T(1) / r;
     for (int c = j + 1 + tid; c < l; c += nt) W[j + c * l] *= inv;
     if (tid == 0) W[j + j * l] = r;
     __syncthreads();
@@ -120,15 +141,15 @@ chol_inv_kernel(const double* __restrict__ G, int64_t ldg, int l, double* __rest
   // In-place inverse of the upper triangular W (column by column):
   // for column j: Winv[j][j] = 1/R[j][j];  Winv[0:j, j] = -Winv[j][j] * Winv[0:j,0:j] R[0:j, j]
   for (int j = 0; j < l; ++j) {
-    const double rjj = W[j + j * l];
+    const T rjj = W[j + j * l];
     if (rjj == 0.0) {
       for (int i = tid; i <= j; i += nt) W[i + j * l] = 0.0;
       __syncthreads();
       continue;
     }
-    const double ajj = 1.0 / rjj;
+    const T ajj = T(1) / rjj;
     // x_i = sum_{t=i}^{j-1} Winv[i][t] * R[t][j], for i < j (uses columns < j, already inverted)
-    double x = 0.0;
+    T x = 0.0;
     const int i = tid;
     if (i < j) {
       for (int t = i; t < j; ++t) x = fma(W[i + t * l], W[t + j * l], x);
@@ -145,11 +166,12 @@ chol_inv_kernel(const double* __restrict__ G, int64_t ldg, int l, double* __rest
   if (tid == 0 && s_deficient) atomicAdd(&status->deficient, s_deficient);
 }
 
-__global__ void tri_product_kernel(const double* __restrict__ R2, const double* __restrict__ R1,
-                                   int l, double* __restrict__ out, int transpose_out) {
+template <typename T>
+__global__ void tri_product_kernel(const T* __restrict__ R2, const T* __restrict__ R1,
+                                   int l, T* __restrict__ out, int transpose_out) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < l * l; t += gridDim.x * blockDim.x) {
     int i = t % l, j = t / l;
-    double s = 0.0;
+    T s = 0.0;
     if (i <= j)
       for (int u = i; u <= j; ++u) s = fma(R2[i + u * l], R1[u + j * l], s);
     if (transpose_out) out[j + i * l] = s;
@@ -161,7 +183,8 @@ __global__ void tri_product_kernel(const double* __restrict__ R2, const double* 
 // One-sided Jacobi
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
@@ -181,21 +204,23 @@ __device__ __forceinline__ int rr_player(int pos, int r, int twoP) {
 //      interleaved rows and reduce them with shuffles inside the group;
 //   B. one thread per pair turns (a, b, g) into a rotation (c, s);
 //   C. the G threads of each pair apply it to their rows.
+template <typename T>
 __global__ void __launch_bounds__(SMALL_THREADS)
-jacobi_svd_kernel(const double* __restrict__ M, int l, int64_t ldm, double* __restrict__ sig,
-                  double* __restrict__ Um, int64_t ldu, double* __restrict__ Vm, int64_t ldv,
-                  double* __restrict__ UsInv, double* __restrict__ gwork, int use_smem,
+jacobi_svd_kernel(const T* __restrict__ M, int l, int64_t ldm, T* __restrict__ sig,
+                  T* __restrict__ Um, int64_t ldu, T* __restrict__ Vm, int64_t ldv,
+                  T* __restrict__ UsInv, T* __restrict__ gwork, int use_smem,
                   DeviceStatus* status) {
-  extern __shared__ double jsm[];
+  extern __shared__ __align__(16) unsigned char jsm_raw[];
+  T* jsm = reinterpret_cast<T*>(jsm_raw);
   const int twoP = (l + 1) & ~1;  // even number of columns (one zero column if l is odd)
   const int P = twoP / 2;
   const bool want_v = Vm != nullptr;
-  double* Wm = use_smem ? jsm : gwork;
-  double* Wv = Wm + (int64_t)l * twoP;
+  T* Wm = use_smem ? jsm : gwork;
+  T* Wv = Wm + (int64_t)l * twoP;
   __shared__ int s_rot;
-  __shared__ double s_norm[RSVD_L_MAX + 1];
-  __shared__ double s_abg[(RSVD_L_MAX + 1) / 2][3];
-  __shared__ double s_cs[(RSVD_L_MAX + 1) / 2][2];
+  __shared__ T s_norm[RSVD_L_MAX + 1];
+  __shared__ T s_abg[(RSVD_L_MAX + 1) / 2][3];
+  __shared__ T s_cs[(RSVD_L_MAX + 1) / 2][2];
   const int tid = threadIdx.x, nt = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, nwarps = nt >> 5;
   // threads per pair: power of two, at most 16 rows each
@@ -211,7 +236,7 @@ jacobi_svd_kernel(const double* __restrict__ M, int l, int64_t ldm, double* __re
   }
   if (tid == 0) s_rot = 0;
   __syncthreads();
-  const double tol = sqrt((double)l) * DBL_EPSILON;
+  const T tol = sqrt((T)l) * Eps<T>::value;
   int sweep = 0;
   const int max_sweeps = 30;
   for (; sweep < max_sweeps; ++sweep) {
@@ -219,14 +244,14 @@ jacobi_svd_kernel(const double* __restrict__ M, int l, int64_t ldm, double* __re
       // A: partial dot products
       for (int it = tid; it < items_pad; it += nt) {
         const int pr = it / G, sub = it % G;
-        double a = 0.0, b = 0.0, g = 0.0;
+        T a = 0.0, b = 0.0, g = 0.0;
         if (it < items) {
           int p = rr_player(pr, r, twoP), q = rr_player(twoP - 1 - pr, r, twoP);
           if (p > q) { int t = p; p = q; q = t; }
-          const double* cp = Wm + (int64_t)p * l;
-          const double* cq = Wm + (int64_t)q * l;
+          const T* cp = Wm + (int64_t)p * l;
+          const T* cq = Wm + (int64_t)q * l;
           for (int i = sub; i < l; i += G) {
-            double x = cp[i], y = cq[i];
+            T x = cp[i], y = cq[i];
             a = fma(x, x, a);
             b = fma(y, y, b);
             g = fma(x, y, g);
@@ -247,12 +272,12 @@ jacobi_svd_kernel(const double* __restrict__ M, int l, int64_t ldm, double* __re
       // B: rotation parameters (Rutishauser): zeta = (b - a) / (2g),
       // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1+t^2), s = c t
       for (int pr = tid; pr < P; pr += nt) {
-        const double a = s_abg[pr][0], b = s_abg[pr][1], g = s_abg[pr][2];
-        double c = 1.0, sn = 0.0;
+        const T a = s_abg[pr][0], b = s_abg[pr][1], g = s_abg[pr][2];
+        T c = T(1), sn = T(0);
         if (g != 0.0 && fabs(g) > tol * sqrt(a) * sqrt(b)) {
-          const double zeta = (b - a) / (2.0 * g);
-          const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
-          c = rsqrt(fma(t, t, 1.0));
+          const T zeta = (b - a) / (T(2) * g);
+          const T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, T(1))));
+          c = rsqrt(fma(t, t, T(1)));
           sn = c * t;
           s_rot = 1;
         }
@@ -263,22 +288,22 @@ jacobi_svd_kernel(const double* __restrict__ M, int l, int64_t ldm, double* __re
       // C: apply
       for (int it = tid; it < items; it += nt) {
         const int pr = it / G, sub = it % G;
-        const double c = s_cs[pr][0], sn = s_cs[pr][1];
+        const T c = s_cs[pr][0], sn = s_cs[pr][1];
         if (sn == 0.0) continue;
         int p = rr_player(pr, r, twoP), q = rr_player(twoP - 1 - pr, r, twoP);
         if (p > q) { int t = p; p = q; q = t; }
-        double* cp = Wm + (int64_t)p * l;
-        double* cq = Wm + (int64_t)q * l;
+        T* cp = Wm + (int64_t)p * l;
+        T* cq = Wm + (int64_t)q * l;
         for (int i = sub; i < l; i += G) {
-          double x = cp[i], y = cq[i];
+          T x = cp[i], y = cq[i];
           cp[i] = c * x - sn * y;
           cq[i] = sn * x + c * y;
         }
         if (want_v) {
-          double* vp = Wv + (int64_t)p * l;
-          double* vq = Wv + (int64_t)q * l;
+          T* vp = Wv + (int64_t)p * l;
+          T* vq = Wv + (int64_t)q * l;
           for (int i = sub; i < l; i += G) {
-            double x = vp[i], y = vq[i];
+            T x = vp[i], y = vq[i];
             vp[i] = c * x - sn * y;
             vq[i] = sn * x + c * y;
           }
@@ -298,8 +323,8 @@ jacobi_svd_kernel(const double* __restrict__ M, int l, int64_t ldm, double* __re
   }
   // column norms
   for (int c = warp; c < l; c += nwarps) {
-    const double* cp = Wm + (int64_t)c * l;
-    double a = 0.0;
+    const T* cp = Wm + (int64_t)c * l;
+    T a = 0.0;
     for (int i = lane; i < l; i += 32) a = fma(cp[i], cp[i], a);
     a = warp_sum(a);
     if (lane == 0) s_norm[c] = sqrt(a);
@@ -307,18 +332,18 @@ jacobi_svd_kernel(const double* __restrict__ M, int l, int64_t ldm, double* __re
   __syncthreads();
   // sort descending by rank; ties keep column order
   for (int c = warp; c < l; c += nwarps) {
-    const double sc = s_norm[c];
+    const T sc = s_norm[c];
     int rank = 0;
     for (int d = lane; d < l; d += 32) {
-      double sd = s_norm[d];
+      T sd = s_norm[d];
       rank += (sd > sc || (sd == sc && d < c)) ? 1 : 0;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) rank += __shfl_xor_sync(0xffffffffu, rank, o);
-    const double inv = sc > 0.0 ? 1.0 / sc : 0.0;
+    const T inv = sc > T(0) ? T(1) / sc : T(0);
     if (lane == 0) sig[rank] = sc;
     for (int i = lane; i < l; i += 32) {
-      const double u = Wm[i + (int64_t)c * l] * inv;
+      const T u = Wm[i + (int64_t)c * l] * inv;
       Um[i + (int64_t)rank * ldu] = u;
       if (UsInv) UsInv[i + (int64_t)rank * l] = u * inv;
       if (want_v) Vm[i + (int64_t)rank * ldv] = Wv[i + (int64_t)c * l];
@@ -330,24 +355,25 @@ jacobi_svd_kernel(const double* __restrict__ M, int l, int64_t ldm, double* __re
 // Sign convention and outputs
 // ---------------------------------------------------------------------------
 
-__global__ void sign_kernel(double* __restrict__ U, int64_t m, int64_t ldu,
-                            double* __restrict__ sign) {
+template <typename T>
+__global__ void sign_kernel(T* __restrict__ U, int64_t m, int64_t ldu,
+                            T* __restrict__ sign) {
   const int col = blockIdx.x;
-  double* u = U + (int64_t)col * ldu;
-  double best = -1.0;
+  T* u = U + (int64_t)col * ldu;
+  T best = -1.0;
   int64_t bidx = 0;
   for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
-    double v = fabs(u[i]);
+    T v = fabs(u[i]);
     if (v > best) { best = v; bidx = i; }
   }
-  __shared__ double sv[1024];
+  __shared__ T sv[1024];
   __shared__ int64_t si[1024];
   sv[threadIdx.x] = best;
   si[threadIdx.x] = bidx;
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
     if (threadIdx.x < s) {
-      double o = sv[threadIdx.x + s];
+      T o = sv[threadIdx.x + s];
       int64_t oi = si[threadIdx.x + s];
       if (o > sv[threadIdx.x] || (o == sv[threadIdx.x] && oi < si[threadIdx.x])) {
         sv[threadIdx.x] = o;
@@ -356,7 +382,7 @@ __global__ void sign_kernel(double* __restrict__ U, int64_t m, int64_t ldu,
     }
     __syncthreads();
   }
-  __shared__ double s_sign;
+  __shared__ T s_sign;
   if (threadIdx.x == 0) {
     s_sign = (u[si[0]] < 0.0) ? -1.0 : 1.0;
     sign[col] = s_sign;
@@ -366,9 +392,10 @@ __global__ void sign_kernel(double* __restrict__ U, int64_t m, int64_t ldu,
     for (int64_t i = threadIdx.x; i < m; i += blockDim.x) u[i] = -u[i];
 }
 
-__global__ void vt_kernel(const double* __restrict__ Vk, int64_t n, int k,
-                          const double* __restrict__ sign, double* __restrict__ VT, int64_t ldvt,
-                          const double* __restrict__ sig, double* __restrict__ S) {
+template <typename T>
+__global__ void vt_kernel(const T* __restrict__ Vk, int64_t n, int k,
+                          const T* __restrict__ sign, T* __restrict__ VT, int64_t ldvt,
+                          const T* __restrict__ sig, double* __restrict__ S) {
   // VT (k x n): VT[i + j*ldvt] = sign[i] * Vk[j + i*n]
   const int64_t total = n * (int64_t)k;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -378,68 +405,83 @@ __global__ void vt_kernel(const double* __restrict__ Vk, int64_t n, int k,
     VT[i + j * ldvt] = sign[i] * Vk[j + (int64_t)i * n];
   }
   if (blockIdx.x == 0)
-    for (int i = threadIdx.x; i < k; i += blockDim.x) S[i] = sig[i];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) S[i] = (double)sig[i];
 }
 
 }  // namespace
 
-cudaError_t launch_chol_inv(const double* G, int64_t ldg, int l, double* R, double* Rinv,
-                            double* work, DeviceStatus* status, cudaStream_t st) {
-  size_t smem = (size_t)l * l * sizeof(double);
-  if (smem <= 200 * 1024) {
-    static bool attr_set = false;
-    if (!attr_set) {
-      cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           200 * 1024);
-      attr_set = true;
-    }
-    chol_inv_kernel<<<1, SMALL_THREADS, smem, st>>>(G, ldg, l, R, Rinv, nullptr, status);
-    note_launch();
-  } else {
-    chol_inv_kernel<<<1, SMALL_THREADS, 0, st>>>(G, ldg, l, R, Rinv, work, status);
-    note_launch();
-  }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_tri_product(const double* R2, const double* R1, int l, double* out,
-                               bool transpose_out, cudaStream_t st) {
-  int total = l * l;
-  tri_product_kernel<<<(total + 255) / 256, 256, 0, st>>>(R2, R1, l, out, transpose_out ? 1 : 0);
-  note_launch();
-  return cudaGetLastError();
-}
-
-cudaError_t launch_jacobi_svd(const double* M, int l, int64_t ldm, double* sig, double* Um,
-                              int64_t ldu, double* Vm, int64_t ldv, double* UsInv, double* work,
-                              DeviceStatus* status, cudaStream_t st) {
-  const int twoP = (l + 1) & ~1;
-  const size_t need = (size_t)(Vm ? 2 : 1) * l * twoP * sizeof(double);
+template <typename T>
+cudaError_t launch_chol_inv(const T* G, int64_t ldg, int l, T* R, T* Rinv, T* work,
+                            DeviceStatus* status, cudaStream_t st) {
+  const size_t smem = (size_t)l * l * sizeof(T);
   const size_t cap = 200 * 1024;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(jacobi_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
+    cudaFuncSetAttribute(chol_inv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
     attr_set = true;
   }
-  const bool smem = need <= cap;
-  jacobi_svd_kernel<<<1, SMALL_THREADS, smem ? need : 0, st>>>(M, l, ldm, sig, Um, ldu, Vm, ldv,
-                                                               UsInv, work, smem ? 1 : 0, status);
+  if (smem <= cap)
+    chol_inv_kernel<T><<<1, SMALL_THREADS, smem, st>>>(G, ldg, l, R, Rinv, nullptr, status);
+  else
+    chol_inv_kernel<T><<<1, SMALL_THREADS, 0, st>>>(G, ldg, l, R, Rinv, work, status);
   note_launch();
   return cudaGetLastError();
 }
 
-cudaError_t launch_finalize_f64(double* U, int64_t m, int64_t ldu, int k, const double* Vk,
-                                int64_t n, double* VT, int64_t ldvt, const double* sig, double* S,
-                                double* sign_work, cudaStream_t st) {
-  sign_kernel<<<k, 1024, 0, st>>>(U, m, ldu, sign_work);
+template <typename T>
+cudaError_t launch_tri_product(const T* R2, const T* R1, int l, T* out, bool transpose_out,
+                               cudaStream_t st) {
+  int total = l * l;
+  tri_product_kernel<T><<<(total + 255) / 256, 256, 0, st>>>(R2, R1, l, out,
+                                                             transpose_out ? 1 : 0);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_jacobi_svd(const T* M, int l, int64_t ldm, T* sig, T* Um, int64_t ldu, T* Vm,
+                              int64_t ldv, T* UsInv, T* work, DeviceStatus* status,
+                              cudaStream_t st) {
+  const int twoP = (l + 1) & ~1;
+  const size_t need = (size_t)(Vm ? 2 : 1) * l * twoP * sizeof(T);
+  const size_t cap = 200 * 1024;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(jacobi_svd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)cap);
+    attr_set = true;
+  }
+  const bool smem = need <= cap;
+  jacobi_svd_kernel<T><<<1, SMALL_THREADS, smem ? need : 0, st>>>(
+      M, l, ldm, sig, Um, ldu, Vm, ldv, UsInv, work, smem ? 1 : 0, status);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_finalize(T* U, int64_t m, int64_t ldu, int k, const T* Vk, int64_t n, T* VT,
+                            int64_t ldvt, const T* sig, double* S, T* sign_work,
+                            cudaStream_t st) {
+  sign_kernel<T><<<k, 1024, 0, st>>>(U, m, ldu, sign_work);
   note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   int64_t total = n * (int64_t)k;
   int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
-  vt_kernel<<<blocks, 256, 0, st>>>(Vk, n, k, sign_work, VT, ldvt, sig, S);
+  vt_kernel<T><<<blocks, 256, 0, st>>>(Vk, n, k, sign_work, VT, ldvt, sig, S);
   note_launch();
   return cudaGetLastError();
 }
+
+#define RSVD_INSTANTIATE_SMALL(T)                                                              \
+  template cudaError_t launch_chol_inv<T>(const T*, int64_t, int, T*, T*, T*, DeviceStatus*,   \
+                                          cudaStream_t);                                       \
+  template cudaError_t launch_tri_product<T>(const T*, const T*, int, T*, bool, cudaStream_t); \
+  template cudaError_t launch_jacobi_svd<T>(const T*, int, int64_t, T*, T*, int64_t, T*,       \
+                                            int64_t, T*, T*, DeviceStatus*, cudaStream_t);     \
+  template cudaError_t launch_finalize<T>(T*, int64_t, int64_t, int, const T*, int64_t, T*,    \
+                                          int64_t, const T*, double*, T*, cudaStream_t);
+RSVD_INSTANTIATE_SMALL(double)
+RSVD_INSTANTIATE_SMALL(float)
 
 }  // namespace rsvd

@@ -1,0 +1,31 @@
+// tcgen05 BF16 passes over A (mixed path): host interface.
+#pragma once
+
+#include "internal.h"
+
+namespace rsvd {
+
+struct ApassCall {
+  bool ax;              // true: Y = A X (contracts n); false: Z = A^T X (contracts m)
+  const void* A;        // BF16 m x n, column-major, lda % 8 == 0, 16-byte aligned
+  int64_t m, n, lda;
+  const void* X;        // BF16 operand: (n for ax, m otherwise) x x_cols, ldx % 8 == 0
+  int64_t ldx;
+  int x_cols;           // columns present in X (the rest of the last part reads as zero)
+  int l;                // output columns
+  int slices;           // operand slices summed into the output (1..3)
+  int slice_stride;     // column offset between slices (>= l rounded up to 16)
+  float* out;           // FP32 (m or n) x l, column-major
+  int64_t ldo;
+  float* part;          // partial slots
+  size_t part_floats;
+};
+
+// Floats of partial-slot workspace a pass with `l` output columns needs.
+size_t apass_partial_floats(int num_sms, int l);
+
+// Enqueues the pass (main kernel + split-tile fixup).  Returns RSVD_OK or a
+// positive RSVD_ERR_* code (unsupported alignment/shape, workspace, CUDA).
+int launch_apass_bf16(const ApassCall& c, int num_sms, int* status, cudaStream_t st);
+
+}  // namespace rsvd

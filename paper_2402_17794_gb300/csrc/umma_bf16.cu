@@ -1,0 +1,528 @@
+// BF16 passes over A on the tcgen05 tensor cores (mixed path of Algorithm 4,
+// steps 2, 5 and 6, Section 3.3):
+//
+//   kind AX  : Y = A X     (m x n times n x N, contracts the long n; A is
+//              MN-major for the MMA because its columns are contiguous)
+//   kind ATX : Z = A^T X   (n x m times m x N, contracts the long m; A is
+//              K-major)
+//
+// A is read exactly once from HBM per pass; X (l <= 256 columns, BF16,
+// column-major) is small and is re-read from L2.  X may hold up to three BF16
+// "slices" side by side (x = x_1 + x_2 + x_3, the bf16x2 / bf16x3 split of an
+// FP32 operand); the MMAs of every slice accumulate into the same TMEM
+// accumulator, so D = A (x_1 + x_2 + x_3) in FP32.  Design:
+//
+//  * Persistent grid, one CTA per SM.  The (tile, k-block) iteration space
+//    (tile = 128 output rows, k-block = 64 of the contraction) is cut into
+//    equal contiguous ranges, one per CTA ("stream-K"), so every SM streams
+//    the same number of bytes of A.  A tile whose k-range is split between
+//    CTAs is written as per-CTA partials and summed by a second kernel in
+//    CTA order (deterministic).
+//  * Warp roles: warp 0 issues TMA (cp.async.bulk.tensor, 128-byte swizzle)
+//    into a ring of shared-memory stages guarded by mbarriers; warp 1 owns
+//    the TMEM accumulator and one lane issues tcgen05.mma (M=128, N<=256 per
+//    instruction, K=16, FP32 accumulate in TMEM) and tcgen05.commit; warps
+//    2-5 drain the accumulator with tcgen05.ld and store FP32 results.
+//  * Every mbarrier wait is bounded (about one second of clock64); on expiry
+//    the CTA records RSVD_ERR_TIMEOUT, stops issuing, drains what it issued
+//    and frees its TMEM before returning.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "internal.h"
+#include "umma.h"
+
+namespace rsvd {
+namespace {
+
+constexpr int BM = 128;               // output rows per tile (MMA M)
+constexpr int BK = 64;                // contraction per stage (one 128-byte swizzle row)
+constexpr int A_STAGE_BYTES = BM * BK * 2;
+constexpr int THREADS = 192;          // 6 warps
+constexpr long long kWaitCycles = 2000000000LL;   // ~1 s at 2 GHz
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait; returns false (and raises the CTA's abort flag) on expiry or
+// when another role already aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  long long t0 = clock64();
+  for (uint32_t it = 0;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255) == 255) {
+      if (*abort) return false;
+      if (clock64() - t0 > kWaitCycles) {
+        *abort = 1;
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* bar, void* dst, int x,
+                                            int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(dst)),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor (tcgen05): start >> 4 in bits 0-13, leading
+// byte offset >> 4 in 16-29, stride byte offset >> 4 in 32-45, descriptor
+// version 1 in bits 46-47, swizzle mode in 61-63 (2 = 128-byte swizzle).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor for kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
+// (bits 7-9, 10-12 = 1), A major (bit 15: 0 K-major, 1 MN-major), B K-major
+// (bit 16 = 0), N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool a_mn_major) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn_major ? 1u : 0u) << 15) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// ---------------------------------------------------------------------------
+// Kernel
+// ---------------------------------------------------------------------------
+
+struct ApassArgs {
+  int64_t rows_out;   // output rows (m for AX, n for ATX)
+  int64_t total;      // tiles * kt iterations
+  int kt;             // k-blocks per tile
+  int parts;          // MMA N-parts
+  int nb;             // columns per part (multiple of 16, <= 256)
+  int slices;         // operand slices accumulated into D
+  int slice_stride;   // columns between slices in the operand
+  int l16;            // operand columns per slice in shared memory (l rounded up to 16)
+  int l;              // output columns
+  int stages;
+  uint32_t tmem_cols;
+  uint32_t lbo_mn, sbo_mn;  // descriptor offsets of the MN-major A layout
+  float* out;
+  int64_t ldo;
+  float* part;        // partial slots, gridDim.x * 2 * BM * l floats
+  int* status;
+};
+
+__device__ __forceinline__ int64_t range_begin(int64_t total, int c, int g) {
+  return (int64_t)((__int128)total * c / g);
+}
+
+template <bool AX>
+__global__ void __launch_bounds__(THREADS, 1)
+apass_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX,
+                  const ApassArgs args) {
+  extern __shared__ uint8_t smem_raw[];
+  // carve: barriers first, then 1024-aligned tiles
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
+  uint64_t* empty = full + args.stages;
+  uint64_t* acc_full = empty + args.stages;
+  uint64_t* acc_empty = acc_full + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t tiles_off = ((raw + 256 + 1023) & ~1023u) - raw;
+  uint8_t* tiles = smem_raw + tiles_off;
+  const int x_stage_bytes = args.slices * args.l16 * 128;
+  const int stage_bytes = A_STAGE_BYTES + x_stage_bytes;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t g0 = range_begin(args.total, blockIdx.x, gridDim.x);
+  const int64_t g1 = range_begin(args.total, blockIdx.x + 1, gridDim.x);
+  if (g0 >= g1) return;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < args.stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, 4);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, args.tmem_cols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      int64_t it = 0;
+      for (int64_t g = g0; g < g1; ++g, ++it) {
+        const int s = (int)(it % args.stages);
+        const uint32_t ph = (uint32_t)((it / args.stages) & 1);
+        if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) break;
+        const int64_t t = g / args.kt;
+        const int kb = (int)(g - t * args.kt);
+        uint8_t* a_s = tiles + (size_t)s * stage_bytes;
+        uint8_t* x_s = a_s + A_STAGE_BYTES;
+        mbar_expect_tx(&full[s], (uint32_t)stage_bytes);
+        if (AX) {
+          tma_load_2d(&tmA, &full[s], a_s, (int)(t * BM), kb * BK);
+          tma_load_2d(&tmA, &full[s], a_s + A_STAGE_BYTES / 2, (int)(t * BM + 64), kb * BK);
+        } else {
+          tma_load_2d(&tmA, &full[s], a_s, kb * BK, (int)(t * BM));
+          tma_load_2d(&tmA, &full[s], a_s + A_STAGE_BYTES / 2, kb * BK, (int)(t * BM + 64));
+        }
+        for (int sl = 0; sl < args.slices; ++sl)
+          for (int p = 0; p < args.parts; ++p)
+            tma_load_2d(&tmX, &full[s], x_s + (sl * args.l16 + p * args.nb) * 128, kb * BK,
+                        sl * args.slice_stride + p * args.nb);
+      }
+      // on abort: wait (bounded) for the loads already issued to land
+      if (*abort_flag) {
+        int64_t issued = it;
+        for (int64_t j = (issued > args.stages ? issued - args.stages : 0); j < issued; ++j) {
+          long long t0 = clock64();
+          while (!mbar_try_wait(&full[j % args.stages], (uint32_t)((j / args.stages) & 1)) &&
+                 clock64() - t0 < kWaitCycles) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(BM, args.nb, AX);
+      int64_t it = 0;
+      int seg = 0;
+      bool ok = true;
+      for (int64_t g = g0; g < g1 && ok; ++g, ++it) {
+        const int s = (int)(it % args.stages);
+        const uint32_t ph = (uint32_t)((it / args.stages) & 1);
+        const int64_t t = g / args.kt;
+        const int kb = (int)(g - t * args.kt);
+        const bool seg_first = (g == g0) || kb == 0;
+        const bool seg_last = (g == g1 - 1) || kb == args.kt - 1;
+        if (seg_first && seg > 0) {
+          // the epilogue must have drained the previous segment
+          if (!mbar_wait(acc_empty, (uint32_t)((seg - 1) & 1), abort_flag)) { ok = false; break; }
+          tc_fence_after();
+        }
+        if (!mbar_wait(&full[s], ph, abort_flag)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t a_base = smem_u32(tiles + (size_t)s * stage_bytes);
+        const uint32_t x_base = a_base + A_STAGE_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          uint64_t adesc;
+          if (AX)  // MN-major A: 2 atoms of 64 rows (LBO apart), K groups of 8 (SBO apart)
+            adesc = sdesc(a_base + kk * 2048, args.lbo_mn, args.sbo_mn);
+          else     // K-major A: rows of 128 bytes, 8-row groups 1024 bytes apart
+            adesc = sdesc(a_base + kk * 32, 16, 1024);
+          for (int sl = 0; sl < args.slices; ++sl)
+            for (int p = 0; p < args.parts; ++p) {
+              const uint64_t bdesc =
+                  sdesc(x_base + (sl * args.l16 + p * args.nb) * 128 + kk * 32, 16, 1024);
+              umma_bf16(tmem_base + p * args.nb, adesc, bdesc, idesc,
+                        (seg_first && kk == 0 && sl == 0) ? 0u : 1u);
+            }
+        }
+        umma_commit(&empty[s]);           // stage reusable once these MMAs finish
+        if (seg_last) {
+          umma_commit(acc_full);          // accumulator ready for the epilogue
+          ++seg;
+        }
+      }
+      if (!ok) {
+        // drain: one more commit tracks every MMA issued so far; wait for it
+        // (bounded) so TMEM is idle before it is freed
+        umma_commit(acc_full);
+        long long t0 = clock64();
+        while (!mbar_try_wait(acc_full, (uint32_t)(seg & 1)) && clock64() - t0 < kWaitCycles) {
+        }
+      }
+    }
+  } else {
+    // ---------------- epilogue (warps 2..5) ----------------
+    const int quad = warp & 3;            // TMEM lane quadrant this warp may access
+    const int row_in_tile = quad * 32 + lane;
+    int seg = 0;
+    int64_t g = g0;
+    while (g < g1) {
+      const int64_t t = g / args.kt;
+      const int kb0 = (int)(g - t * args.kt);
+      const int64_t gend = (g1 < (t + 1) * args.kt) ? g1 : (t + 1) * args.kt;
+      const bool full_tile = (kb0 == 0) && (gend - t * args.kt == args.kt);
+      if (!mbar_wait(acc_full, (uint32_t)(seg & 1), abort_flag)) break;
+      tc_fence_after();
+      float* dst;
+      int64_t ld;
+      int64_t row;
+      if (full_tile) {
+        row = t * BM + row_in_tile;
+        dst = args.out;
+        ld = args.ldo;
+      } else {
+        const int slot = (g == g0) ? 0 : 1;
+        row = row_in_tile;
+        dst = args.part + ((size_t)blockIdx.x * 2 + slot) * (size_t)BM * args.l;
+        ld = BM;
+      }
+      const bool row_ok = full_tile ? (row < args.rows_out) : true;
+      const uint32_t lane_base = tmem_base + ((uint32_t)(quad * 32) << 16);
+      for (int c0 = 0; c0 < args.l; c0 += 16) {
+        uint32_t r[16];
+        tmem_ld16(lane_base + (uint32_t)c0, r);
+        tmem_wait_ld();
+        if (row_ok) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (c0 + j < args.l) dst[row + (int64_t)(c0 + j) * ld] = __uint_as_float(r[j]);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acc_empty);
+      ++seg;
+      g = gend;
+    }
+  }
+
+  __syncthreads();
+  if (threadIdx.x == 0 && *abort_flag) atomicOr(args.status, 1 << RSVD_ERR_TIMEOUT);
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, args.tmem_cols);
+  }
+}
+
+// Sums the per-CTA partials of every tile whose k-range was split, in CTA
+// order.  One block per tile; tiles written whole by one CTA are skipped.
+__global__ void apass_fixup_kernel(const float* __restrict__ part, int grid, int64_t total, int kt,
+                                   int l, int64_t rows_out, float* __restrict__ out, int64_t ldo) {
+  auto begin = [&](int c) { return (int64_t)((__int128)total * c / grid); };
+  auto cta_of = [&](int64_t g) {
+    int c = (int)((__int128)g * grid / total);
+    while (c + 1 < grid && begin(c + 1) <= g) ++c;
+    while (c > 0 && begin(c) > g) --c;
+    return c;
+  };
+  const int64_t t = blockIdx.x;
+  const int cf = cta_of(t * kt), cl = cta_of((t + 1) * kt - 1);
+  if (cf == cl) return;  // written directly by one CTA
+  const int64_t per_tile = (int64_t)BM * l;
+  for (int64_t idx = threadIdx.x; idx < per_tile; idx += blockDim.x) {
+    const int c = (int)(idx / BM), r = (int)(idx % BM);
+    const int64_t row = t * BM + r;
+    if (row >= rows_out) continue;
+    float s = 0.f;
+    for (int cc = cf; cc <= cl; ++cc) {
+      const int64_t b = begin(cc);
+      if (b >= begin(cc + 1)) continue;
+      const int slot = (b / kt == t) ? 0 : 1;
+      s += part[((size_t)cc * 2 + slot) * per_tile + (size_t)c * BM + r];
+    }
+    out[row + (int64_t)c * ldo] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+bool make_map_bf16(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld,
+                   int box_rows, int box_cols) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)rows, (cuuint64_t)cols};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)box_rows, (cuuint32_t)box_cols};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// MN-major A (the Y = A X pass): the stage holds two 64-row boxes of the A
+// tile (64 K-rows of 128 bytes each); the leading byte offset steps between
+// the two 64-element MN atoms (one box, 64 x 128 bytes apart) and the stride
+// byte offset between 8-row K groups (1024 bytes).
+constexpr uint32_t kLboMn = BK * 128, kSboMn = 1024;
+
+}  // namespace
+
+size_t apass_partial_floats(int num_sms, int l) { return (size_t)num_sms * 2 * BM * l; }
+
+int launch_apass_bf16(const ApassCall& c, int num_sms, int* status, cudaStream_t st) {
+  // shape checks (host-side; the kernel assumes them)
+  if (c.lda % 8 || c.ldx % 8 || ((uintptr_t)c.A % 16) || ((uintptr_t)c.X % 16))
+    return RSVD_ERR_UNSUPPORTED;
+  const int64_t rows_out = c.ax ? c.m : c.n;
+  const int64_t kdim = c.ax ? c.n : c.m;
+  const int l16 = (c.l + 15) / 16 * 16;
+  if (c.l < 1 || c.l > 256 || c.slices < 1 || c.slices > 3) return RSVD_ERR_UNSUPPORTED;
+  if (c.slice_stride < l16 && c.slices > 1) return RSVD_ERR_UNSUPPORTED;
+  // N per MMA: one part for l16 <= 256 (the instruction's limit)
+  const int parts = 1;
+  const int nb = l16;
+  uint32_t tmem_cols = 32;
+  while (tmem_cols < (uint32_t)l16) tmem_cols <<= 1;
+  const int64_t tiles = (rows_out + BM - 1) / BM;
+  const int kt = (int)((kdim + BK - 1) / BK);
+  const int64_t total = tiles * kt;
+  const int stage_bytes = A_STAGE_BYTES + c.slices * l16 * 128;
+  const int smem_cap = 227 * 1024;
+  int stages = (smem_cap - 2048) / stage_bytes;
+  stages = std::min(stages, 8);
+  if (stages < 2) return RSVD_ERR_UNSUPPORTED;
+  const size_t smem = 2048 + (size_t)stages * stage_bytes;
+
+  CUtensorMap tmA, tmX;
+  // A: rows x cols = m x n; X: (kdim) x (operand columns) with ld ldx
+  if (!make_map_bf16(&tmA, c.A, c.m, c.n, c.lda, 64, 64)) return RSVD_ERR_CUDA;
+  if (!make_map_bf16(&tmX, c.X, kdim, c.x_cols, c.ldx, 64, nb)) return RSVD_ERR_CUDA;
+
+  int grid = (int)std::min<int64_t>(num_sms, total);
+  ApassArgs a;
+  a.rows_out = rows_out;
+  a.total = total;
+  a.kt = kt;
+  a.parts = parts;
+  a.nb = nb;
+  a.slices = c.slices;
+  a.slice_stride = c.slice_stride;
+  a.l16 = l16;
+  a.l = c.l;
+  a.stages = stages;
+  a.tmem_cols = tmem_cols;
+  a.lbo_mn = kLboMn;
+  a.sbo_mn = kSboMn;
+  a.out = c.out;
+  a.ldo = c.ldo;
+  a.part = c.part;
+  a.status = status;
+  if (c.part_floats < apass_partial_floats(grid, c.l)) return RSVD_ERR_WORKSPACE;
+  if (c.ax) {
+    cudaFuncSetAttribute(apass_bf16_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    apass_bf16_kernel<true><<<grid, THREADS, smem, st>>>(tmA, tmX, a);
+  } else {
+    cudaFuncSetAttribute(apass_bf16_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    apass_bf16_kernel<false><<<grid, THREADS, smem, st>>>(tmA, tmX, a);
+  }
+  note_launch();
+  if (cudaGetLastError() != cudaSuccess) return RSVD_ERR_CUDA;
+  apass_fixup_kernel<<<(unsigned)tiles, 256, 0, st>>>(c.part, grid, total, kt, c.l, rows_out,
+                                                       c.out, c.ldo);
+  note_launch();
+  if (cudaGetLastError() != cudaSuccess) return RSVD_ERR_CUDA;
+  return RSVD_OK;
+}
+
+}  // namespace rsvd
+
