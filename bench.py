@@ -43,6 +43,12 @@ WORKLOADS = {
              "k=64, p=16, q=2; Gaussian Omega 8192x80",
         m=16384, n=8192, k=64, p=16, q=2, spectrum=("poly", 1.5), seed_a=0, seed=2,
         dtype="f64"),
+    "mixed-bf16": dict(
+        desc="mixed precision: A 65536x16384 stored BF16, Haar factors, sigma_i=exp(-i/40) "
+             "plus 1e-4 Gaussian noise floor; k=128, p=32, q=3 (+1 bf16x2 refinement step, "
+             "bf16x3 final B); FP32 accumulate",
+        m=65536, n=16384, k=128, p=32, q=3, spectrum=("exp", 40.0), terms=640, noise=1e-4,
+        seed_a=0, seed=2, dtype="bf16"),
 }
 
 
@@ -134,17 +140,126 @@ def _max_over_ranks(x: float, world: int) -> float:
 def _sigma(w):
     from paper_2402_17794_gb300 import synthetic as syn
     kind, arg = w["spectrum"]
-    r = min(w["m"], w["n"])
+    r = w.get("terms", min(w["m"], w["n"]))
     if kind == "poly":
         return syn.spectrum("poly", r, alpha=arg)
+    if kind == "exp":
+        return syn.spectrum("exp", r, r=arg)
     raise ValueError(kind)
 
 
 def _make_input(w, rank):
     import torch
     from paper_2402_17794_gb300 import synthetic as syn
+    if w["dtype"] == "bf16":
+        return syn.lowrank_matrix_torch(w["m"], w["n"], _sigma(w), seed=w["seed_a"] + 1000 * rank,
+                                        device="cuda", dtype=torch.bfloat16,
+                                        factor_dtype=torch.float32,
+                                        noise_2norm=w.get("noise", 0.0))
     return syn.lowrank_matrix_torch(w["m"], w["n"], _sigma(w), seed=w["seed_a"] + 1000 * rank,
                                     device="cuda", dtype=torch.float64)
+
+
+def run_mixed(args, world, rank, sampler_uuid):
+    """The mixed-precision workload: solves/s and the tcgen05 passes over A
+    timed alone against the HBM roofline."""
+    import torch
+
+    from paper_2402_17794_gb300 import rsvd as R
+
+    w = WORKLOADS["mixed-bf16"]
+    m, n, k, p, q, seed = w["m"], w["n"], w["k"], w["p"], w["q"], w["seed"]
+    l = k + p
+    a_bytes = m * n * 2
+    passes = 2 * (q + 1) + 2
+    dA = _make_input(w, rank)
+    stream = torch.cuda.current_stream()
+    plan = R.Plan(m, n, l, a_dtype=R.BF16, mode=R.MIXED)
+    U = torch.empty(k, m, dtype=torch.float32, device="cuda")
+    S = torch.empty(k, dtype=torch.float64, device="cuda")
+    VT = torch.empty(n, k, dtype=torch.float32, device="cuda")
+
+    def step():
+        R._check(R.rsvd_solve(plan.handle, dA, m, n, m, k, p, q, seed, U, m, S, VT, k),
+                 "rsvd_solve (mixed)")
+
+    for _ in range(args.warmup):
+        step()
+    st = plan.status()
+    if st != 0:
+        raise RuntimeError(f"mixed warm-up failed: {R.rsvd_status_string(st)}")
+    steps = max(args.steps, 10)
+    sampler = ClockSampler(sampler_uuid)
+    sampler.start()
+    _barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat = []
+    for _ in range(steps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        lat.append((a, b))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = _max_over_ranks(e0.elapsed_time(e1), world)
+    per = sorted(a.elapsed_time(b) for a, b in lat)
+    st = plan.status()
+    if st != 0:
+        raise RuntimeError(f"mixed solve failed: {R.rsvd_status_string(st)}")
+
+    # the tcgen05 passes alone (one BF16 operand slice, l = 160)
+    X_n = torch.randn(l, n, device="cuda").to(torch.bfloat16)
+    X_m = torch.randn(l, m, device="cuda").to(torch.bfloat16)
+    Y = torch.empty(l, m, dtype=torch.float32, device="cuda")
+    Z = torch.empty(l, n, dtype=torch.float32, device="cuda")
+
+    def time_call(fn, reps=10):
+        fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    t_ax = time_call(lambda: R.rsvd_apply_a(plan.handle, dA, m, n, m, X_n, n, l, Y, m))
+    t_atx = time_call(lambda: R.rsvd_apply_at(plan.handle, dA, m, n, m, X_m, m, l, Z, n))
+    st = plan.status()
+    if st != 0:
+        raise RuntimeError(f"mixed pass failed: {R.rsvd_status_string(st)}")
+    peaks, _ = _peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    dom_ms = max(t_ax, t_atx)
+    dom = "apass_bf16_kernel<true> (Y = A X)" if t_ax >= t_atx else \
+        "apass_bf16_kernel<false> (Z = A^T X)"
+    achieved = a_bytes / (dom_ms / 1e3) / 1e9
+    out = {
+        "workload": w["desc"], "value": round(steps * world / (ms / 1e3), 3), "unit": "solves/s",
+        "ms_per_solve": round(ms / steps, 4),
+        "p50_ms": round(per[len(per) // 2], 4), "p99_ms": round(per[min(len(per) - 1, int(0.99 * len(per)))], 4),
+        "dtype": "bf16 A, fp32 accumulate", "passes_per_solve": passes,
+        "a_pass": {"ms_ax": round(t_ax, 4), "ms_atx": round(t_atx, 4),
+                   "gbps_ax": round(a_bytes / (t_ax / 1e3) / 1e9, 1),
+                   "gbps_atx": round(a_bytes / (t_atx / 1e3) / 1e9, 1),
+                   "gbps_in_solve": round(passes * a_bytes / (ms / steps / 1e3) / 1e9, 1)},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
+                     "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                     "traffic": _traffic_from_profile("mixed-bf16"),
+                     "algorithmic_bytes_per_launch": a_bytes,
+                     "ms_per_launch": round(dom_ms, 4)},
+        "clocks": clocks,
+    }
+    del dA
+    return out
 
 
 def _oracle_rate(A_host, w, budget_s: float):
@@ -313,6 +428,12 @@ def run_ours(args):
     if st != 0:
         raise RuntimeError(f"e2e solve failed: {R.rsvd_status_string(st)}")
 
+    # --- the mixed-precision workload beside it ---
+    mixed = None
+    if not args.no_mixed:
+        del A_h, dA2
+        mixed = run_mixed(args, world, rank, uuid)
+
     # --- CPU oracle on this host (rank 0, N = 1 only) ---
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -335,6 +456,7 @@ def run_ours(args):
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "mixed": mixed,
         "gpu_launches": int(launches),
         "gpu_launches_per_step": launches / args.steps,
         "jacobi_sweeps": sweeps,
@@ -348,7 +470,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def _traffic_from_profile():
+def _traffic_from_profile(key="plain-fp64"):
     """DRAM bytes per launch of the dominant kernel from the committed ncu
     summary, if that summary was taken on the current kernel source."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -357,7 +479,7 @@ def _traffic_from_profile():
     try:
         with open(path) as f:
             d = json.load(f)
-        return d.get("plain-fp64")
+        return d.get(key)
     except (OSError, ValueError):
         return None
 
@@ -430,6 +552,20 @@ def run_profile_case(args):
     st = plan.status()
     if st != 0:
         raise RuntimeError(R.rsvd_status_string(st))
+    del dA, plan
+    # tcgen05 passes: A 16384 x 16384 BF16 (512 MB), l = 160
+    m = n = 16384
+    l = 160
+    dA = torch.randn(n, m, device="cuda").to(torch.bfloat16)
+    plan = R.Plan(m, n, l, a_dtype=R.BF16, mode=R.MIXED)
+    Xn = torch.randn(l, n, device="cuda").to(torch.bfloat16)
+    Y = torch.empty(l, m, dtype=torch.float32, device="cuda")
+    for _ in range(2):
+        R.rsvd_apply_a(plan.handle, dA, m, n, m, Xn, n, l, Y, m)
+        R.rsvd_apply_at(plan.handle, dA, m, n, m, Xn, m, l, Y, n)
+    st = plan.status()
+    if st != 0:
+        raise RuntimeError(R.rsvd_status_string(st))
     print("profile case done")
 
 
@@ -443,6 +579,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0,
                     help="seconds of CPU oracle time for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the mixed-precision (BF16) workload")
     ap.add_argument("--profile-case", action="store_true",
                     help="run a reduced case of the same kernels for ncu (no timing)")
     args = ap.parse_args()

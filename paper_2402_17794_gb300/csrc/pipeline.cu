@@ -82,6 +82,17 @@ int mixed_pass(rsvd_plan_t P, bool ax, const void* A, int64_t m, int64_t n, int6
   c.ldo = ldo;
   c.part = MW.apart;
   c.part_floats = MW.apart_floats;
+  rc = launch_apass_bf16(c, P->num_sms, &dstatus(P)->flags, P->stream);
+  if (rc != RSVD_ERR_UNSUPPORTED || slices == 1) return rc;
+  // the slices do not fit two shared-memory stages at this l: run the leading
+  // slices, then add the last slice's product in a second pass
+  c.slices = slices - 1;
+  c.x_cols = (slices - 1) * l16;
+  if ((rc = launch_apass_bf16(c, P->num_sms, &dstatus(P)->flags, P->stream))) return rc;
+  c.slices = 1;
+  c.X = MW.xcat + (size_t)(slices - 1) * l16 * ldx;
+  c.x_cols = l16;
+  c.accumulate = true;
   return launch_apass_bf16(c, P->num_sms, &dstatus(P)->flags, P->stream);
 }
 
@@ -133,8 +144,10 @@ Layout make_layout(int64_t m, int64_t n, int l, int mode, int num_sms) {
   L.qb = take((size_t)n * l * e);
   L.part = take((size_t)kPartSplits * mn * l * e);
   L.small_stride = align_up((size_t)l * l * e);
-  // G, R1, R1inv, R2, R2inv, Mt, Um, Vm, chol work, jacobi work (2 l x lpad), sig, sign
-  L.small = take(L.small_stride * 9 + align_up(2 * (size_t)l * lpad * e) + align_up(2 * (size_t)l * e));
+  // G, R1, R1inv, R2, R2inv, Mt, Um, Vm, jacobi work (2 l x lpad), sig, sign, chol work
+  L.small = take(L.small_stride * 8 + align_up(2 * (size_t)l * lpad * e) +
+                 align_up(2 * (size_t)l * e) +
+                 align_up(((size_t)l * l + 32 * (size_t)(l + 32)) * e));
   if (mode == RSVD_MODE_MIXED) {
     const int l16 = (l + 15) / 16 * 16;
     L.om16 = take((size_t)round8(mn) * 3 * l16 * sizeof(__nv_bfloat16));
@@ -168,11 +181,12 @@ Work<T> work_of(rsvd_plan_t P) {
   W.Mt = (T*)(s + 5 * st);
   W.Um = (T*)(s + 6 * st);
   W.Vm = (T*)(s + 7 * st);
-  W.cholw = (T*)(s + 8 * st);
-  W.jw = (T*)(s + 9 * st);
+  W.jw = (T*)(s + 8 * st);
   const int l = P->l_max, lpad = (l + 1) & ~1;
-  W.sig = (T*)(s + 9 * st + align_up(2 * (size_t)l * lpad * sizeof(T)));
+  const size_t jw_bytes = align_up(2 * (size_t)l * lpad * sizeof(T));
+  W.sig = (T*)(s + 8 * st + jw_bytes);
   W.sign = W.sig + l;
+  W.cholw = (T*)(s + 8 * st + jw_bytes + align_up(2 * (size_t)l * sizeof(T)));
   return W;
 }
 template Work<double> work_of<double>(rsvd_plan_t);

@@ -54,31 +54,41 @@ __device__ __forceinline__ void set_flag(DeviceStatus* s, int code) {
 }
 
 // G (ldg) -> R (ld l, upper; lower part zeroed), Rinv (ld l, upper).
-// `work` must hold l*l Ts (it may be shared memory or global).
+// W (l*l) and the 32 x (l + 32) scratch S live in dynamic shared memory when
+// they fit, else in `gwork` (l*l + 32*(l+32) elements).
+//
+// Cholesky: right-looking, one pivot per step, trailing update of the upper
+// triangle by a 32 x 32 thread grid.  Inverse (in place, LAPACK trtri's
+// block-column order with 32 x 32 blocks):
+//   1. every diagonal block D_b is inverted in parallel, one warp per block
+//      and one lane per column (back substitution against a copy of D_b);
+//   2. for block columns b = 1, 2, ...:  X(0:b, b) = -X(0:b, 0:b) R(0:b, b) X(b, b)
+//      as two small dense products over all threads.
 template <typename T>
 __global__ void __launch_bounds__(SMALL_THREADS)
 chol_inv_kernel(const T* __restrict__ G, int64_t ldg, int l, T* __restrict__ R,
                 T* __restrict__ Rinv, T* __restrict__ gwork, DeviceStatus* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* W = gwork ? gwork : reinterpret_cast<T*>(smem_raw);  // column-major l x l working copy
+  T* W = gwork ? gwork : reinterpret_cast<T*>(smem_raw);  // column-major l x l
+  T* S = W + (int64_t)l * l;                                  // 32 x (l + 32) scratch
   __shared__ T s_maxdiag;
-  __shared__ T s_r;
+  __shared__ T s_r, s_inv;
   __shared__ int s_bad;
   __shared__ int s_deficient;
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int tx = tid & 31, ty = tid >> 5;   // 32 x 32 grid
 
   for (int t = tid; t < l * l; t += nt) {
     int i = t % l, j = t / l;
-    W[t] = (i <= j) ? G[i + (int64_t)j * ldg] : 0.0;
+    W[t] = (i <= j) ? G[i + (int64_t)j * ldg] : T(0);
   }
   if (tid == 0) {
-    s_maxdiag = 0.0;
     s_bad = 0;
     s_deficient = 0;
   }
   __syncthreads();
   if (tid == 0) {
-    T mx = 0.0;
+    T mx = T(0);
     int bad = 0;
     for (int j = 0; j < l; ++j) {
       T d = W[j + j * l];
@@ -91,77 +101,101 @@ chol_inv_kernel(const T* __restrict__ G, int64_t ldg, int l, T* __restrict__ R,
   __syncthreads();
   if (s_bad) {
     for (int t = tid; t < l * l; t += nt) {
-      R[t] = 0.0;
-      Rinv[t] = 0.0;
+      R[t] = T(0);
+      Rinv[t] = T(0);
     }
     if (tid == 0) set_flag(status, RSVD_ERR_NONFINITE);
     return;
   }
   const T tol = Eps<T>::drop_factor(l) * Eps<T>::value * s_maxdiag;
 
-  // Right-looking Cholesky on the upper triangle: G = R^T R.
+  // ---- Cholesky: G = R^T R on the upper triangle ----
   for (int j = 0; j < l; ++j) {
     if (tid == 0) {
-      T d = W[j + j * l];
+      const T d = W[j + j * l];
       if (!(d > tol)) {
         s_r = T(0);  // dropped column
+        s_inv = T(0);
         s_deficient++;
       } else {
         s_r = sqrt(d);
+        s_inv = T(1) / s_r;
       }
     }
     __syncthreads();
-    const T r = s_r;
-    if (r == 0.0) {
-      for (int c = j + tid; c < l; c += nt) W[j + c * l] = 0.0;
-      __syncthreads();
-      continue;
-    }
-    const T inv = T(1) / r;
+    const T r = s_r, inv = s_inv;
+    // row j of R: W[j][c] * inv for c > j (zero for a dropped column)
     for (int c = j + 1 + tid; c < l; c += nt) W[j + c * l] *= inv;
     if (tid == 0) W[j + j * l] = r;
     __syncthreads();
-    // trailing update of the upper triangle: W[i][c] -= R[j][i] R[j][c], j < i <= c
-    const int rem = l - j - 1;
-    for (int t = tid; t < rem * rem; t += nt) {
-      const int ii = t % rem, cc = t / rem;
-      if (ii <= cc) {
-        const int i = j + 1 + ii, c = j + 1 + cc;
-        W[i + c * l] -= W[j + i * l] * W[j + c * l];
+    if (r != T(0)) {
+      // W[i][c] -= R[j][i] R[j][c] for j < i <= c
+      for (int c = j + 1 + ty; c < l; c += 32) {
+        const T rjc = W[j + c * l];
+        for (int i = j + 1 + tx; i <= c; i += 32) W[i + c * l] -= W[j + i * l] * rjc;
       }
     }
     __syncthreads();
   }
-  // R out
   for (int t = tid; t < l * l; t += nt) {
     int i = t % l, j = t / l;
-    R[t] = (i <= j) ? W[t] : 0.0;
+    R[t] = (i <= j) ? W[t] : T(0);
   }
   __syncthreads();
-  // In-place inverse of the upper triangular W (column by column):
-  // for column j: Winv[j][j] = 1/R[j][j];  Winv[0:j, j] = -Winv[j][j] * Winv[0:j,0:j] R[0:j, j]
-  for (int j = 0; j < l; ++j) {
-    const T rjj = W[j + j * l];
-    if (rjj == 0.0) {
-      for (int i = tid; i <= j; i += nt) W[i + j * l] = 0.0;
-      __syncthreads();
-      continue;
+
+  // ---- Inverse, step 1: diagonal 32 x 32 blocks, one warp each ----
+  const int nb = (l + 31) / 32;
+  // copy every diagonal block to S (block b at S + b*1024, column-major 32 x 32)
+  for (int t = tid; t < nb * 1024; t += nt) {
+    const int b = t >> 10, e = t & 1023, i = e & 31, c = e >> 5;
+    const int gi = b * 32 + i, gc = b * 32 + c;
+    S[t] = (gi < l && gc < l) ? W[gi + gc * l] : T(0);
+  }
+  __syncthreads();
+  for (int b = ty; b < nb; b += 32) {
+    const int c = tx, gc = b * 32 + c;
+    const T* D = S + b * 1024;
+    if (gc < l) {
+      const T dcc = D[c + c * 32];
+      if (dcc == T(0)) {
+        for (int i = 0; i <= c; ++i) W[b * 32 + i + gc * l] = T(0);
+      } else {
+        W[gc + gc * l] = T(1) / dcc;
+        for (int i = c - 1; i >= 0; --i) {
+          const T dii = D[i + i * 32];
+          T acc = T(0);
+          for (int t2 = i + 1; t2 <= c; ++t2) acc = fma(D[i + t2 * 32], W[b * 32 + t2 + gc * l], acc);
+          W[b * 32 + i + gc * l] = (dii == T(0)) ? T(0) : -acc / dii;
+        }
+      }
     }
-    const T ajj = T(1) / rjj;
-    // x_i = sum_{t=i}^{j-1} Winv[i][t] * R[t][j], for i < j (uses columns < j, already inverted)
-    T x = 0.0;
-    const int i = tid;
-    if (i < j) {
-      for (int t = i; t < j; ++t) x = fma(W[i + t * l], W[t + j * l], x);
+  }
+  __syncthreads();
+
+  // ---- Inverse, step 2: block columns left to right ----
+  for (int bj = 1; bj < nb; ++bj) {
+    const int c0 = bj * 32, cw = min(32, l - c0);
+    const int rows = c0;  // rows 0 .. c0-1
+    // (a) S(r, c) = sum_{u=r}^{c0-1} X[r][u] R[u][c0+c]   (X upper, already final)
+    for (int t = tid; t < rows * cw; t += nt) {
+      const int r = t % rows, c = t / rows;
+      T acc = T(0);
+      for (int u = r; u < c0; ++u) acc = fma(W[r + u * l], W[u + (c0 + c) * l], acc);
+      S[r + c * rows] = acc;
     }
     __syncthreads();
-    if (i < j) W[i + j * l] = -ajj * x;
-    if (tid == 0) W[j + j * l] = ajj;
+    // (b) X[r][c0+c] = - sum_{s=0}^{c} S(r, s) X[c0+s][c0+c]
+    for (int t = tid; t < rows * cw; t += nt) {
+      const int r = t % rows, c = t / rows;
+      T acc = T(0);
+      for (int s2 = 0; s2 <= c; ++s2) acc = fma(S[r + s2 * rows], W[c0 + s2 + (c0 + c) * l], acc);
+      W[r + (c0 + c) * l] = -acc;
+    }
     __syncthreads();
   }
   for (int t = tid; t < l * l; t += nt) {
     int i = t % l, j = t / l;
-    Rinv[t] = (i <= j) ? W[t] : 0.0;
+    Rinv[t] = (i <= j) ? W[t] : T(0);
   }
   if (tid == 0 && s_deficient) atomicAdd(&status->deficient, s_deficient);
 }
@@ -413,7 +447,7 @@ __global__ void vt_kernel(const T* __restrict__ Vk, int64_t n, int k,
 template <typename T>
 cudaError_t launch_chol_inv(const T* G, int64_t ldg, int l, T* R, T* Rinv, T* work,
                             DeviceStatus* status, cudaStream_t st) {
-  const size_t smem = (size_t)l * l * sizeof(T);
+  const size_t smem = ((size_t)l * l + 32 * (size_t)(l + 32)) * sizeof(T);
   const size_t cap = 200 * 1024;
   static bool attr_set = false;
   if (!attr_set) {

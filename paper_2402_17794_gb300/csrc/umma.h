@@ -19,13 +19,15 @@ struct ApassCall {
   int64_t ldo;
   float* part;          // partial slots
   size_t part_floats;
+  bool accumulate = false;  // out += A X instead of out = A X
 };
 
 // Floats of partial-slot workspace a pass with `l` output columns needs.
 size_t apass_partial_floats(int num_sms, int l);
 
 // Enqueues the pass (main kernel + split-tile fixup).  Returns RSVD_OK or a
-// positive RSVD_ERR_* code (unsupported alignment/shape, workspace, CUDA).
+// positive RSVD_ERR_* code (unsupported alignment/shape -- including operand
+// slices too wide for two shared-memory stages --, workspace, CUDA).
 int launch_apass_bf16(const ApassCall& c, int num_sms, int* status, cudaStream_t st);
 
 }  // namespace rsvd

@@ -182,18 +182,16 @@ struct ApassArgs {
   int64_t rows_out;   // output rows (m for AX, n for ATX)
   int64_t total;      // tiles * kt iterations
   int kt;             // k-blocks per tile
-  int parts;          // MMA N-parts
-  int nb;             // columns per part (multiple of 16, <= 256)
   int slices;         // operand slices accumulated into D
   int slice_stride;   // columns between slices in the operand
-  int l16;            // operand columns per slice in shared memory (l rounded up to 16)
+  int l16;            // MMA N: output columns rounded up to 16 (<= 256)
   int l;              // output columns
   int stages;
   uint32_t tmem_cols;
-  uint32_t lbo_mn, sbo_mn;  // descriptor offsets of the MN-major A layout
   float* out;
   int64_t ldo;
-  float* part;        // partial slots, gridDim.x * 2 * BM * l floats
+  float* part;        // partial slots, gridDim.x * 2 * (MT*128) * l floats
+  int accumulate;     // 1: out += result, 0: out = result
   int* status;
 };
 
@@ -201,12 +199,17 @@ __device__ __forceinline__ int64_t range_begin(int64_t total, int c, int g) {
   return (int64_t)((__int128)total * c / g);
 }
 
-template <bool AX>
+// MT: 128-row M sub-tiles per CTA tile (each with its own TMEM accumulator of
+// l16 columns); they share every X stage, so X is fetched once per MT*128
+// rows of A.
+template <bool AX, int MT>
 __global__ void __launch_bounds__(THREADS, 1)
 apass_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX,
                   const ApassArgs args) {
+  constexpr int BMT = BM * MT;
+  constexpr int A_BYTES = A_STAGE_BYTES * MT;
   extern __shared__ uint8_t smem_raw[];
-  // carve: barriers first, then 1024-aligned tiles
+  // carve: barriers first, then 1024-aligned stages
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
   uint64_t* empty = full + args.stages;
   uint64_t* acc_full = empty + args.stages;
@@ -217,7 +220,7 @@ apass_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   const uint32_t tiles_off = ((raw + 256 + 1023) & ~1023u) - raw;
   uint8_t* tiles = smem_raw + tiles_off;
   const int x_stage_bytes = args.slices * args.l16 * 128;
-  const int stage_bytes = A_STAGE_BYTES + x_stage_bytes;
+  const int stage_bytes = A_BYTES + x_stage_bytes;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t g0 = range_begin(args.total, blockIdx.x, gridDim.x);
@@ -246,31 +249,33 @@ apass_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   if (warp == 0) {
     // ---------------- TMA producer ----------------
     if (lane == 0) {
-      int64_t it = 0;
-      for (int64_t g = g0; g < g1; ++g, ++it) {
-        const int s = (int)(it % args.stages);
-        const uint32_t ph = (uint32_t)((it / args.stages) & 1);
+      int s = 0;
+      uint32_t ph = 0;
+      int64_t t = g0 / args.kt;
+      int kb = (int)(g0 - t * args.kt);
+      int64_t issued = 0;
+      for (int64_t g = g0; g < g1; ++g) {
         if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) break;
-        const int64_t t = g / args.kt;
-        const int kb = (int)(g - t * args.kt);
         uint8_t* a_s = tiles + (size_t)s * stage_bytes;
-        uint8_t* x_s = a_s + A_STAGE_BYTES;
+        uint8_t* x_s = a_s + A_BYTES;
         mbar_expect_tx(&full[s], (uint32_t)stage_bytes);
-        if (AX) {
-          tma_load_2d(&tmA, &full[s], a_s, (int)(t * BM), kb * BK);
-          tma_load_2d(&tmA, &full[s], a_s + A_STAGE_BYTES / 2, (int)(t * BM + 64), kb * BK);
-        } else {
-          tma_load_2d(&tmA, &full[s], a_s, kb * BK, (int)(t * BM));
-          tma_load_2d(&tmA, &full[s], a_s + A_STAGE_BYTES / 2, kb * BK, (int)(t * BM + 64));
+#pragma unroll
+        for (int h = 0; h < 2 * MT; ++h) {  // 64-row boxes of the A tile
+          if (AX)
+            tma_load_2d(&tmA, &full[s], a_s + h * (A_STAGE_BYTES / 2), (int)(t * BMT + h * 64),
+                        kb * BK);
+          else
+            tma_load_2d(&tmA, &full[s], a_s + h * (A_STAGE_BYTES / 2), kb * BK,
+                        (int)(t * BMT + h * 64));
         }
         for (int sl = 0; sl < args.slices; ++sl)
-          for (int p = 0; p < args.parts; ++p)
-            tma_load_2d(&tmX, &full[s], x_s + (sl * args.l16 + p * args.nb) * 128, kb * BK,
-                        sl * args.slice_stride + p * args.nb);
+          tma_load_2d(&tmX, &full[s], x_s + sl * args.l16 * 128, kb * BK, sl * args.slice_stride);
+        ++issued;
+        if (++s == args.stages) { s = 0; ph ^= 1u; }
+        if (++kb == args.kt) { kb = 0; ++t; }
       }
       // on abort: wait (bounded) for the loads already issued to land
       if (*abort_flag) {
-        int64_t issued = it;
         for (int64_t j = (issued > args.stages ? issued - args.stages : 0); j < issued; ++j) {
           long long t0 = clock64();
           while (!mbar_try_wait(&full[j % args.stages], (uint32_t)((j / args.stages) & 1)) &&
@@ -282,15 +287,18 @@ apass_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      const uint32_t idesc = idesc_bf16(BM, args.nb, AX);
-      int64_t it = 0;
+      const uint32_t idesc = idesc_bf16(BM, args.l16, AX);
+      const uint32_t tiles_base = smem_u32(tiles);
+      // descriptor start-address steps (in 16-byte units) per 16-wide K step
+      constexpr uint64_t a_kstep = AX ? (2048 >> 4) : (32 >> 4);
+      constexpr uint64_t b_kstep = 32 >> 4;
+      int s = 0;
+      uint32_t ph = 0;
+      int64_t t = g0 / args.kt;
+      int kb = (int)(g0 - t * args.kt);
       int seg = 0;
       bool ok = true;
-      for (int64_t g = g0; g < g1 && ok; ++g, ++it) {
-        const int s = (int)(it % args.stages);
-        const uint32_t ph = (uint32_t)((it / args.stages) & 1);
-        const int64_t t = g / args.kt;
-        const int kb = (int)(g - t * args.kt);
+      for (int64_t g = g0; g < g1; ++g) {
         const bool seg_first = (g == g0) || kb == 0;
         const bool seg_last = (g == g1 - 1) || kb == args.kt - 1;
         if (seg_first && seg > 0) {
@@ -300,28 +308,31 @@ apass_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         }
         if (!mbar_wait(&full[s], ph, abort_flag)) { ok = false; break; }
         tc_fence_after();
-        const uint32_t a_base = smem_u32(tiles + (size_t)s * stage_bytes);
-        const uint32_t x_base = a_base + A_STAGE_BYTES;
+        const uint32_t a_base = tiles_base + (uint32_t)s * (uint32_t)stage_bytes;
+        const uint32_t x_base = a_base + A_BYTES;
+        // MN-major A (AX): two 64-element MN atoms per sub-tile, 64 K-rows of
+        // 128 bytes each: leading offset BK*128 bytes, 8-row K groups 1024 apart.
+        // K-major A (ATX): rows of 128 bytes, 8-row groups 1024 bytes apart.
+        const uint64_t bd0 = sdesc(x_base, 16, 1024);
+        for (int sl = 0; sl < args.slices; ++sl) {
+          const uint64_t bd = bd0 + (uint64_t)((sl * args.l16 * 128) >> 4);
 #pragma unroll
-        for (int kk = 0; kk < BK / 16; ++kk) {
-          uint64_t adesc;
-          if (AX)  // MN-major A: 2 atoms of 64 rows (LBO apart), K groups of 8 (SBO apart)
-            adesc = sdesc(a_base + kk * 2048, args.lbo_mn, args.sbo_mn);
-          else     // K-major A: rows of 128 bytes, 8-row groups 1024 bytes apart
-            adesc = sdesc(a_base + kk * 32, 16, 1024);
-          for (int sl = 0; sl < args.slices; ++sl)
-            for (int p = 0; p < args.parts; ++p) {
-              const uint64_t bdesc =
-                  sdesc(x_base + (sl * args.l16 + p * args.nb) * 128 + kk * 32, 16, 1024);
-              umma_bf16(tmem_base + p * args.nb, adesc, bdesc, idesc,
+          for (int h = 0; h < MT; ++h) {
+            const uint32_t ah = a_base + h * A_STAGE_BYTES;
+            const uint64_t ad = AX ? sdesc(ah, BK * 128, 1024) : sdesc(ah, 16, 1024);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk)
+              umma_bf16(tmem_base + h * args.l16, ad + kk * a_kstep, bd + kk * b_kstep, idesc,
                         (seg_first && kk == 0 && sl == 0) ? 0u : 1u);
-            }
+          }
         }
         umma_commit(&empty[s]);           // stage reusable once these MMAs finish
         if (seg_last) {
-          umma_commit(acc_full);          // accumulator ready for the epilogue
+          umma_commit(acc_full);          // accumulators ready for the epilogue
           ++seg;
         }
+        if (++s == args.stages) { s = 0; ph ^= 1u; }
+        if (++kb == args.kt) { kb = 0; ++t; }
       }
       if (!ok) {
         // drain: one more commit tracks every MMA issued so far; wait for it
@@ -335,7 +346,7 @@ apass_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   } else {
     // ---------------- epilogue (warps 2..5) ----------------
     const int quad = warp & 3;            // TMEM lane quadrant this warp may access
-    const int row_in_tile = quad * 32 + lane;
+    const uint32_t lane_base = tmem_base + ((uint32_t)(quad * 32) << 16);
     int seg = 0;
     int64_t g = g0;
     while (g < g1) {
@@ -347,27 +358,34 @@ apass_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       tc_fence_after();
       float* dst;
       int64_t ld;
-      int64_t row;
+      int64_t row0;
       if (full_tile) {
-        row = t * BM + row_in_tile;
+        row0 = t * BMT;
         dst = args.out;
         ld = args.ldo;
       } else {
         const int slot = (g == g0) ? 0 : 1;
-        row = row_in_tile;
-        dst = args.part + ((size_t)blockIdx.x * 2 + slot) * (size_t)BM * args.l;
-        ld = BM;
+        row0 = 0;
+        dst = args.part + ((size_t)blockIdx.x * 2 + slot) * (size_t)BMT * args.l;
+        ld = BMT;
       }
-      const bool row_ok = full_tile ? (row < args.rows_out) : true;
-      const uint32_t lane_base = tmem_base + ((uint32_t)(quad * 32) << 16);
-      for (int c0 = 0; c0 < args.l; c0 += 16) {
-        uint32_t r[16];
-        tmem_ld16(lane_base + (uint32_t)c0, r);
-        tmem_wait_ld();
-        if (row_ok) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            if (c0 + j < args.l) dst[row + (int64_t)(c0 + j) * ld] = __uint_as_float(r[j]);
+      for (int h = 0; h < MT; ++h) {
+        const int64_t row = row0 + h * BM + quad * 32 + lane;
+        const bool row_ok = full_tile ? (row < args.rows_out) : true;
+        const bool acc_out = full_tile && args.accumulate;
+        for (int c0 = 0; c0 < args.l; c0 += 16) {
+          uint32_t r[16];
+          tmem_ld16(lane_base + (uint32_t)(h * args.l16 + c0), r);
+          tmem_wait_ld();
+          if (row_ok) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (c0 + j < args.l) {
+                float* d = dst + row + (int64_t)(c0 + j) * ld;
+                *d = acc_out ? *d + __uint_as_float(r[j]) : __uint_as_float(r[j]);
+              }
+          }
         }
       }
       tc_fence_before();
@@ -388,31 +406,50 @@ apass_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
 
 // Sums the per-CTA partials of every tile whose k-range was split, in CTA
 // order.  One block per tile; tiles written whole by one CTA are skipped.
+// The (at most a few) CTA boundaries touching the tile are resolved once per
+// block, then every thread sums its elements.
 __global__ void apass_fixup_kernel(const float* __restrict__ part, int grid, int64_t total, int kt,
-                                   int l, int64_t rows_out, float* __restrict__ out, int64_t ldo) {
-  auto begin = [&](int c) { return (int64_t)((__int128)total * c / grid); };
-  auto cta_of = [&](int64_t g) {
-    int c = (int)((__int128)g * grid / total);
-    while (c + 1 < grid && begin(c + 1) <= g) ++c;
-    while (c > 0 && begin(c) > g) --c;
-    return c;
-  };
+                                   int bmt, int l, int64_t rows_out, float* __restrict__ out,
+                                   int64_t ldo, int accumulate) {
+  constexpr int kMaxShare = 32;
+  __shared__ int s_cta[kMaxShare];
+  __shared__ int s_slot[kMaxShare];
+  __shared__ int s_n;
   const int64_t t = blockIdx.x;
-  const int cf = cta_of(t * kt), cl = cta_of((t + 1) * kt - 1);
-  if (cf == cl) return;  // written directly by one CTA
-  const int64_t per_tile = (int64_t)BM * l;
+  if (threadIdx.x == 0) {
+    auto begin = [&](int c) { return (int64_t)((__int128)total * c / grid); };
+    auto cta_of = [&](int64_t g) {
+      int c = (int)((__int128)g * grid / total);
+      while (c + 1 < grid && begin(c + 1) <= g) ++c;
+      while (c > 0 && begin(c) > g) --c;
+      return c;
+    };
+    const int cf = cta_of(t * kt), cl = cta_of((t + 1) * kt - 1);
+    int n = 0;
+    if (cf != cl) {
+      for (int cc = cf; cc <= cl && n < kMaxShare; ++cc) {
+        const int64_t b = begin(cc);
+        if (b >= begin(cc + 1)) continue;
+        s_cta[n] = cc;
+        s_slot[n] = (b / kt == t) ? 0 : 1;
+        ++n;
+      }
+    }
+    s_n = n;
+  }
+  __syncthreads();
+  const int n = s_n;
+  if (n == 0) return;  // written directly by one CTA
+  const int64_t per_tile = (int64_t)bmt * l;
   for (int64_t idx = threadIdx.x; idx < per_tile; idx += blockDim.x) {
-    const int c = (int)(idx / BM), r = (int)(idx % BM);
-    const int64_t row = t * BM + r;
+    const int c = (int)(idx / bmt), r = (int)(idx % bmt);
+    const int64_t row = t * bmt + r;
     if (row >= rows_out) continue;
     float s = 0.f;
-    for (int cc = cf; cc <= cl; ++cc) {
-      const int64_t b = begin(cc);
-      if (b >= begin(cc + 1)) continue;
-      const int slot = (b / kt == t) ? 0 : 1;
-      s += part[((size_t)cc * 2 + slot) * per_tile + (size_t)c * BM + r];
-    }
-    out[row + (int64_t)c * ldo] = s;
+    for (int j = 0; j < n; ++j)
+      s += part[((size_t)s_cta[j] * 2 + s_slot[j]) * per_tile + (size_t)c * bmt + r];
+    float* d = out + row + (int64_t)c * ldo;
+    *d = accumulate ? *d + s : s;
   }
 }
 
@@ -447,15 +484,9 @@ bool make_map_bf16(CUtensorMap* map, const void* base, int64_t rows, int64_t col
   return r == CUDA_SUCCESS;
 }
 
-// MN-major A (the Y = A X pass): the stage holds two 64-row boxes of the A
-// tile (64 K-rows of 128 bytes each); the leading byte offset steps between
-// the two 64-element MN atoms (one box, 64 x 128 bytes apart) and the stride
-// byte offset between 8-row K groups (1024 bytes).
-constexpr uint32_t kLboMn = BK * 128, kSboMn = 1024;
-
 }  // namespace
 
-size_t apass_partial_floats(int num_sms, int l) { return (size_t)num_sms * 2 * BM * l; }
+size_t apass_partial_floats(int num_sms, int l) { return (size_t)num_sms * 2 * (2 * BM) * l; }
 
 int launch_apass_bf16(const ApassCall& c, int num_sms, int* status, cudaStream_t st) {
   // shape checks (host-side; the kernel assumes them)
@@ -466,15 +497,16 @@ int launch_apass_bf16(const ApassCall& c, int num_sms, int* status, cudaStream_t
   const int l16 = (c.l + 15) / 16 * 16;
   if (c.l < 1 || c.l > 256 || c.slices < 1 || c.slices > 3) return RSVD_ERR_UNSUPPORTED;
   if (c.slice_stride < l16 && c.slices > 1) return RSVD_ERR_UNSUPPORTED;
-  // N per MMA: one part for l16 <= 256 (the instruction's limit)
-  const int parts = 1;
-  const int nb = l16;
+  // two 128-row sub-tiles per CTA tile when the output has the rows and TMEM
+  // holds both accumulators
+  const int mt = (rows_out > BM && 2 * l16 <= 512) ? 2 : 1;
+  const int bmt = BM * mt;
   uint32_t tmem_cols = 32;
-  while (tmem_cols < (uint32_t)l16) tmem_cols <<= 1;
-  const int64_t tiles = (rows_out + BM - 1) / BM;
+  while (tmem_cols < (uint32_t)(mt * l16)) tmem_cols <<= 1;
+  const int64_t tiles = (rows_out + bmt - 1) / bmt;
   const int kt = (int)((kdim + BK - 1) / BK);
   const int64_t total = tiles * kt;
-  const int stage_bytes = A_STAGE_BYTES + c.slices * l16 * 128;
+  const int stage_bytes = A_STAGE_BYTES * mt + c.slices * l16 * 128;
   const int smem_cap = 227 * 1024;
   int stages = (smem_cap - 2048) / stage_bytes;
   stages = std::min(stages, 8);
@@ -484,41 +516,46 @@ int launch_apass_bf16(const ApassCall& c, int num_sms, int* status, cudaStream_t
   CUtensorMap tmA, tmX;
   // A: rows x cols = m x n; X: (kdim) x (operand columns) with ld ldx
   if (!make_map_bf16(&tmA, c.A, c.m, c.n, c.lda, 64, 64)) return RSVD_ERR_CUDA;
-  if (!make_map_bf16(&tmX, c.X, kdim, c.x_cols, c.ldx, 64, nb)) return RSVD_ERR_CUDA;
+  if (!make_map_bf16(&tmX, c.X, kdim, c.x_cols, c.ldx, 64, l16)) return RSVD_ERR_CUDA;
 
-  int grid = (int)std::min<int64_t>(num_sms, total);
+  // every CTA gets a non-empty range, and no tile is shared by more CTAs than
+  // the fixup kernel resolves
+  int grid = (int)std::min<int64_t>(std::min<int64_t>(num_sms, total), tiles * 30);
   ApassArgs a;
   a.rows_out = rows_out;
   a.total = total;
   a.kt = kt;
-  a.parts = parts;
-  a.nb = nb;
   a.slices = c.slices;
   a.slice_stride = c.slice_stride;
   a.l16 = l16;
   a.l = c.l;
   a.stages = stages;
   a.tmem_cols = tmem_cols;
-  a.lbo_mn = kLboMn;
-  a.sbo_mn = kSboMn;
   a.out = c.out;
   a.ldo = c.ldo;
   a.part = c.part;
+  a.accumulate = c.accumulate ? 1 : 0;
   a.status = status;
-  if (c.part_floats < apass_partial_floats(grid, c.l)) return RSVD_ERR_WORKSPACE;
+  if (c.part_floats < (size_t)grid * 2 * bmt * c.l) return RSVD_ERR_WORKSPACE;
+  if ((int64_t)kt * grid / total + 2 > 32) return RSVD_ERR_UNSUPPORTED;
+#define RSVD_LAUNCH_APASS(AXV, MTV)                                                          \
+  do {                                                                                       \
+    cudaFuncSetAttribute(apass_bf16_kernel<AXV, MTV>,                                        \
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);            \
+    apass_bf16_kernel<AXV, MTV><<<grid, THREADS, smem, st>>>(tmA, tmX, a);                   \
+  } while (0)
   if (c.ax) {
-    cudaFuncSetAttribute(apass_bf16_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    apass_bf16_kernel<true><<<grid, THREADS, smem, st>>>(tmA, tmX, a);
+    if (mt == 2) RSVD_LAUNCH_APASS(true, 2);
+    else RSVD_LAUNCH_APASS(true, 1);
   } else {
-    cudaFuncSetAttribute(apass_bf16_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    apass_bf16_kernel<false><<<grid, THREADS, smem, st>>>(tmA, tmX, a);
+    if (mt == 2) RSVD_LAUNCH_APASS(false, 2);
+    else RSVD_LAUNCH_APASS(false, 1);
   }
+#undef RSVD_LAUNCH_APASS
   note_launch();
   if (cudaGetLastError() != cudaSuccess) return RSVD_ERR_CUDA;
-  apass_fixup_kernel<<<(unsigned)tiles, 256, 0, st>>>(c.part, grid, total, kt, c.l, rows_out,
-                                                       c.out, c.ldo);
+  apass_fixup_kernel<<<(unsigned)tiles, 256, 0, st>>>(c.part, grid, total, kt, bmt, c.l, rows_out,
+                                                       c.out, c.ldo, a.accumulate);
   note_launch();
   if (cudaGetLastError() != cudaSuccess) return RSVD_ERR_CUDA;
   return RSVD_OK;

@@ -145,8 +145,8 @@ def lowrank_matrix_torch(m: int, n: int, sigma: np.ndarray, seed: int, *,
 
     ``factor_dtype`` (default float64) is the precision of the Haar factors
     and of the product; ``dtype`` the stored type of A (default float64).
-    Gaussians are drawn on the CPU from a seeded torch Generator so the
-    matrix does not depend on the device's random number generator.
+    The Gaussians of the Haar factors are drawn on the CPU from a seeded
+    torch Generator; the noise floor, if any, from a seeded device Generator.
     """
     import torch
 
@@ -172,13 +172,15 @@ def lowrank_matrix_torch(m: int, n: int, sigma: np.ndarray, seed: int, *,
     at = (v * s) @ u.T
     del u, v
     if noise_2norm > 0.0:
-        g = torch.Generator(device="cpu")
+        # the noise floor is drawn on the device (seeded); at 10^9 entries a
+        # host draw would dominate the set-up time
+        g = torch.Generator(device=device)
         g.manual_seed((int(seed) * 1000003 + _STREAM_NOISE) & 0x7FFFFFFFFFFFFFFF)
         scale = noise_2norm / (np.sqrt(m) + np.sqrt(n))
         for j0 in range(0, n, 1024):
             j1 = min(n, j0 + 1024)
-            e = torch.randn(j1 - j0, m, generator=g, dtype=torch.float32)
-            at[j0:j1] += (scale * e).to(device=device, dtype=factor_dtype)
+            e = torch.randn(j1 - j0, m, generator=g, dtype=torch.float32, device=device)
+            at[j0:j1] += (scale * e).to(factor_dtype)
     out = torch.zeros(n, lda, dtype=dtype, device=device)
     out[:, :m] = at.to(dtype)
     return out
