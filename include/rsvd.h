@@ -223,6 +223,35 @@ int rsvd_orth(rsvd_plan_t plan, const void* Y, int64_t rows, int l, int64_t ldy,
 int rsvd_small_svd(rsvd_plan_t plan, const void* M, int l, int64_t ldm,
                    void* sig, void* Um, int64_t ldu, void* Vm, int64_t ldv);
 
+/* ---------------------------------------------------------------------- */
+/* Allocation-free entry point                                             */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * rsvd_apply_a_f64_static: Y = A X in FP64 (the product of
+ * rsvd_apply_a on a plain plan) for callers that may not allocate device
+ * memory -- for instance code running inside a host framework that owns all
+ * device memory and forbids allocation during the call, or a section that
+ * was handed only its inputs and outputs -- and so cannot own a plan
+ * workspace.  The thesis has no counterpart; this is a deployment aid.
+ *   A  m x n (lda >= m), X n x l (ldx >= n), Y m x l (ldy >= m): device FP64.
+ *   cuda_stream: the cudaStream_t the work is enqueued on (NULL = default).
+ * The split-K partial sums live in one fixed device array built into the
+ * library (32 MiB, 4 Mi doubles), held by every GPU that loads the library
+ * until the process exits.  Limit: m * l <= 4 Mi (4194304); larger sizes
+ * return RSVD_ERR_WORKSPACE without touching Y.  The call allocates nothing
+ * (no cudaMalloc, no library allocator).  All calls share the array, so
+ * calls that overlap on the GPU (other streams, other host threads) race;
+ * the array needs no clearing (each call writes every element it reads).
+ * The first call on a device looks up the array's device address for that
+ * device, so make it before any stream capture.
+ * Errors: -1 A NULL; -2 m; -3 n; -4 lda; -5 X NULL; -6 ldx; -7 l; -8 Y NULL;
+ * -9 ldy; RSVD_ERR_CUDA if a CUDA call fails.
+ */
+int rsvd_apply_a_f64_static(const double* A, int64_t m, int64_t n, int64_t lda,
+                            const double* X, int64_t ldx, int l, double* Y, int64_t ldy,
+                            void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

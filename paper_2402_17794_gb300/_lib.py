@@ -38,6 +38,8 @@ SIGNATURES = {
                           P_double, c_int64]),
     "rsvd_small_svd": (c_int, [c_void_p, P_double, c_int, c_int64, P_double, P_double, c_int64,
                                P_double, c_int64]),
+    "rsvd_apply_a_f64_static": (c_int, [c_void_p, c_int64, c_int64, c_int64, c_void_p, c_int64,
+                                        c_int, c_void_p, c_int64, c_void_p]),
 }
 
 _LIB = None

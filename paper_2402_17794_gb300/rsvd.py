@@ -146,6 +146,11 @@ def rsvd_small_svd(plan, M, l, ldm, sig, Um, ldu, Vm, ldv) -> int:
                                       ldv)
 
 
+def rsvd_apply_a_f64_static(A, m, n, lda, X, ldx, l, Y, ldy, stream=None) -> int:
+    return _lib.load().rsvd_apply_a_f64_static(_ptr(A), m, n, lda, _ptr(X), ldx, l, _ptr(Y), ldy,
+                                               _stream_handle(stream))
+
+
 # ---------------------------------------------------------------------------
 # Convenience wrapper
 # ---------------------------------------------------------------------------
