@@ -59,8 +59,12 @@ namespace rsvd {
 
 // ---- kernels' host launchers (all enqueue on `st`) ----
 
-// Omega (n x l) for (seed, stream): FP64, FP32 or BF16 output.
+// Omega (n x l) for (seed, stream): FP64, FP32 or BF16 output, each rounded
+// from the FP64 value.  kOutF32Fast (internal, mixed path): FP32 Box-Muller on
+// 24-bit uniforms from the same Philox words (the FP64 transcendental
+// functions run at the FP64 rate, 1/64 of FP32 on this GPU).
 constexpr int kOutF32 = RSVD_F32;
+constexpr int kOutF32Fast = 101;
 cudaError_t launch_gaussian(int64_t n, int l, uint64_t seed, uint32_t stream_id,
                             int out_dtype, void* out, int64_t ldo, cudaStream_t st);
 
@@ -80,7 +84,8 @@ cudaError_t launch_gemm(const GemmArgs<T>& g, T* part, size_t part_elems, int nu
 
 // One-CTA Cholesky of the l x l Gram G (ldg) -> upper R (l x l, ld l) and
 // its inverse Rinv (ld l); deficient pivots zero the row of R and the row and
-// column of Rinv.  Sets status bits on non-finite input.  work: l*l elements.
+// column of Rinv.  Sets status bits on non-finite input.  work: l*l + 33*(l+64)
+// elements (used when that does not fit in shared memory).
 template <typename T>
 cudaError_t launch_chol_inv(const T* G, int64_t ldg, int l, T* R, T* Rinv, T* work,
                             DeviceStatus* status, cudaStream_t st);

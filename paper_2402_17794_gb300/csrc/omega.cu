@@ -32,9 +32,12 @@ __device__ __forceinline__ double uniform52(uint32_t wa, uint32_t wb) {
   return ((double)x + 0.5) * 0x1p-52;
 }
 
-__device__ __forceinline__ double gaussian_at(uint64_t t, uint32_t stream, uint32_t k0,
-                                              uint32_t k1) {
-  uint32_t c0 = (uint32_t)t, c1 = (uint32_t)(t >> 32), c2 = stream, c3 = 0;
+__device__ __forceinline__ void philox10(uint64_t t, uint32_t stream, uint32_t k0, uint32_t k1,
+                                         uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t& c3) {
+  c0 = (uint32_t)t;
+  c1 = (uint32_t)(t >> 32);
+  c2 = stream;
+  c3 = 0;
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
     if (r) {
@@ -43,9 +46,35 @@ __device__ __forceinline__ double gaussian_at(uint64_t t, uint32_t stream, uint3
     }
     philox_round(c0, c1, c2, c3, k0, k1);
   }
+}
+
+__device__ __forceinline__ double gaussian_at(uint64_t t, uint32_t stream, uint32_t k0,
+                                              uint32_t k1) {
+  uint32_t c0, c1, c2, c3;
+  philox10(t, stream, k0, k1, c0, c1, c2, c3);
   double u1 = uniform52(c0, c1);
   double u2 = uniform52(c2, c3);
   return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+}
+
+// FP32 Box-Muller on u = (w >> 8 + 1/2) 2^-24 from words 0 and 2.
+__device__ __forceinline__ float gaussian_at_f32(uint64_t t, uint32_t stream, uint32_t k0,
+                                                 uint32_t k1) {
+  uint32_t c0, c1, c2, c3;
+  philox10(t, stream, k0, k1, c0, c1, c2, c3);
+  const float u1 = ((float)(c0 >> 8) + 0.5f) * 0x1p-24f;
+  const float u2 = ((float)(c2 >> 8) + 0.5f) * 0x1p-24f;
+  return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+}
+
+__global__ void gaussian_f32_fast_kernel(int64_t n, int l, uint32_t k0, uint32_t k1,
+                                         uint32_t stream, float* __restrict__ out, int64_t ldo) {
+  const uint64_t total = (uint64_t)n * (uint64_t)l;
+  for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
+       t += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t j = t / (uint64_t)n, i = t - j * (uint64_t)n;
+    out[i + j * (uint64_t)ldo] = gaussian_at_f32(t, stream, k0, k1);
+  }
 }
 
 template <typename T>
@@ -81,6 +110,10 @@ cudaError_t launch_gaussian(int64_t n, int l, uint64_t seed, uint32_t stream_id,
   uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   if (out_dtype == RSVD_F64) {
     gaussian_kernel<double><<<blocks, threads, 0, st>>>(n, l, k0, k1, stream_id, (double*)out, ldo);
+    note_launch();
+  } else if (out_dtype == kOutF32Fast) {
+    gaussian_f32_fast_kernel<<<blocks, threads, 0, st>>>(n, l, k0, k1, stream_id, (float*)out,
+                                                         ldo);
     note_launch();
   } else if (out_dtype == RSVD_F32) {
     gaussian_kernel<float><<<blocks, threads, 0, st>>>(n, l, k0, k1, stream_id, (float*)out, ldo);

@@ -27,29 +27,29 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
 
+// x = x_1 + x_2 + ... : slice s of column c (blockIdx.y = s * stride + c)
+// holds the BF16 rounding of what the earlier slices left over.
 __global__ void split_bf16_kernel(const float* __restrict__ X, int64_t rows, int l, int64_t ldx,
-                                  int slices, int stride, __nv_bfloat16* __restrict__ out,
-                                  int64_t ldo) {
-  const int64_t total = rows * (int64_t)slices * stride;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t cc = t / rows, r = t - cc * rows;
-    const int s = (int)(cc / stride), c = (int)(cc % stride);
+                                  int stride, __nv_bfloat16* __restrict__ out, int64_t ldo) {
+  const int cc = blockIdx.y;
+  const int s = cc / stride, c = cc - s * stride;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows;
+       r += (int64_t)gridDim.x * blockDim.x) {
     float v = (c < l) ? X[r + (int64_t)c * ldx] : 0.f;
     __nv_bfloat16 h = __float2bfloat16_rn(v);
     for (int j = 0; j < s; ++j) {  // peel the leading slices off
       v -= __bfloat162float(h);
       h = __float2bfloat16_rn(v);
     }
-    out[r + cc * ldo] = h;
+    out[r + (int64_t)cc * ldo] = h;
   }
 }
 
 int split_operand(rsvd_plan_t P, const float* X, int64_t rows, int l, int64_t ldx, int slices,
                   int stride, __nv_bfloat16* out, int64_t ldo) {
-  const int64_t total = rows * (int64_t)slices * stride;
-  const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)P->num_sms * 8);
-  split_bf16_kernel<<<blocks, 256, 0, P->stream>>>(X, rows, l, ldx, slices, stride, out, ldo);
+  const int bx = (int)std::min<int64_t>((rows + 255) / 256, 16);
+  dim3 grid(bx, slices * stride);
+  split_bf16_kernel<<<grid, 256, 0, P->stream>>>(X, rows, l, ldx, stride, out, ldo);
   note_launch();
   RSVD_CK(cudaGetLastError());
   return RSVD_OK;
@@ -147,7 +147,7 @@ Layout make_layout(int64_t m, int64_t n, int l, int mode, int num_sms) {
   // G, R1, R1inv, R2, R2inv, Mt, Um, Vm, jacobi work (2 l x lpad), sig, sign, chol work
   L.small = take(L.small_stride * 8 + align_up(2 * (size_t)l * lpad * e) +
                  align_up(2 * (size_t)l * e) +
-                 align_up(((size_t)l * l + 32 * (size_t)(l + 32)) * e));
+                 align_up(((size_t)l * l + 33 * (size_t)(l + 64)) * e));
   if (mode == RSVD_MODE_MIXED) {
     const int l16 = (l + 15) / 16 * 16;
     L.om16 = take((size_t)round8(mn) * 3 * l16 * sizeof(__nv_bfloat16));
@@ -279,7 +279,7 @@ int solve_mixed(rsvd_plan_t P, const void* A, int64_t m, int64_t n, int64_t lda,
   Work<float> W = work_of<float>(P);
   int rc;
   // 1. Omega (FP32, rounded to BF16 for the pass);  2. Y = A Omega;  3. Q = orth(Y)
-  RSVD_CK(launch_gaussian(n, l, seed, 0u, kOutF32, W.om, n, P->stream));
+  RSVD_CK(launch_gaussian(n, l, seed, 0u, kOutF32Fast, W.om, n, P->stream));
   if ((rc = mixed_pass(P, true, A, m, n, lda, W.om, l, 1, W.y, m))) return rc;
   if ((rc = orth<float>(P, W.y, m, l, m, W.qm, m, nullptr, false))) return rc;
   // 4-5. q power steps on a BF16 operand, then one refinement step on bf16x2

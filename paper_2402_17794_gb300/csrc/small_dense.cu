@@ -54,8 +54,8 @@ __device__ __forceinline__ void set_flag(DeviceStatus* s, int code) {
 }
 
 // G (ldg) -> R (ld l, upper; lower part zeroed), Rinv (ld l, upper).
-// W (l*l) and the 32 x (l + 32) scratch S live in dynamic shared memory when
-// they fit, else in `gwork` (l*l + 32*(l+32) elements).
+// W (l*l) and the scratch S (33*(l+64) elements) live in dynamic shared
+// memory when they fit, else in `gwork` (l*l + 33*(l+64) elements).
 //
 // Cholesky: right-looking, one pivot per step, trailing update of the upper
 // triangle by a 32 x 32 thread grid.  Inverse (in place, LAPACK trtri's
@@ -70,7 +70,7 @@ chol_inv_kernel(const T* __restrict__ G, int64_t ldg, int l, T* __restrict__ R,
                 T* __restrict__ Rinv, T* __restrict__ gwork, DeviceStatus* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* W = gwork ? gwork : reinterpret_cast<T*>(smem_raw);  // column-major l x l
-  T* S = W + (int64_t)l * l;                                  // 32 x (l + 32) scratch
+  T* S = W + (int64_t)l * l;                                  // 33 x (l + 64) scratch
   __shared__ T s_maxdiag;
   __shared__ T s_r, s_inv;
   __shared__ int s_bad;
@@ -109,30 +109,85 @@ chol_inv_kernel(const T* __restrict__ G, int64_t ldg, int l, T* __restrict__ R,
   }
   const T tol = Eps<T>::drop_factor(l) * Eps<T>::value * s_maxdiag;
 
-  // ---- Cholesky: G = R^T R on the upper triangle ----
-  for (int j = 0; j < l; ++j) {
-    if (tid == 0) {
-      const T d = W[j + j * l];
-      if (!(d > tol)) {
-        s_r = T(0);  // dropped column
-        s_inv = T(0);
-        s_deficient++;
-      } else {
-        s_r = sqrt(d);
-        s_inv = T(1) / s_r;
+  // ---- Cholesky: G = R^T R on the upper triangle, 32-wide panels ----
+  // Per panel k (rows/columns k0 .. k0+kw-1):
+  //  (i)   warp 0 factors the diagonal block in a padded copy (S, 32 x 33);
+  //  (ii)  the panel rows R[k0:k0+kw, c] = D^-T G[k0:k0+kw, c] for the columns
+  //        right of the block, one thread per column, in a transposed padded
+  //        copy P (c-major, stride 33) so threads touch distinct banks;
+  //  (iii) trailing update G[i][c] -= sum_t P[i][t] P[c][t] for i <= c.
+  T* Dg = S;                 // 32 x 33 diagonal block (column-major, ld 33)
+  T* Dinv = S + 32 * 33;     // 32 reciprocal pivots
+  T* Pp = S + 33 * 33;       // (l - k0 - kw) x 33 transposed panel
+  for (int k0 = 0; k0 < l; k0 += 32) {
+    const int kw = min(32, l - k0);
+    const int c_beg = k0 + kw, nc = l - c_beg;
+    // load the diagonal block (upper) and the panel rows (transposed)
+    for (int t = tid; t < 32 * 32; t += nt) {
+      const int i = t & 31, c = t >> 5;
+      Dg[i + c * 33] = (i < kw && c < kw && i <= c) ? W[k0 + i + (k0 + c) * l] : T(0);
+    }
+    for (int t = tid; t < nc * 32; t += nt) {
+      const int i = t & 31, c = t >> 5;   // i: panel row, c: column offset
+      Pp[c * 33 + i] = (i < kw) ? W[k0 + i + (c_beg + c) * l] : T(0);
+    }
+    __syncthreads();
+    if (ty == 0) {
+      // (i) one warp, lane = column within the block
+      const int c = tx;
+      for (int j = 0; j < kw; ++j) {
+        const T d = Dg[j + j * 33];
+        T r, inv;
+        if (!(d > tol)) {
+          r = T(0);
+          inv = T(0);
+          if (c == 0) s_deficient++;
+        } else {
+          r = sqrt(d);
+          inv = T(1) / r;
+        }
+        __syncwarp();
+        if (c > j && c < kw) Dg[j + c * 33] *= inv;
+        if (c == j) {
+          Dg[j + j * 33] = r;
+          Dinv[j] = inv;
+        }
+        __syncwarp();
+        if (c > j && c < kw) {
+          const T rjc = Dg[j + c * 33];
+          for (int i = j + 1; i <= c; ++i) Dg[i + c * 33] -= Dg[j + i * 33] * rjc;
+        }
+        __syncwarp();
       }
     }
     __syncthreads();
-    const T r = s_r, inv = s_inv;
-    // row j of R: W[j][c] * inv for c > j (zero for a dropped column)
-    for (int c = j + 1 + tid; c < l; c += nt) W[j + c * l] *= inv;
-    if (tid == 0) W[j + j * l] = r;
+    // (ii) panel rows: solve D^T x = g per column (forward substitution)
+    for (int c = tid; c < nc; c += nt) {
+      T* x = Pp + c * 33;
+      for (int i = 0; i < kw; ++i) {
+        T acc = x[i];
+        for (int t2 = 0; t2 < i; ++t2) acc -= Dg[t2 + i * 33] * x[t2];
+        x[i] = acc * Dinv[i];   // a dropped pivot (Dinv 0) zeroes the row
+      }
+    }
     __syncthreads();
-    if (r != T(0)) {
-      // W[i][c] -= R[j][i] R[j][c] for j < i <= c
-      for (int c = j + 1 + ty; c < l; c += 32) {
-        const T rjc = W[j + c * l];
-        for (int i = j + 1 + tx; i <= c; i += 32) W[i + c * l] -= W[j + i * l] * rjc;
+    // write the factored block and panel rows back; (iii) trailing update
+    for (int t = tid; t < 32 * 32; t += nt) {
+      const int i = t & 31, c = t >> 5;
+      if (i < kw && c < kw && i <= c) W[k0 + i + (k0 + c) * l] = Dg[i + c * 33];
+    }
+    for (int t = tid; t < nc * 32; t += nt) {
+      const int i = t & 31, c = t >> 5;
+      if (i < kw) W[k0 + i + (c_beg + c) * l] = Pp[c * 33 + i];
+    }
+    for (int cc = ty; cc < nc; cc += 32) {
+      const T* pc = Pp + cc * 33;
+      for (int ii = tx; ii <= cc; ii += 32) {
+        const T* pi = Pp + ii * 33;
+        T acc = T(0);
+#pragma unroll 8
+        for (int t2 = 0; t2 < kw; ++t2) acc = fma(pi[t2], pc[t2], acc);
+        W[c_beg + ii + (c_beg + cc) * l] -= acc;
       }
     }
     __syncthreads();
@@ -447,7 +502,7 @@ __global__ void vt_kernel(const T* __restrict__ Vk, int64_t n, int k,
 template <typename T>
 cudaError_t launch_chol_inv(const T* G, int64_t ldg, int l, T* R, T* Rinv, T* work,
                             DeviceStatus* status, cudaStream_t st) {
-  const size_t smem = ((size_t)l * l + 32 * (size_t)(l + 32)) * sizeof(T);
+  const size_t smem = ((size_t)l * l + 33 * (size_t)(l + 64)) * sizeof(T);
   const size_t cap = 200 * 1024;
   static bool attr_set = false;
   if (!attr_set) {

@@ -441,15 +441,16 @@ __global__ void apass_fixup_kernel(const float* __restrict__ part, int grid, int
   const int n = s_n;
   if (n == 0) return;  // written directly by one CTA
   const int64_t per_tile = (int64_t)bmt * l;
-  for (int64_t idx = threadIdx.x; idx < per_tile; idx += blockDim.x) {
-    const int c = (int)(idx / bmt), r = (int)(idx % bmt);
-    const int64_t row = t * bmt + r;
-    if (row >= rows_out) continue;
-    float s = 0.f;
-    for (int j = 0; j < n; ++j)
-      s += part[((size_t)s_cta[j] * 2 + s_slot[j]) * per_tile + (size_t)c * bmt + r];
-    float* d = out + row + (int64_t)c * ldo;
-    *d = accumulate ? *d + s : s;
+  for (int c = 0; c < l; ++c) {
+    for (int r = threadIdx.x; r < bmt; r += blockDim.x) {
+      const int64_t row = t * bmt + r;
+      if (row >= rows_out) continue;
+      float s = 0.f;
+      for (int j = 0; j < n; ++j)
+        s += part[((size_t)s_cta[j] * 2 + s_slot[j]) * per_tile + (size_t)c * bmt + r];
+      float* d = out + row + (int64_t)c * ldo;
+      *d = accumulate ? *d + s : s;
+    }
   }
 }
 
