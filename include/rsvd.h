@@ -224,6 +224,58 @@ int rsvd_small_svd(rsvd_plan_t plan, const void* M, int l, int64_t ldm,
                    void* sig, void* Um, int64_t ldu, void* Vm, int64_t ldv);
 
 /* ---------------------------------------------------------------------- */
+/* Batches: many independent problems of uneven size in grouped launches    */
+/* (the thesis' method applied per problem; every step of Algorithm 4 runs  */
+/* once for the whole batch).                                               */
+/* ---------------------------------------------------------------------- */
+
+/* One problem of a batch: the arguments of rsvd_solve (device pointers). */
+typedef struct rsvd_problem_s {
+  const void* A;          /* m x n, lda >= m, the batch plan's dtype */
+  int64_t m, n, lda;
+  int k, p, q;            /* 1 <= k, 0 <= p, k + p <= min(m, n), q >= 0 */
+  uint64_t seed;
+  void* U;                /* m x k, ldu >= m, the plan's dtype */
+  int64_t ldu;
+  double* S;              /* k, descending */
+  void* VT;               /* k x n, ldvt >= k, the plan's dtype */
+  int64_t ldvt;
+} rsvd_problem_t;
+
+/*
+ * rsvd_batch_plan_create: a plan for batches of up to max_count problems
+ * whose m's sum to at most rows_total and whose n's sum to at most
+ * cols_total, each with k + p <= l_max.  a_dtype RSVD_F64 (every step in
+ * FP64) or RSVD_F32 (every step in FP32) on the CUDA cores.  Workspace is
+ * queried and set as for other plans.  Allocates pinned host memory for the
+ * per-batch problem table and an event, nothing on the device.
+ * Errors: -1 plan; -2 max_count < 1; -3 rows_total < 1; -4 cols_total < 1;
+ * -5 l_max outside 1..RSVD_L_MAX; -6 dtype; RSVD_ERR_CUDA.
+ */
+int rsvd_batch_plan_create(rsvd_plan_t* plan, int max_count, int64_t rows_total,
+                           int64_t cols_total, int l_max, int a_dtype, void* cuda_stream);
+
+/*
+ * rsvd_solve_batched: enqueues the rank-k randomized SVD (Algorithm 4) of every
+ * problem in `problems` (host array of `count` entries) on the plan's stream.
+ * Each problem's result depends only on its own inputs (no work is split
+ * across problems), so it is the same in any batch.  Waits on the host only
+ * until the previous batched solve's problem table has left the pinned
+ * staging buffer.
+ * Errors: -1 plan is not a batch plan; -2 count outside 1..max_count;
+ * -3 problems NULL; RSVD_ERR_WORKSPACE when sizes exceed the plan or no
+ * workspace is set; -(100 + i) when problem i has an invalid argument.
+ */
+int rsvd_solve_batched(rsvd_plan_t plan, int count, const rsvd_problem_t* problems);
+
+/*
+ * rsvd_batch_status: waits for the plan's stream and writes each problem's
+ * status (RSVD_OK or a positive RSVD_ERR_* code) of the last batched solve to
+ * the host array codes[0..count-1].
+ */
+int rsvd_batch_status(rsvd_plan_t plan, int count, int* codes);
+
+/* ---------------------------------------------------------------------- */
 /* Allocation-free entry point                                             */
 /* ---------------------------------------------------------------------- */
 

@@ -14,6 +14,14 @@ c_int, c_int64, c_uint32, c_uint64 = ctypes.c_int, ctypes.c_int64, ctypes.c_uint
 c_void_p, c_size_t = ctypes.c_void_p, ctypes.c_size_t
 P_double = ctypes.c_void_p
 
+class RsvdProblem(ctypes.Structure):
+    """rsvd_problem_t of include/rsvd.h."""
+    _fields_ = [("A", c_void_p), ("m", c_int64), ("n", c_int64), ("lda", c_int64),
+                ("k", c_int), ("p", c_int), ("q", c_int), ("seed", c_uint64),
+                ("U", c_void_p), ("ldu", c_int64), ("S", c_void_p), ("VT", c_void_p),
+                ("ldvt", c_int64)]
+
+
 # name -> (restype, argtypes), in the order of include/rsvd.h
 SIGNATURES = {
     "rsvd_plan_create": (c_int, [ctypes.POINTER(c_void_p), c_int64, c_int64, c_int, c_int, c_int,
@@ -38,6 +46,10 @@ SIGNATURES = {
                           P_double, c_int64]),
     "rsvd_small_svd": (c_int, [c_void_p, P_double, c_int, c_int64, P_double, P_double, c_int64,
                                P_double, c_int64]),
+    "rsvd_batch_plan_create": (c_int, [ctypes.POINTER(c_void_p), c_int, c_int64, c_int64, c_int,
+                                       c_int, c_void_p]),
+    "rsvd_solve_batched": (c_int, [c_void_p, c_int, ctypes.POINTER(RsvdProblem)]),
+    "rsvd_batch_status": (c_int, [c_void_p, c_int, ctypes.POINTER(c_int)]),
     "rsvd_apply_a_f64_static": (c_int, [c_void_p, c_int64, c_int64, c_int64, c_void_p, c_int64,
                                         c_int, c_void_p, c_int64, c_void_p]),
 }

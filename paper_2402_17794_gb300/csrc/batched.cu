@@ -1,0 +1,467 @@
+// Many independent randomized SVDs (Algorithm 4, Section 3.3) in grouped
+// launches: every step of the path runs once for the whole batch.
+//
+//  * One table of per-problem contexts (operand pointers, sizes, workspace
+//    slices) is copied to the device per batched solve; every grouped kernel
+//    reads its problem's entry with blockIdx.y (GEMMs, elementwise steps) or
+//    blockIdx.x (the l x l steps), so uneven sizes share one launch and no
+//    launch depends on another problem's size beyond the grid bounds.
+//  * GEMMs: 2-D grid (row tiles of the largest problem, problems[, column
+//    tiles]); CTAs past a problem's extent exit at once.  No split-K, so a
+//    problem's result does not depend on what else is in the batch.
+//  * l x l steps (Cholesky + inverse, Jacobi SVD, signs): one CTA per problem.
+//  * Power steps: problem i takes part in iteration j only while j < q_i.
+// Arithmetic is FP64 (RSVD_F64 plans) or FP32 (RSVD_F32 plans) throughout.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "batched.h"
+#include "gemm_body.cuh"
+#include "omega_body.cuh"
+#include "pipeline.h"
+#include "small_body.cuh"
+
+namespace rsvd {
+namespace {
+
+using dense::SMALL_THREADS;
+using simt::BM;
+using simt::THREADS;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+template <typename T>
+struct Ctx {
+  const T* A;
+  int64_t m, n, lda;
+  int k, p, q, l;
+  uint64_t seed;
+  T* U;
+  int64_t ldu;
+  double* S;
+  T* VT;
+  int64_t ldvt;
+  T *om, *y, *qm, *tmp, *z, *qb;
+  T *G, *R1, *R1i, *R2, *R2i, *Mt, *Um, *UsInv, *jw, *sig, *sign, *cholw;
+  DeviceStatus* status;
+};
+
+// GEMM operands of each grouped step for one problem.
+enum GOp {
+  OP_A_OM_Y = 0,    // Y = A Omega (or A W)
+  OP_AT_QM_Z,       // Z = A^T Q
+  OP_GRAM_Y,        // G = Y^T Y
+  OP_GRAM_Z,        // G = Z^T Z
+  OP_GRAM_TM,       // G = T^T T, T m x l
+  OP_GRAM_TN,       // G = T^T T, T n x l
+  OP_TRSM_Y,        // T = Y R1^-1 (m x l)
+  OP_TRSM_Z,        // T = Z R1^-1 (n x l)
+  OP_TRSM_TM_QM,    // Q = T R2^-1 (m x l)
+  OP_TRSM_TN_OM,    // W = T R2^-1 (n x l)
+  OP_LIFT_U,        // U = Q U~_k
+  OP_LIFT_V,        // T = Z (U~ Sigma^-1)_k   (n x k)
+  OP_GRAM_V,        // G = T^T T (k x k)
+  OP_TRSM_V,        // Qb = T R1^-1 (n x k)
+  OP_COUNT
+};
+
+template <typename T>
+__device__ __forceinline__ GemmArgs<T> op_args(const Ctx<T>& P, int op) {
+  const int l = P.l, k = P.k;
+  switch (op) {
+    case OP_A_OM_Y: return {P.A, P.lda, false, P.om, P.n, P.y, P.m, P.m, P.n, l};
+    case OP_AT_QM_Z: return {P.A, P.lda, true, P.qm, P.m, P.z, P.n, P.n, P.m, l};
+    case OP_GRAM_Y: return {P.y, P.m, true, P.y, P.m, P.G, l, l, P.m, l};
+    case OP_GRAM_Z: return {P.z, P.n, true, P.z, P.n, P.G, l, l, P.n, l};
+    case OP_GRAM_TM: return {P.tmp, P.m, true, P.tmp, P.m, P.G, l, l, P.m, l};
+    case OP_GRAM_TN: return {P.tmp, P.n, true, P.tmp, P.n, P.G, l, l, P.n, l};
+    case OP_TRSM_Y: return {P.y, P.m, false, P.R1i, l, P.tmp, P.m, P.m, l, l};
+    case OP_TRSM_Z: return {P.z, P.n, false, P.R1i, l, P.tmp, P.n, P.n, l, l};
+    case OP_TRSM_TM_QM: return {P.tmp, P.m, false, P.R2i, l, P.qm, P.m, P.m, l, l};
+    case OP_TRSM_TN_OM: return {P.tmp, P.n, false, P.R2i, l, P.om, P.n, P.n, l, l};
+    case OP_LIFT_U: return {P.qm, P.m, false, P.Um, l, P.U, P.ldu, P.m, l, k};
+    case OP_LIFT_V: return {P.z, P.n, false, P.UsInv, l, P.tmp, P.n, P.n, l, k};
+    case OP_GRAM_V: return {P.tmp, P.n, true, P.tmp, P.n, P.G, k, k, P.n, k};
+    default: return {P.tmp, P.n, false, P.R1i, k, P.qb, P.n, P.n, k, k};
+  }
+}
+
+// iter >= 0: only problems with q > iter take part (power steps).
+__device__ __forceinline__ bool active(int q, int iter) { return iter < 0 || iter < q; }
+
+template <typename T, int TN, bool TRANS>
+__global__ void __launch_bounds__(THREADS)
+grouped_gemm_kernel(const Ctx<T>* __restrict__ ctx, int op, int iter) {
+  const Ctx<T>& P = ctx[blockIdx.y];
+  if (!active(P.q, iter)) return;
+  const GemmArgs<T> g = op_args(P, op);
+  const int64_t r0 = (int64_t)blockIdx.x * BM;
+  const int c0 = blockIdx.z * 16 * TN;
+  if (r0 >= g.M || c0 >= g.N) return;
+  simt::gemm_tile<T, TN, TRANS>(g.A, g.lda, g.X, g.ldx, g.C, g.ldc, g.M, g.N, r0, c0, 0, g.K);
+}
+
+// Cholesky + inverse: which 0 -> (G, l) into R1/R1i, 1 -> into R2/R2i,
+// 2 -> (G, k) into R1/R1i (re-orthonormalisation of V_k).
+template <typename T>
+__global__ void __launch_bounds__(SMALL_THREADS)
+grouped_chol_kernel(const Ctx<T>* __restrict__ ctx, int which, int iter, int use_smem) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Ctx<T>& P = ctx[blockIdx.x];
+  if (!active(P.q, iter)) return;
+  const int l = which == 2 ? P.k : P.l;
+  T* R = which == 1 ? P.R2 : P.R1;
+  T* Ri = which == 1 ? P.R2i : P.R1i;
+  T* W = use_smem ? reinterpret_cast<T*>(smem_raw) : P.cholw;
+  dense::chol_inv_body<T>(P.G, l, l, R, Ri, W, P.status);
+}
+
+// Mt = (R2 R1)^T, the transposed R factor of B^T.
+template <typename T>
+__global__ void grouped_tri_kernel(const Ctx<T>* __restrict__ ctx) {
+  const Ctx<T>& P = ctx[blockIdx.y];
+  const int l = P.l;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < l * l; t += gridDim.x * blockDim.x) {
+    const int i = t % l, j = t / l;
+    T s = T(0);
+    if (i <= j)
+      for (int u = i; u <= j; ++u) s = fma(P.R2[i + u * l], P.R1[u + j * l], s);
+    P.Mt[j + i * l] = s;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(SMALL_THREADS)
+grouped_jacobi_kernel(const Ctx<T>* __restrict__ ctx, int use_smem) {
+  extern __shared__ __align__(16) unsigned char jsm_raw[];
+  const Ctx<T>& P = ctx[blockIdx.x];
+  T* Wm = use_smem ? reinterpret_cast<T*>(jsm_raw) : P.jw;
+  dense::jacobi_body<T>(P.Mt, P.l, P.l, P.sig, P.Um, P.l, nullptr, P.l, P.UsInv, Wm, P.status);
+}
+
+template <typename T>
+__global__ void grouped_gaussian_kernel(const Ctx<T>* __restrict__ ctx);
+
+template <>
+__global__ void grouped_gaussian_kernel<double>(const Ctx<double>* __restrict__ ctx) {
+  const Ctx<double>& P = ctx[blockIdx.y];
+  const uint64_t total = (uint64_t)P.n * (uint64_t)P.l;
+  for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
+       t += (uint64_t)gridDim.x * blockDim.x)
+    P.om[t] = omega::gaussian_value_f64(t, 0u, P.seed);   // om is n x l, ld n: index t = j*n + i
+}
+
+template <>
+__global__ void grouped_gaussian_kernel<float>(const Ctx<float>* __restrict__ ctx) {
+  const Ctx<float>& P = ctx[blockIdx.y];
+  const uint64_t total = (uint64_t)P.n * (uint64_t)P.l;
+  for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
+       t += (uint64_t)gridDim.x * blockDim.x)
+    P.om[t] = (float)omega::gaussian_value_f64(t, 0u, P.seed);
+}
+
+template <typename T>
+__global__ void grouped_sign_kernel(const Ctx<T>* __restrict__ ctx) {
+  const Ctx<T>& P = ctx[blockIdx.y];
+  const int col = blockIdx.x;
+  if (col >= P.k) return;
+  dense::sign_body<T>(P.U + (int64_t)col * P.ldu, P.m, P.sign + col);
+}
+
+template <typename T>
+__global__ void grouped_vt_kernel(const Ctx<T>* __restrict__ ctx) {
+  const Ctx<T>& P = ctx[blockIdx.y];
+  const int64_t total = P.n * (int64_t)P.k;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = t / P.k;
+    const int i = (int)(t - j * P.k);
+    P.VT[i + j * P.ldvt] = P.sign[i] * P.qb[j + (int64_t)i * P.n];
+  }
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i < P.k; i += blockDim.x) P.S[i] = (double)P.sig[i];
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+
+struct BatchShape {
+  int count;
+  int64_t max_m, max_n;
+  int max_l, max_k, max_q;
+};
+
+template <typename T>
+size_t small_elems(int l) {
+  const int lpad = (l + 1) & ~1;
+  return 8 * (size_t)l * l + 2 * (size_t)l * lpad + 2 * (size_t)l + (size_t)l * l +
+         33 * (size_t)(l + 64);
+}
+
+template <typename T, bool TRANS>
+int launch_grouped_gemm(rsvd_plan_t P, const Ctx<T>* dctx, const BatchShape& b, int op, int iter,
+                        int64_t max_rows, int max_cols) {
+  const int per = std::min(max_cols, 96);
+  const int tn = (per + 15) / 16;
+  const int col_tiles = (max_cols + 16 * tn - 1) / (16 * tn);
+  dim3 grid((unsigned)((max_rows + BM - 1) / BM), (unsigned)b.count, (unsigned)col_tiles);
+  switch (tn) {
+#define RSVD_G(TNV) \
+  case TNV: grouped_gemm_kernel<T, TNV, TRANS><<<grid, THREADS, 0, P->stream>>>(dctx, op, iter); break;
+    RSVD_G(1) RSVD_G(2) RSVD_G(3) RSVD_G(4) RSVD_G(5) RSVD_G(6)
+#undef RSVD_G
+    default: return RSVD_ERR_UNSUPPORTED;
+  }
+  note_launch();
+  RSVD_CK(cudaGetLastError());
+  return RSVD_OK;
+}
+
+template <typename T>
+int gop(rsvd_plan_t P, const Ctx<T>* d, const BatchShape& b, int op, int iter) {
+  const int64_t mm = b.max_m, nn = b.max_n;
+  const int L = b.max_l, K = b.max_k;
+  switch (op) {
+    case OP_A_OM_Y: return launch_grouped_gemm<T, false>(P, d, b, op, iter, mm, L);
+    case OP_AT_QM_Z: return launch_grouped_gemm<T, true>(P, d, b, op, iter, nn, L);
+    case OP_GRAM_Y: case OP_GRAM_Z: case OP_GRAM_TM: case OP_GRAM_TN:
+      return launch_grouped_gemm<T, true>(P, d, b, op, iter, L, L);
+    case OP_TRSM_Y: case OP_TRSM_TM_QM: return launch_grouped_gemm<T, false>(P, d, b, op, iter, mm, L);
+    case OP_TRSM_Z: case OP_TRSM_TN_OM: return launch_grouped_gemm<T, false>(P, d, b, op, iter, nn, L);
+    case OP_LIFT_U: return launch_grouped_gemm<T, false>(P, d, b, op, iter, mm, K);
+    case OP_LIFT_V: return launch_grouped_gemm<T, false>(P, d, b, op, iter, nn, K);
+    case OP_GRAM_V: return launch_grouped_gemm<T, true>(P, d, b, op, iter, K, K);
+    default: return launch_grouped_gemm<T, false>(P, d, b, op, iter, nn, K);
+  }
+}
+
+template <typename T>
+int gchol(rsvd_plan_t P, const Ctx<T>* d, const BatchShape& b, int which, int iter) {
+  const int l = which == 2 ? b.max_k : b.max_l;
+  const size_t smem = ((size_t)l * l + 33 * (size_t)(l + 64)) * sizeof(T);
+  const size_t cap = 200 * 1024;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(grouped_chol_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)cap);
+    attr_set = true;
+  }
+  const bool sm = smem <= cap;
+  grouped_chol_kernel<T><<<b.count, SMALL_THREADS, sm ? smem : 0, P->stream>>>(d, which, iter,
+                                                                               sm ? 1 : 0);
+  note_launch();
+  RSVD_CK(cudaGetLastError());
+  return RSVD_OK;
+}
+
+// CholeskyQR2 over the batch: src -> dst (dst_op < 0: only the R factor Mt).
+template <typename T>
+int gorth(rsvd_plan_t P, const Ctx<T>* d, const BatchShape& b, bool on_m, int iter, bool want_q,
+          bool want_r) {
+  int rc;
+  if ((rc = gop<T>(P, d, b, on_m ? OP_GRAM_Y : OP_GRAM_Z, iter))) return rc;
+  if ((rc = gchol<T>(P, d, b, 0, iter))) return rc;
+  if ((rc = gop<T>(P, d, b, on_m ? OP_TRSM_Y : OP_TRSM_Z, iter))) return rc;
+  if ((rc = gop<T>(P, d, b, on_m ? OP_GRAM_TM : OP_GRAM_TN, iter))) return rc;
+  if ((rc = gchol<T>(P, d, b, 1, iter))) return rc;
+  if (want_q && (rc = gop<T>(P, d, b, on_m ? OP_TRSM_TM_QM : OP_TRSM_TN_OM, iter))) return rc;
+  if (want_r) {
+    dim3 grid((unsigned)std::max(1, (b.max_l * b.max_l + 255) / 256), (unsigned)b.count);
+    grouped_tri_kernel<T><<<grid, 256, 0, P->stream>>>(d);
+    note_launch();
+    RSVD_CK(cudaGetLastError());
+  }
+  return RSVD_OK;
+}
+
+// Y = A W or Y = A Omega for every problem; orth(Y) -> Q.  (Z, W likewise.)
+template <typename T>
+int solve_batched_t(rsvd_plan_t P, const Ctx<T>* d, const BatchShape& b) {
+  int rc;
+  {
+    dim3 grid(64, (unsigned)b.count);
+    grouped_gaussian_kernel<T><<<grid, 256, 0, P->stream>>>(d);
+    note_launch();
+    RSVD_CK(cudaGetLastError());
+  }
+  if ((rc = gop<T>(P, d, b, OP_A_OM_Y, -1))) return rc;
+  if ((rc = gorth<T>(P, d, b, true, -1, true, false))) return rc;
+  for (int j = 0; j < b.max_q; ++j) {
+    if ((rc = gop<T>(P, d, b, OP_AT_QM_Z, j))) return rc;
+    if ((rc = gorth<T>(P, d, b, false, j, true, false))) return rc;
+    if ((rc = gop<T>(P, d, b, OP_A_OM_Y, j))) return rc;
+    if ((rc = gorth<T>(P, d, b, true, j, true, false))) return rc;
+  }
+  if ((rc = gop<T>(P, d, b, OP_AT_QM_Z, -1))) return rc;
+  if ((rc = gorth<T>(P, d, b, false, -1, false, true))) return rc;
+  {
+    const int twoP = (b.max_l + 1) & ~1;
+    const size_t need = (size_t)b.max_l * twoP * sizeof(T);
+    const size_t cap = 200 * 1024;
+    static bool attr_set = false;
+    if (!attr_set) {
+      cudaFuncSetAttribute(grouped_jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)cap);
+      attr_set = true;
+    }
+    const bool sm = need <= cap;
+    grouped_jacobi_kernel<T><<<b.count, SMALL_THREADS, sm ? need : 0, P->stream>>>(d, sm ? 1 : 0);
+    note_launch();
+    RSVD_CK(cudaGetLastError());
+  }
+  if ((rc = gop<T>(P, d, b, OP_LIFT_U, -1))) return rc;
+  if ((rc = gop<T>(P, d, b, OP_LIFT_V, -1))) return rc;
+  if ((rc = gop<T>(P, d, b, OP_GRAM_V, -1))) return rc;
+  if ((rc = gchol<T>(P, d, b, 2, -1))) return rc;
+  if ((rc = gop<T>(P, d, b, OP_TRSM_V, -1))) return rc;
+  {
+    dim3 grid((unsigned)b.max_k, (unsigned)b.count);
+    grouped_sign_kernel<T><<<grid, 1024, 0, P->stream>>>(d);
+    note_launch();
+    dim3 g2(64, (unsigned)b.count);
+    grouped_vt_kernel<T><<<g2, 256, 0, P->stream>>>(d);
+    note_launch();
+    RSVD_CK(cudaGetLastError());
+  }
+  return RSVD_OK;
+}
+
+template <typename T>
+int fill_ctx(rsvd_plan_t P, int count, const rsvd_problem_t* pr, BatchShape* b) {
+  const BatchLayout& L = *P->batch_lay;
+  Ctx<T>* h = reinterpret_cast<Ctx<T>*>(P->h_ctx);
+  char* ws = P->ws;
+  int64_t moff = 0, noff = 0;
+  b->count = count;
+  b->max_m = b->max_n = 0;
+  b->max_l = b->max_k = 1;
+  b->max_q = 0;
+  const size_t per_small = align_up(small_elems<T>(P->l_max) * sizeof(T)) +
+                           align_up(sizeof(DeviceStatus));
+  for (int i = 0; i < count; ++i) {
+    const rsvd_problem_t& q = pr[i];
+    Ctx<T>& c = h[i];
+    const int l = q.k + q.p;
+    c.A = (const T*)q.A;
+    c.m = q.m;
+    c.n = q.n;
+    c.lda = q.lda;
+    c.k = q.k;
+    c.p = q.p;
+    c.q = q.q;
+    c.l = l;
+    c.seed = q.seed;
+    c.U = (T*)q.U;
+    c.ldu = q.ldu;
+    c.S = q.S;
+    c.VT = (T*)q.VT;
+    c.ldvt = q.ldvt;
+    const int lm = P->l_max;
+    c.om = (T*)(ws + L.om) + noff * lm;
+    c.z = (T*)(ws + L.z) + noff * lm;
+    c.qb = (T*)(ws + L.qb) + noff * lm;
+    c.y = (T*)(ws + L.y) + moff * lm;
+    c.qm = (T*)(ws + L.qm) + moff * lm;
+    c.tmp = (T*)(ws + L.tmp) + (moff + noff) * lm;
+    char* sb = ws + L.small + (size_t)i * per_small;
+    T* s = (T*)sb;
+    const size_t ll = (size_t)lm * lm;
+    c.G = s;
+    c.R1 = s + ll;
+    c.R1i = s + 2 * ll;
+    c.R2 = s + 3 * ll;
+    c.R2i = s + 4 * ll;
+    c.Mt = s + 5 * ll;
+    c.Um = s + 6 * ll;
+    c.UsInv = s + 7 * ll;
+    c.jw = s + 8 * ll;
+    const int lpad = (lm + 1) & ~1;
+    c.sig = c.jw + 2 * (size_t)lm * lpad;
+    c.sign = c.sig + lm;
+    c.cholw = c.sign + lm;
+    c.status = (DeviceStatus*)(sb + align_up(small_elems<T>(lm) * sizeof(T)));
+    moff += q.m;
+    noff += q.n;
+    b->max_m = std::max(b->max_m, q.m);
+    b->max_n = std::max(b->max_n, q.n);
+    b->max_l = std::max(b->max_l, l);
+    b->max_k = std::max(b->max_k, q.k);
+    b->max_q = std::max(b->max_q, q.q);
+  }
+  return RSVD_OK;
+}
+
+}  // namespace
+
+BatchLayout make_batch_layout(int max_count, int64_t rows_total, int64_t cols_total, int l,
+                              int dtype) {
+  BatchLayout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += align_up(bytes);
+    return o;
+  };
+  const size_t e = dtype == RSVD_F64 ? sizeof(double) : sizeof(float);
+  const size_t small = dtype == RSVD_F64 ? small_elems<double>(l) : small_elems<float>(l);
+  L.om = take((size_t)cols_total * l * e);
+  L.z = take((size_t)cols_total * l * e);
+  L.qb = take((size_t)cols_total * l * e);
+  L.y = take((size_t)rows_total * l * e);
+  L.qm = take((size_t)rows_total * l * e);
+  L.tmp = take((size_t)(rows_total + cols_total) * l * e);
+  L.small = take((size_t)max_count * (align_up(small * e) + align_up(sizeof(DeviceStatus))));
+  L.ctx = take((size_t)max_count * sizeof(Ctx<double>));
+  L.total = off;
+  return L;
+}
+
+size_t batch_ctx_bytes(int max_count) { return (size_t)max_count * sizeof(Ctx<double>); }
+
+int solve_batched(rsvd_plan_t P, int count, const rsvd_problem_t* pr) {
+  // the previous solve's table copy must have left the staging buffer
+  if (cudaEventSynchronize(P->ctx_event) != cudaSuccess) return RSVD_ERR_CUDA;
+  BatchShape b;
+  int rc;
+  const size_t bytes = (size_t)count * sizeof(Ctx<double>);
+  void* dctx = P->ws + P->batch_lay->ctx;
+  if (P->dtype == RSVD_F64) {
+    if ((rc = fill_ctx<double>(P, count, pr, &b))) return rc;
+  } else {
+    if ((rc = fill_ctx<float>(P, count, pr, &b))) return rc;
+  }
+  RSVD_CK(cudaMemcpyAsync(dctx, P->h_ctx, bytes, cudaMemcpyHostToDevice, P->stream));
+  RSVD_CK(cudaEventRecord(P->ctx_event, P->stream));
+  // per-problem status words start clear
+  {
+    const size_t per_small =
+        (P->dtype == RSVD_F64 ? align_up(small_elems<double>(P->l_max) * sizeof(double))
+                              : align_up(small_elems<float>(P->l_max) * sizeof(float))) +
+        align_up(sizeof(DeviceStatus));
+    const size_t st_off = per_small - align_up(sizeof(DeviceStatus));
+    RSVD_CK(cudaMemset2DAsync(P->ws + P->batch_lay->small + st_off, per_small, 0, sizeof(DeviceStatus),
+                              count, P->stream));
+  }
+  if (P->dtype == RSVD_F64)
+    return solve_batched_t<double>(P, (const Ctx<double>*)dctx, b);
+  return solve_batched_t<float>(P, (const Ctx<float>*)dctx, b);
+}
+
+int batch_status(rsvd_plan_t P, int count, int* codes) {
+  const size_t per_small =
+      (P->dtype == RSVD_F64 ? align_up(small_elems<double>(P->l_max) * sizeof(double))
+                            : align_up(small_elems<float>(P->l_max) * sizeof(float))) +
+      align_up(sizeof(DeviceStatus));
+  const size_t st_off = per_small - align_up(sizeof(DeviceStatus));
+  // gather the first word (flags) of each problem's status into the pinned buffer
+  RSVD_CK(cudaMemcpy2DAsync(P->h_ctx, sizeof(int), P->ws + P->batch_lay->small + st_off, per_small,
+                            sizeof(int), count, cudaMemcpyDeviceToHost, P->stream));
+  RSVD_CK(cudaStreamSynchronize(P->stream));
+  const int* f = (const int*)P->h_ctx;
+  for (int i = 0; i < count; ++i) codes[i] = status_from_flags(f[i]);
+  return RSVD_OK;
+}
+
+}  // namespace rsvd

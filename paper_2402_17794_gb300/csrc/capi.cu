@@ -9,6 +9,7 @@
 #include <cstring>
 #include <new>
 
+#include "batched.h"
 #include "pipeline.h"
 #include "umma.h"
 
@@ -45,6 +46,10 @@ int rsvd_plan_create(rsvd_plan_t* plan, int64_t m_max, int64_t n_max, int l_max,
   P->stream = (cudaStream_t)cuda_stream;
   P->ws = nullptr;
   P->ws_bytes = 0;
+  P->batched = 0;
+  P->batch_lay = nullptr;
+  P->h_ctx = nullptr;
+  P->ctx_event = nullptr;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
@@ -61,13 +66,90 @@ int rsvd_plan_create(rsvd_plan_t* plan, int64_t m_max, int64_t n_max, int l_max,
 int rsvd_workspace_size(rsvd_plan_t plan, size_t* bytes) {
   if (!plan) return -1;
   if (!bytes) return -2;
-  *bytes = plan->lay.total;
+  *bytes = plan->batched ? plan->batch_lay->total : plan->lay.total;
   return RSVD_OK;
+}
+
+int rsvd_batch_plan_create(rsvd_plan_t* plan, int max_count, int64_t rows_total,
+                           int64_t cols_total, int l_max, int a_dtype, void* cuda_stream) {
+  if (!plan) return -1;
+  *plan = nullptr;
+  if (max_count < 1) return -2;
+  if (rows_total < 1) return -3;
+  if (cols_total < 1) return -4;
+  if (l_max < 1 || l_max > RSVD_L_MAX) return -5;
+  if (a_dtype != RSVD_F64 && a_dtype != RSVD_F32) return -6;
+  rsvd_plan_s* P = new (std::nothrow) rsvd_plan_s();
+  if (!P) return RSVD_ERR_CUDA;
+  P->m_max = rows_total;
+  P->n_max = cols_total;
+  P->l_max = l_max;
+  P->dtype = a_dtype;
+  P->mode = RSVD_MODE_PLAIN;
+  P->stream = (cudaStream_t)cuda_stream;
+  P->ws = nullptr;
+  P->ws_bytes = 0;
+  P->batched = 1;
+  P->max_count = max_count;
+  P->rows_total = rows_total;
+  P->cols_total = cols_total;
+  P->h_ctx = nullptr;
+  P->ctx_event = nullptr;
+  P->h_status = nullptr;
+  P->batch_lay = new (std::nothrow) BatchLayout(
+      make_batch_layout(max_count, rows_total, cols_total, l_max, a_dtype));
+  int dev = 0;
+  if (!P->batch_lay || cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaMallocHost(&P->h_ctx, batch_ctx_bytes(max_count) + 4 * sizeof(int) * max_count) !=
+          cudaSuccess ||
+      cudaEventCreateWithFlags(&P->ctx_event, cudaEventDisableTiming) != cudaSuccess) {
+    if (P->h_ctx) cudaFreeHost(P->h_ctx);
+    delete P->batch_lay;
+    delete P;
+    return RSVD_ERR_CUDA;
+  }
+  *plan = P;
+  return RSVD_OK;
+}
+
+int rsvd_solve_batched(rsvd_plan_t plan, int count, const rsvd_problem_t* problems) {
+  if (!plan || !plan->batched) return -1;
+  if (count < 1 || count > plan->max_count) return -2;
+  if (!problems) return -3;
+  if (!plan->ws || plan->ws_bytes < plan->batch_lay->total) return RSVD_ERR_WORKSPACE;
+  int64_t rows = 0, cols = 0;
+  for (int i = 0; i < count; ++i) {
+    const rsvd_problem_t& q = problems[i];
+    const int l = q.k + q.p;
+    if (!q.A || q.m < 1 || q.n < 1 || q.lda < q.m || q.k < 1 || q.p < 0 || q.q < 0 ||
+        l > (q.m < q.n ? q.m : q.n) || !q.U || q.ldu < q.m || !q.S || !q.VT || q.ldvt < q.k)
+      return -(100 + i);
+    if (l > plan->l_max) return RSVD_ERR_WORKSPACE;
+    rows += q.m;
+    cols += q.n;
+  }
+  if (rows > plan->rows_total || cols > plan->cols_total) return RSVD_ERR_WORKSPACE;
+  return solve_batched(plan, count, problems);
+}
+
+int rsvd_batch_status(rsvd_plan_t plan, int count, int* codes) {
+  if (!plan || !plan->batched) return -1;
+  if (count < 1 || count > plan->max_count) return -2;
+  if (!codes) return -3;
+  if (!plan->ws) return RSVD_ERR_WORKSPACE;
+  return batch_status(plan, count, codes);
 }
 
 int rsvd_set_workspace(rsvd_plan_t plan, void* dev_ptr, size_t bytes) {
   if (!plan) return -1;
   if (!dev_ptr || ((uintptr_t)dev_ptr % kAlign)) return -2;
+  if (plan->batched) {
+    if (bytes < plan->batch_lay->total) return RSVD_ERR_WORKSPACE;
+    plan->ws = (char*)dev_ptr;
+    plan->ws_bytes = bytes;
+    return RSVD_OK;
+  }
   if (bytes < plan->lay.total) return RSVD_ERR_WORKSPACE;
   plan->ws = (char*)dev_ptr;
   plan->ws_bytes = bytes;
@@ -86,6 +168,8 @@ int rsvd_plan_set_stream(rsvd_plan_t plan, void* cuda_stream) {
 int rsvd_plan_status(rsvd_plan_t plan) {
   if (!plan) return -1;
   if (!plan->ws) return RSVD_ERR_WORKSPACE;
+  if (plan->batched)  // per-problem codes: rsvd_batch_status
+    return cudaStreamSynchronize(plan->stream) == cudaSuccess ? RSVD_OK : RSVD_ERR_CUDA;
   DeviceStatus* d = dstatus(plan);
   if (cudaMemcpyAsync(plan->h_status, &d->flags, sizeof(int), cudaMemcpyDeviceToHost,
                       plan->stream) != cudaSuccess)
@@ -112,6 +196,9 @@ int rsvd_plan_diagnostics(rsvd_plan_t plan, int* jacobi_sweeps, int* dropped_col
 int rsvd_plan_destroy(rsvd_plan_t plan) {
   if (!plan) return -1;
   if (plan->h_status) cudaFreeHost(plan->h_status);
+  if (plan->h_ctx) cudaFreeHost(plan->h_ctx);
+  if (plan->ctx_event) cudaEventDestroy(plan->ctx_event);
+  delete plan->batch_lay;
   delete plan;
   return RSVD_OK;
 }

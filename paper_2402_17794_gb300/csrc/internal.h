@@ -43,6 +43,10 @@ struct Layout {
 
 }  // namespace rsvd
 
+namespace rsvd {
+struct BatchLayout;
+}
+
 struct rsvd_plan_s {
   int64_t m_max, n_max;
   int l_max;
@@ -53,6 +57,13 @@ struct rsvd_plan_s {
   rsvd::Layout lay;
   int* h_status;     // pinned host copy of DeviceStatus.flags
   int num_sms;
+  // batch plans (rsvd_batch_plan_create)
+  int batched;
+  int max_count;
+  int64_t rows_total, cols_total;
+  rsvd::BatchLayout* batch_lay;   // owned
+  void* h_ctx;                    // pinned staging for the context table
+  cudaEvent_t ctx_event;          // marks the table copy of the last batched solve
 };
 
 namespace rsvd {

@@ -18,7 +18,7 @@ import torch
 
 from . import _lib
 
-F64, BF16 = 0, 2
+F64, F32, BF16 = 0, 1, 2
 PLAIN, MIXED = 0, 1
 STATUS = {0: "ok", 1: "cholesky", 2: "jacobi", 3: "timeout", 4: "workspace", 5: "cuda",
           6: "nonfinite", 7: "unsupported"}
@@ -146,6 +146,26 @@ def rsvd_small_svd(plan, M, l, ldm, sig, Um, ldu, Vm, ldv) -> int:
                                       ldv)
 
 
+def rsvd_batch_plan_create(max_count, rows_total, cols_total, l_max, a_dtype=F64, stream=None):
+    lib = _lib.load()
+    h = ctypes.c_void_p()
+    _check(lib.rsvd_batch_plan_create(ctypes.byref(h), max_count, rows_total, cols_total, l_max,
+                                      a_dtype, _stream_handle(stream)), "rsvd_batch_plan_create")
+    return h
+
+
+def rsvd_solve_batched(plan, problems) -> int:
+    """problems: a sequence of _lib.RsvdProblem (or an already built array)."""
+    arr = problems if isinstance(problems, ctypes.Array) else (_lib.RsvdProblem * len(problems))(*problems)
+    return _lib.load().rsvd_solve_batched(plan, len(arr), arr)
+
+
+def rsvd_batch_status(plan, count):
+    codes = (ctypes.c_int * count)()
+    _check(_lib.load().rsvd_batch_status(plan, count, codes), "rsvd_batch_status")
+    return list(codes)
+
+
 def rsvd_apply_a_f64_static(A, m, n, lda, X, ldx, l, Y, ldy, stream=None) -> int:
     return _lib.load().rsvd_apply_a_f64_static(_ptr(A), m, n, lda, _ptr(X), ldx, l, _ptr(Y), ldy,
                                                _stream_handle(stream))
@@ -154,6 +174,55 @@ def rsvd_apply_a_f64_static(A, m, n, lda, X, ldx, l, Y, ldy, stream=None) -> int
 # ---------------------------------------------------------------------------
 # Convenience wrapper
 # ---------------------------------------------------------------------------
+
+class BatchPlan:
+    """Owns a batch plan (rsvd_batch_plan_create) and its workspace.
+
+    solve(items) takes a list of (A, m, n, k, p, q, seed) with A a
+    column-major device tensor (n, lda) of the plan's dtype and returns
+    [(U, S, VT)] column-major tensors; enqueued only (status() waits)."""
+
+    def __init__(self, max_count, rows_total, cols_total, l_max, a_dtype=F64, stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("the randomized SVD library needs a CUDA GPU")
+        self.handle = rsvd_batch_plan_create(max_count, rows_total, cols_total, l_max, a_dtype,
+                                             stream)
+        self.dtype = torch.float64 if a_dtype == F64 else torch.float32
+        nbytes = rsvd_workspace_size(self.handle)
+        self.workspace = torch.empty(max(nbytes, 256), dtype=torch.uint8, device="cuda")
+        rsvd_set_workspace(self.handle, self.workspace)
+        self.count = 0
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None:
+            try:
+                rsvd_plan_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+    def solve(self, items, outs=None):
+        probs, results = [], []
+        for i, (A, m, n, k, p, q, seed) in enumerate(items):
+            if outs is None:
+                U = torch.empty(k, m, dtype=self.dtype, device=A.device)
+                S = torch.empty(k, dtype=torch.float64, device=A.device)
+                VT = torch.empty(n, k, dtype=self.dtype, device=A.device)
+            else:
+                U, S, VT = outs[i]
+            probs.append(_lib.RsvdProblem(A.data_ptr(), m, n, A.shape[1], k, p, q, seed,
+                                          U.data_ptr(), U.shape[1], S.data_ptr(), VT.data_ptr(),
+                                          VT.shape[1]))
+            results.append((U, S, VT))
+        _check(rsvd_solve_batched(self.handle, probs), "rsvd_solve_batched")
+        self.count = len(probs)
+        self._keep = (items, results)
+        return results
+
+    def status(self):
+        return rsvd_batch_status(self.handle, self.count)
+
 
 class Plan:
     """Owns a C plan and its torch-allocated workspace."""
