@@ -132,9 +132,25 @@ def _max_over_ranks(x: float, world: int) -> float:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_rate(local_units: float, local_ms: float, world: int):
+    """Whole-job rate of replicas: units summed over ranks divided by the
+    slowest rank's time.  Returns (units/s, max ms)."""
+    ms = _max_over_ranks(local_ms, world)
+    units = local_units
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([local_units], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        units = float(t.item())
+    return units / (ms / 1e3), ms
 
 
 def _time_calls(plan_handle, fn, reps=10):
@@ -318,6 +334,121 @@ def _cores():
         return os.cpu_count()
 
 
+def _batched_problems(count, seed, device="cuda"):
+    """The batched workload: FP32 matrices with m log-uniform in [256, 4096],
+    n uniform in [256, 2048], sigma_i = exp(-i/r) with r uniform in [5, 50];
+    k uniform in [10, 64], p = 10, q = 1 (Haar factors; terms below 1e-8 of
+    sigma_1 are dropped)."""
+    import numpy as np
+    import torch
+
+    from paper_2402_17794_gb300 import synthetic as syn
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        m = int(np.exp(rng.uniform(np.log(256), np.log(4096))))
+        n = int(rng.integers(256, 2049))
+        r = float(rng.uniform(5.0, 50.0))
+        k = int(rng.integers(10, 65))
+        terms = min(m, n, int(r * np.log(1e8)) + 1)
+        A = syn.lowrank_matrix_torch(m, n, syn.spectrum("exp", terms, r=r), seed=seed * 7919 + i,
+                                     device=device, dtype=torch.float32,
+                                     factor_dtype=torch.float32)
+        out.append((A, m, n, k, 10, 1, 1000 + i))
+    return out
+
+
+def run_batched(args, stream):
+    """512 uneven FP32 problems in one grouped solve."""
+    import torch
+
+    from paper_2402_17794_gb300 import rsvd as R
+    items = _batched_problems(512, 11)
+    rows = sum(it[1] for it in items)
+    cols = sum(it[2] for it in items)
+    l_max = max(it[3] + it[4] for it in items)
+    plan = R.BatchPlan(len(items), rows, cols, l_max, R.F32)
+    outs = [(torch.empty(k, m, dtype=torch.float32, device="cuda"),
+             torch.empty(k, dtype=torch.float64, device="cuda"),
+             torch.empty(n, k, dtype=torch.float32, device="cuda"))
+            for (_, m, n, k, _, _, _) in items]
+    for _ in range(3):
+        plan.solve(items, outs)
+    codes = plan.status()
+    steps = 5
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        plan.solve(items, outs)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    a_bytes = sum(m * n * 4 for (_, m, n, _, _, _, _) in items)
+    return {"workload": "512 FP32 matrices, m log-uniform [256,4096], n uniform [256,2048], "
+                        "sigma_i=exp(-i/r), r~U[5,50]; k~U{10..64}, p=10, q=1; one grouped solve",
+            "value": round(len(items) / (ms / 1e3), 1), "unit": "solves/s",
+            "ms_per_batch": round(ms, 3), "problems": len(items),
+            "a_bytes_per_pass": a_bytes,
+            "a_pass_equiv_gbps": round(4 * a_bytes / (ms / 1e3) / 1e9, 1),
+            "failed": sum(1 for c in codes if c != 0), "dtype": "f32"}
+
+
+def run_serving(args):
+    """Poisson arrivals at 2000 req/s; 95% FP32 matrices sized as the batched
+    workload, 5% 8192x8192 with sigma_i = 1/i, k=256, p=32, q=2; tolerance
+    1e-3 or 1e-6 (half each); admission capped at 150 GB of HBM."""
+    import time
+
+    import numpy as np
+    import torch
+
+    from paper_2402_17794_gb300 import serve
+    from paper_2402_17794_gb300 import synthetic as syn
+    rng = np.random.default_rng(21)
+    small = _batched_problems(32, 13)
+    bigs = [syn.lowrank_matrix_torch(8192, 8192, syn.spectrum("poly", 8192, alpha=1.0),
+                                     seed=900 + j, dtype=torch.float32,
+                                     factor_dtype=torch.float32) for j in range(2)]
+    torch.cuda.synchronize()
+    rate, dur = 2000.0, args.serve_seconds
+    reqs, t, i = [], 0.0, 0
+    while True:
+        t += float(rng.exponential(1.0 / rate))
+        if t > dur:
+            break
+        tol = 1e-3 if rng.random() < 0.5 else 1e-6
+        if rng.random() < 0.05:
+            A = bigs[i % 2]
+            reqs.append(serve.Request(i, 8192, 8192, 256, 32, 2, tol, 5000 + i, t, A=A))
+        else:
+            A, m, n, k, p, q, _ = small[i % len(small)]
+            k = int(rng.integers(10, 65))
+            reqs.append(serve.Request(i, m, n, k, p, q, tol, 5000 + i, t, A=A))
+        i += 1
+    specs = [serve.LaneSpec("f32-small", 64, 64 * 4096, 64 * 2048, 80),
+             serve.LaneSpec("f64-small", 64, 64 * 4096, 64 * 2048, 80),
+             serve.LaneSpec("f32-big", 4, 4 * 8192, 4 * 8192, 288),
+             serve.LaneSpec("f64-big", 4, 4 * 8192, 4 * 8192, 288)]
+    srv = serve.Server(specs, serve.TorchBackend(), 150 * 10**9, lanes_per_class=2)
+    stats = serve.run(srv, reqs, time.perf_counter, max_wall=900.0)
+    per = {}
+    for cls in ("f32-small", "f64-small", "f32-big", "f64-big"):
+        lat = [r.latency for r in srv.finished if serve.request_class(r) == cls]
+        per[cls] = {"n": len(lat), "p50_ms": round(serve.percentile(lat, 50) * 1e3, 2),
+                    "p99_ms": round(serve.percentile(lat, 99) * 1e3, 2)}
+    return {"workload": "Poisson 2000 req/s for %.0f s; 95%% FP32 matrices as the batched "
+                        "workload, 5%% 8192x8192 sigma_i=1/i k=256 p=32 q=2; tolerance 1e-3 or "
+                        "1e-6 (half each); admission cap 150 GB" % dur,
+            "offered_rps": rate, "requests": len(reqs),
+            "value": round(stats["throughput_rps"], 1), "unit": "solves/s",
+            "p50_ms": round(stats["p50_ms"], 2), "p99_ms": round(stats["p99_ms"], 2),
+            "wall_s": round(stats["wall_s"], 2), "batches": stats["batches"],
+            "admission_stalls": stats["admission_stalls"], "failed": stats["failed"],
+            "per_class": per}
+
+
 def run_ours(args):
     import torch
 
@@ -377,9 +508,7 @@ def run_ours(args):
     if st != 0:
         raise RuntimeError(f"timed solve failed: {R.rsvd_status_string(st)}")
     sweeps, _ = R.rsvd_plan_diagnostics(plan.handle)
-    ms_max = _max_over_ranks(ms, world)
-    solves = args.steps * world
-    value = solves / (ms_max / 1e3)
+    value, ms_max = job_rate(args.steps, ms, world)
     ms_per_step = ms_max / args.steps
 
     # --- the dominant kernels, timed alone through the step entry points ---
@@ -457,6 +586,9 @@ def run_ours(args):
         del A_h, dA2
         mixed = run_mixed(args, world, rank, uuid)
 
+    batched = None if args.no_batched else run_batched(args, stream)
+    serving = None if args.no_serving else run_serving(args)
+
     # --- CPU oracle on this host (rank 0, N = 1 only) ---
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -480,6 +612,8 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "mixed": mixed,
+        "batched": batched,
+        "serving": serving,
         "gpu_launches": int(launches),
         "gpu_launches_per_step": launches / args.steps,
         "jacobi_sweeps": sweeps,
@@ -604,6 +738,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the mixed-precision (BF16) workload")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched workload")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving workload")
+    ap.add_argument("--serve-seconds", type=float, default=2.0,
+                    help="seconds of Poisson arrivals in the serving run (the workload "
+                         "definition uses 30)")
     ap.add_argument("--profile-case", action="store_true",
                     help="run a reduced case of the same kernels for ncu (no timing)")
     args = ap.parse_args()
