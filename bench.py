@@ -300,7 +300,7 @@ def run_mixed(args, world, rank, sampler_uuid):
                    "gbps_in_solve": round(passes * a_bytes / (ms / steps / 1e3) / 1e9, 1)},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
                      "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-                     "traffic": _traffic_from_profile("mixed-bf16"),
+                     "traffic": _traffic_from_profile("mixed-bf16", "ax" if t_ax >= t_atx else "atx"),
                      "algorithmic_bytes_per_launch": a_bytes,
                      "ms_per_launch": round(dom_ms, 4),
                      "timing": f"{how}: main kernel + split-tile fixup per pass"},
@@ -530,7 +530,7 @@ def run_ours(args):
     dom = "gemm_simt_kernel<double,5,true> (A^T X pass)" if t_at >= t_an else \
         "gemm_simt_kernel<double,5,false> (A X pass)"
     achieved = flops / (dom_ms / 1e3) / 1e12
-    traffic = _traffic_from_profile()
+    traffic = _traffic_from_profile("plain-fp64", "atx" if t_at >= t_an else "ax")
     roofline = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 4),
                 "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
                 "frac": round(achieved / fp64_peak, 4),
@@ -627,17 +627,23 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def _traffic_from_profile(key="plain-fp64"):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary, if that summary was taken on the current kernel source."""
+def _traffic_from_profile(key="plain-fp64", pas="atx"):
+    """DRAM bytes per launch of the dominant kernel (`pas` = "ax" or "atx")
+    from the committed ncu summary, or None when the kernel's source has
+    changed since those counters were taken."""
+    import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(path):
-        return None
     try:
         with open(path) as f:
-            d = json.load(f)
-        return d.get(key)
-    except (OSError, ValueError):
+            ent = json.load(f)[key]
+        h = hashlib.sha256()
+        for name in ent["source_files"]:
+            with open(os.path.join(ROOT, "paper_2402_17794_gb300", "csrc", name), "rb") as f:
+                h.update(f.read())
+        if h.hexdigest() != ent["source_sha256"]:
+            return None
+        return ent[pas]["dram_bytes_per_launch"]
+    except (OSError, ValueError, KeyError):
         return None
 
 
