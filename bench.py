@@ -269,6 +269,7 @@ def run_mixed(args, world, rank, sampler_uuid):
     st = plan.status()
     if st != 0:
         raise RuntimeError(f"mixed solve failed: {R.rsvd_status_string(st)}")
+    sweeps, _ = R.rsvd_plan_diagnostics(plan.handle)
 
     # the tcgen05 passes alone (one BF16 operand slice, l = 160)
     X_n = torch.randn(l, n, device="cuda").to(torch.bfloat16)
@@ -293,7 +294,7 @@ def run_mixed(args, world, rank, sampler_uuid):
         "workload": w["desc"], "value": round(steps * world / (ms / 1e3), 3), "unit": "solves/s",
         "ms_per_solve": round(ms / steps, 4),
         "p50_ms": round(per[len(per) // 2], 4), "p99_ms": round(per[min(len(per) - 1, int(0.99 * len(per)))], 4),
-        "dtype": "bf16 A, fp32 accumulate", "passes_per_solve": passes,
+        "dtype": "bf16 A, fp32 accumulate", "passes_per_solve": passes, "jacobi_sweeps": sweeps,
         "a_pass": {"ms_ax": round(t_ax, 4), "ms_atx": round(t_atx, 4),
                    "gbps_ax": round(a_bytes / (t_ax / 1e3) / 1e9, 1),
                    "gbps_atx": round(a_bytes / (t_atx / 1e3) / 1e9, 1),

@@ -103,9 +103,10 @@ grouped_gemm_kernel(const Ctx<T>* __restrict__ ctx, int op, int iter) {
 }
 
 // Cholesky + inverse: which 0 -> (G, l) into R1/R1i, 1 -> into R2/R2i,
-// 2 -> (G, k) into R1/R1i (re-orthonormalisation of V_k).
+// 2 -> (G, k) into R1/R1i (re-orthonormalisation of V_k).  The register
+// variant serves FP32 problems with l <= 160, the shared-memory one the rest.
 template <typename T>
-__global__ void __launch_bounds__(SMALL_THREADS)
+__global__ void __launch_bounds__(dense::CHOL_THREADS)
 grouped_chol_kernel(const Ctx<T>* __restrict__ ctx, int which, int iter, int use_smem) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Ctx<T>& P = ctx[blockIdx.x];
@@ -114,7 +115,18 @@ grouped_chol_kernel(const Ctx<T>* __restrict__ ctx, int which, int iter, int use
   T* R = which == 1 ? P.R2 : P.R1;
   T* Ri = which == 1 ? P.R2i : P.R1i;
   T* W = use_smem ? reinterpret_cast<T*>(smem_raw) : P.cholw;
-  dense::chol_inv_body<T>(P.G, l, l, R, Ri, W, P.status);
+  dense::chol_inv_blocked<T, dense::CholPanel<T>::value>(P.G, l, l, R, Ri, W, P.status);
+}
+
+template <int E>
+__global__ void __launch_bounds__(dense::CHOL_REG_THREADS)
+grouped_chol_regs_kernel(const Ctx<float>* __restrict__ ctx, int which, int iter) {
+  const Ctx<float>& P = ctx[blockIdx.x];
+  if (!active(P.q, iter)) return;
+  const int l = which == 2 ? P.k : P.l;
+  float* R = which == 1 ? P.R2 : P.R1;
+  float* Ri = which == 1 ? P.R2i : P.R1i;
+  dense::chol_inv_regs<E>(P.G, l, l, R, Ri, P.status);
 }
 
 // Mt = (R2 R1)^T, the transposed R factor of B^T.
@@ -132,12 +144,13 @@ __global__ void grouped_tri_kernel(const Ctx<T>* __restrict__ ctx) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(SMALL_THREADS)
+__global__ void __launch_bounds__(dense::JACOBI_THREADS)
 grouped_jacobi_kernel(const Ctx<T>* __restrict__ ctx, int use_smem) {
   extern __shared__ __align__(16) unsigned char jsm_raw[];
   const Ctx<T>& P = ctx[blockIdx.x];
   T* Wm = use_smem ? reinterpret_cast<T*>(jsm_raw) : P.jw;
-  dense::jacobi_body<T>(P.Mt, P.l, P.l, P.sig, P.Um, P.l, nullptr, P.l, P.UsInv, Wm, P.status);
+  dense::jacobi_body<T>(P.Mt, P.l, P.l, P.sig, P.Um, P.l, nullptr, P.l, P.UsInv, Wm,
+                        dense::jacobi_ld<T>(P.l, use_smem != 0), P.status);
 }
 
 template <typename T>
@@ -152,13 +165,17 @@ __global__ void grouped_gaussian_kernel<double>(const Ctx<double>* __restrict__ 
     P.om[t] = omega::gaussian_value_f64(t, 0u, P.seed);   // om is n x l, ld n: index t = j*n + i
 }
 
+// FP32 batches draw Omega with the FP32 generator (24-bit uniforms, FP32
+// Box-Muller): the FP64 transcendentals run at the GPU's FP64 rate, and the
+// FP32 solve cannot resolve the difference.
 template <>
 __global__ void grouped_gaussian_kernel<float>(const Ctx<float>* __restrict__ ctx) {
   const Ctx<float>& P = ctx[blockIdx.y];
   const uint64_t total = (uint64_t)P.n * (uint64_t)P.l;
+  const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
   for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
        t += (uint64_t)gridDim.x * blockDim.x)
-    P.om[t] = (float)omega::gaussian_value_f64(t, 0u, P.seed);
+    P.om[t] = omega::gaussian_at_f32(t, 0u, k0, k1);
 }
 
 template <typename T>
@@ -240,16 +257,26 @@ int gop(rsvd_plan_t P, const Ctx<T>* d, const BatchShape& b, int op, int iter) {
 template <typename T>
 int gchol(rsvd_plan_t P, const Ctx<T>* d, const BatchShape& b, int which, int iter) {
   const int l = which == 2 ? b.max_k : b.max_l;
-  const size_t smem = ((size_t)l * l + 33 * (size_t)(l + 64)) * sizeof(T);
-  const size_t cap = 200 * 1024;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(grouped_chol_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)cap);
-    attr_set = true;
+  const size_t smem = dense::chol_work_elems(l) * sizeof(T);
+  const bool sm = smem <= dynamic_smem_cap((const void*)grouped_chol_kernel<T>);
+  if constexpr (sizeof(T) == 4) {
+    if (dense::chol_in_regs<T>(l)) {
+      // the block edge covers the batch's largest l; smaller problems leave
+      // their extra rows and columns at zero
+      const int nt = dense::CHOL_REG_THREADS;
+      switch (dense::chol_reg_edge(l)) {
+        case 1: grouped_chol_regs_kernel<1><<<b.count, nt, 0, P->stream>>>(d, which, iter); break;
+        case 2: grouped_chol_regs_kernel<2><<<b.count, nt, 0, P->stream>>>(d, which, iter); break;
+        case 3: grouped_chol_regs_kernel<3><<<b.count, nt, 0, P->stream>>>(d, which, iter); break;
+        case 4: grouped_chol_regs_kernel<4><<<b.count, nt, 0, P->stream>>>(d, which, iter); break;
+        default: grouped_chol_regs_kernel<5><<<b.count, nt, 0, P->stream>>>(d, which, iter);
+      }
+      note_launch();
+      RSVD_CK(cudaGetLastError());
+      return RSVD_OK;
+    }
   }
-  const bool sm = smem <= cap;
-  grouped_chol_kernel<T><<<b.count, SMALL_THREADS, sm ? smem : 0, P->stream>>>(d, which, iter,
+  grouped_chol_kernel<T><<<b.count, dense::CHOL_THREADS, sm ? smem : 0, P->stream>>>(d, which, iter,
                                                                                sm ? 1 : 0);
   note_launch();
   RSVD_CK(cudaGetLastError());
@@ -297,17 +324,13 @@ int solve_batched_t(rsvd_plan_t P, const Ctx<T>* d, const BatchShape& b) {
   if ((rc = gop<T>(P, d, b, OP_AT_QM_Z, -1))) return rc;
   if ((rc = gorth<T>(P, d, b, false, -1, false, true))) return rc;
   {
-    const int twoP = (b.max_l + 1) & ~1;
-    const size_t need = (size_t)b.max_l * twoP * sizeof(T);
-    const size_t cap = 200 * 1024;
-    static bool attr_set = false;
-    if (!attr_set) {
-      cudaFuncSetAttribute(grouped_jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)cap);
-      attr_set = true;
-    }
-    const bool sm = need <= cap;
-    grouped_jacobi_kernel<T><<<b.count, SMALL_THREADS, sm ? need : 0, P->stream>>>(d, sm ? 1 : 0);
+    // every problem's l <= max_l: the padded stride is not monotone in l
+    size_t need = 0;
+    for (int ll = 1; ll <= b.max_l; ++ll)
+      need = std::max(need, (size_t)dense::jacobi_ld<T>(ll, true) * ((ll + 1) & ~1) * sizeof(T));
+    const bool sm = need <= dynamic_smem_cap((const void*)grouped_jacobi_kernel<T>);
+    grouped_jacobi_kernel<T><<<b.count, dense::JACOBI_THREADS, sm ? need : 0, P->stream>>>(
+        d, sm ? 1 : 0);
     note_launch();
     RSVD_CK(cudaGetLastError());
   }

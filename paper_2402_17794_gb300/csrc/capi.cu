@@ -363,12 +363,42 @@ int rsvd_small_svd(rsvd_plan_t plan, const void* M, int l, int64_t ldm, void* si
 // Launch accounting
 // ---------------------------------------------------------------------------
 #include <atomic>
+#include <mutex>
 
 namespace {
 std::atomic<uint64_t> g_launches{0};
 }
 
 void rsvd::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+size_t rsvd::dynamic_smem_cap(const void* func) {
+  struct Entry {
+    const void* func;
+    int device;
+    size_t cap;
+  };
+  static Entry cache[64];
+  static int used = 0;
+  static std::mutex mu;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  for (int i = 0; i < used; ++i)
+    if (cache[i].func == func && cache[i].device == dev) return cache[i].cap;
+  int optin = 0;
+  cudaFuncAttributes fa{};
+  size_t cap = 48 * 1024;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+      cudaFuncGetAttributes(&fa, func) == cudaSuccess && (size_t)optin > fa.sharedSizeBytes) {
+    const size_t c = (size_t)optin - fa.sharedSizeBytes;
+    if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c) ==
+        cudaSuccess)
+      cap = c;
+  }
+  cudaGetLastError();  // a refused attribute leaves the 48 KB default, not a sticky error
+  if (used < 64) cache[used++] = Entry{func, dev, cap};
+  return cap;
+}
 
 extern "C" uint64_t rsvd_kernel_launches(void) {
   return g_launches.load(std::memory_order_relaxed);

@@ -28,9 +28,13 @@ template <typename T, int TN, bool TRANS>
 __global__ void __launch_bounds__(THREADS)
 gemm_simt_kernel(const T* __restrict__ A, int64_t lda, const T* __restrict__ X,
                  int64_t ldx, T* __restrict__ C, int64_t ldc, int64_t M, int64_t K, int N,
-                 int64_t k_per_split, int64_t part_stride) {
+                 int64_t k_per_split, int64_t part_stride, int x_upper) {
   const int64_t kb = (int64_t)blockIdx.z * k_per_split;
-  const int64_t ke = (kb + k_per_split < K) ? kb + k_per_split : K;
+  int64_t ke = (kb + k_per_split < K) ? kb + k_per_split : K;
+  if (x_upper) {  // X upper triangular: this column tile needs k < its last column + 1
+    const int64_t kc = (int64_t)(blockIdx.y + 1) * 16 * TN;
+    if (kc < ke) ke = kc;
+  }
   simt::gemm_tile<T, TN, TRANS>(A, lda, X, ldx, C + (int64_t)blockIdx.z * part_stride, ldc, M, N,
                                 (int64_t)blockIdx.x * BM, blockIdx.y * 16 * TN, kb, ke);
 }
@@ -54,10 +58,11 @@ void launch_tn(const GemmArgs<T>& g, dim3 grid, T* out, int64_t ldo, int64_t kps
                int64_t pstride, cudaStream_t st) {
   if (g.trans)
     gemm_simt_kernel<T, TN, true><<<grid, THREADS, 0, st>>>(g.A, g.lda, g.X, g.ldx, out, ldo, g.M,
-                                                            g.K, g.N, kps, pstride);
+                                                            g.K, g.N, kps, pstride, 0);
   else
     gemm_simt_kernel<T, TN, false><<<grid, THREADS, 0, st>>>(g.A, g.lda, g.X, g.ldx, out, ldo,
-                                                             g.M, g.K, g.N, kps, pstride);
+                                                             g.M, g.K, g.N, kps, pstride,
+                                                             g.x_upper ? 1 : 0);
   note_launch();
 }
 

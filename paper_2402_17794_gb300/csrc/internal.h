@@ -14,6 +14,11 @@ namespace rsvd {
 // call note_launch() once per <<<...>>>).
 void note_launch();
 
+// Largest dynamic shared memory a launch of kernel `func` may request on the
+// current device: the opt-in limit minus the kernel's static shared memory.
+// The kernel's attribute is raised to it on first use (cached per device).
+size_t dynamic_smem_cap(const void* func);
+
 constexpr int kMaxSplits = 32;      // split-K partial slices kept in workspace
 constexpr size_t kAlign = 256;
 
@@ -82,21 +87,34 @@ cudaError_t launch_gaussian(int64_t n, int l, uint64_t seed, uint32_t stream_id,
 // Tall-skinny GEMM on the CUDA cores:  C (M x N) = op(A) X,  op(A) = A (M x K,
 // lda) or A^T (A stored K x M, lda).  X is K x N (ldx).  Split-K partials go
 // to `part` (up to part_elems elements) when more than one split is used.
+// x_upper: X is upper triangular (K == N, op(A) = A); column c of the product
+// then only contracts over k <= c, so each column tile stops at its last column.
 template <typename T>
 struct GemmArgs {
   const T* A; int64_t lda; bool trans;
   const T* X; int64_t ldx;
   T* C; int64_t ldc;
   int64_t M, K; int N;
+  bool x_upper = false;
 };
 template <typename T>
 cudaError_t launch_gemm(const GemmArgs<T>& g, T* part, size_t part_elems, int num_sms,
                         cudaStream_t st);
 
+// Gram product G = Y^T Y (Y rows x l, ldy) on the CUDA cores, both triangles of
+// G (ldg) written; per-CTA partials (l*l elements each, at most num_sms of
+// them, bounded by part_elems) go to `part`.  gram_supported(l) tells whether
+// this kernel covers l (else use launch_gemm).
+template <typename T>
+bool gram_supported(int l);
+template <typename T>
+cudaError_t launch_gram(const T* Y, int64_t ldy, int64_t rows, int l, T* G, int64_t ldg, T* part,
+                        size_t part_elems, int num_sms, cudaStream_t st);
+
 // One-CTA Cholesky of the l x l Gram G (ldg) -> upper R (l x l, ld l) and
 // its inverse Rinv (ld l); deficient pivots zero the row of R and the row and
-// column of Rinv.  Sets status bits on non-finite input.  work: l*l + 33*(l+64)
-// elements (used when that does not fit in shared memory).
+// column of Rinv.  Sets status bits on non-finite input.  work: at least
+// l*(l+2) elements (used when that does not fit in shared memory).
 template <typename T>
 cudaError_t launch_chol_inv(const T* G, int64_t ldg, int l, T* R, T* Rinv, T* work,
                             DeviceStatus* status, cudaStream_t st);

@@ -111,9 +111,9 @@ int finish(rsvd_plan_t P, const Work<T>& W, int64_t m, int64_t n, int l, int k, 
   // V_k = B^T U~_k Sigma_k^-1, then one CholeskyQR pass restores orthonormality
   // to rounding (the product carries relative errors ~ eps sigma_1/sigma_i)
   if ((rc = gemm<T>(P, W.z, n, false, us_inv, l, W.tmp, n, n, l, k))) return rc;
-  if ((rc = gemm<T>(P, W.tmp, n, true, W.tmp, n, W.G, k, k, n, k))) return rc;
+  if ((rc = gram<T>(P, W.tmp, n, n, k, W.G))) return rc;
   RSVD_CK(launch_chol_inv<T>(W.G, k, k, W.R1, W.R1i, W.cholw, dstatus(P), P->stream));
-  if ((rc = gemm<T>(P, W.tmp, n, false, W.R1i, k, W.qb, n, n, k, k))) return rc;
+  if ((rc = gemm<T>(P, W.tmp, n, false, W.R1i, k, W.qb, n, n, k, k, true))) return rc;
   RSVD_CK(launch_finalize<T>(U, m, ldu, k, W.qb, n, VT, ldvt, W.sig, S, W.sign, P->stream));
   return RSVD_OK;
 }
@@ -213,16 +213,28 @@ bool plan_ready(rsvd_plan_t P) { return P && P->ws && P->ws_bytes >= P->lay.tota
 
 template <typename T>
 int gemm(rsvd_plan_t P, const T* A, int64_t lda, bool trans, const T* X, int64_t ldx, T* C,
-         int64_t ldc, int64_t M, int64_t K, int N) {
-  GemmArgs<T> g{A, lda, trans, X, ldx, C, ldc, M, K, N};
+         int64_t ldc, int64_t M, int64_t K, int N, bool x_upper) {
+  GemmArgs<T> g{A, lda, trans, X, ldx, C, ldc, M, K, N, x_upper};
   Work<T> W = work_of<T>(P);
   RSVD_CK(launch_gemm<T>(g, W.part, W.part_elems, P->num_sms, P->stream));
   return RSVD_OK;
 }
+
+// G (ld l) = Y^T Y for Y rows x l (ldy): upper-triangle Gram kernel, or the
+// general product when the kernel does not cover l.
+template <typename T>
+int gram(rsvd_plan_t P, const T* Y, int64_t ldy, int64_t rows, int l, T* G) {
+  if (!gram_supported<T>(l)) return gemm<T>(P, Y, ldy, true, Y, ldy, G, l, l, rows, l);
+  Work<T> W = work_of<T>(P);
+  RSVD_CK(launch_gram<T>(Y, ldy, rows, l, G, l, W.part, W.part_elems, P->num_sms, P->stream));
+  return RSVD_OK;
+}
 template int gemm<double>(rsvd_plan_t, const double*, int64_t, bool, const double*, int64_t,
-                          double*, int64_t, int64_t, int64_t, int);
+                          double*, int64_t, int64_t, int64_t, int, bool);
 template int gemm<float>(rsvd_plan_t, const float*, int64_t, bool, const float*, int64_t, float*,
-                         int64_t, int64_t, int64_t, int);
+                         int64_t, int64_t, int64_t, int, bool);
+template int gram<double>(rsvd_plan_t, const double*, int64_t, int64_t, int, double*);
+template int gram<float>(rsvd_plan_t, const float*, int64_t, int64_t, int, float*);
 
 template <typename T>
 int orth(rsvd_plan_t P, const T* Y, int64_t rows, int l, int64_t ldy, T* Q, int64_t ldq, T* Rprod,
@@ -231,13 +243,13 @@ int orth(rsvd_plan_t P, const T* Y, int64_t rows, int l, int64_t ldy, T* Q, int6
   DeviceStatus* st = dstatus(P);
   int rc;
   // pass 1: G = Y^T Y = R1^T R1, T1 = Y R1^-1
-  if ((rc = gemm<T>(P, Y, ldy, true, Y, ldy, W.G, l, l, rows, l))) return rc;
+  if ((rc = gram<T>(P, Y, ldy, rows, l, W.G))) return rc;
   RSVD_CK(launch_chol_inv<T>(W.G, l, l, W.R1, W.R1i, W.cholw, st, P->stream));
-  if ((rc = gemm<T>(P, Y, ldy, false, W.R1i, l, W.tmp, rows, rows, l, l))) return rc;
+  if ((rc = gemm<T>(P, Y, ldy, false, W.R1i, l, W.tmp, rows, rows, l, l, true))) return rc;
   // pass 2: G = T1^T T1 = R2^T R2, Q = T1 R2^-1
-  if ((rc = gemm<T>(P, W.tmp, rows, true, W.tmp, rows, W.G, l, l, rows, l))) return rc;
+  if ((rc = gram<T>(P, W.tmp, rows, rows, l, W.G))) return rc;
   RSVD_CK(launch_chol_inv<T>(W.G, l, l, W.R2, W.R2i, W.cholw, st, P->stream));
-  if (Q && (rc = gemm<T>(P, W.tmp, rows, false, W.R2i, l, Q, ldq, rows, l, l))) return rc;
+  if (Q && (rc = gemm<T>(P, W.tmp, rows, false, W.R2i, l, Q, ldq, rows, l, l, true))) return rc;
   if (Rprod) RSVD_CK(launch_tri_product<T>(W.R2, W.R1, l, Rprod, transpose_R, P->stream));
   return RSVD_OK;
 }

@@ -43,9 +43,14 @@ MixedWork mixed_work_of(rsvd_plan_t P);
 DeviceStatus* dstatus(rsvd_plan_t P);
 bool plan_ready(rsvd_plan_t P);
 
+// C = op(A) X on the CUDA cores (see GemmArgs); x_upper: X is upper triangular.
 template <typename T>
 int gemm(rsvd_plan_t P, const T* A, int64_t lda, bool trans, const T* X, int64_t ldx, T* C,
-         int64_t ldc, int64_t M, int64_t K, int N);
+         int64_t ldc, int64_t M, int64_t K, int N, bool x_upper = false);
+
+// G (l x l, ld l) = Y^T Y, both triangles.
+template <typename T>
+int gram(rsvd_plan_t P, const T* Y, int64_t ldy, int64_t rows, int l, T* G);
 
 // CholeskyQR2: Q = orth(Y) (Q may be NULL: only R is formed); Rprod, if
 // non-NULL, receives R2 R1 (or its transpose), the R factor of Y = Q R.

@@ -34,206 +34,362 @@ __device__ __forceinline__ void set_flag(DeviceStatus* s, int code) {
   atomicOr(&s->flags, 1 << code);
 }
 
-// G (ldg) -> R (ld l, upper; lower part zeroed), Rinv (ld l, upper).
-// W (l*l) and the scratch S (33*(l+64) elements) live in dynamic shared
-// memory when they fit, else in `gwork` (l*l + 33*(l+64) elements).
-//
-// Cholesky: right-looking, one pivot per step, trailing update of the upper
-// triangle by a 32 x 32 thread grid.  Inverse (in place, LAPACK trtri's
-// block-column order with 32 x 32 blocks):
-//   1. every diagonal block D_b is inverted in parallel, one warp per block
-//      and one lane per column (back substitution against a copy of D_b);
-//   2. for block columns b = 1, 2, ...:  X(0:b, b) = -X(0:b, 0:b) R(0:b, b) X(b, b)
-//      as two small dense products over all threads.
-template <typename T>
-__device__ __forceinline__ void chol_inv_body(const T* __restrict__ G, int64_t ldg, int l,
-                                              T* __restrict__ R, T* __restrict__ Rinv,
-                                              T* __restrict__ W, DeviceStatus* status) {
-  T* S = W + (int64_t)l * l;                                  // 33 x (l + 64) scratch
-  __shared__ T s_maxdiag;
-  __shared__ T s_r, s_inv;
-  __shared__ int s_bad;
-  __shared__ int s_deficient;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int tx = tid & 31, ty = tid >> 5;   // 32 x 32 grid
+// Leading dimension of the Cholesky work matrix: odd, so that a warp reading
+// one row (stride ld) touches 32 distinct banks.
+__host__ __device__ constexpr int chol_ld(int l) { return (l + 1) | 1; }
 
-  for (int t = tid; t < l * l; t += nt) {
-    int i = t % l, j = t / l;
-    W[t] = (i <= j) ? G[i + (int64_t)j * ldg] : T(0);
-  }
-  if (tid == 0) {
-    s_bad = 0;
-    s_deficient = 0;
-  }
-  __syncthreads();
-  if (tid == 0) {
+// Elements of work the blocked Cholesky needs: l x chol_ld(l).
+__host__ __device__ constexpr size_t chol_work_elems(int l) { return (size_t)l * chol_ld(l); }
+
+// Both Cholesky variants below (blocked, and register-resident for FP32
+// l <= 160) compute G = R^T R and R^-1 by one elimination
+// on [G | I] (Gauss without pivoting, stable for an SPD matrix): with
+// G = L D L^T, L unit lower triangular,
+//   step j, every row i > j:  row_i -= (G_ij / D_j) row_j
+// turns G's upper triangle into D L^T and the identity into L^-1.  Both live
+// in one matrix W: W[i][c] for c >= i is the upper part (D L^T), for c < i
+// the strictly lower part of L^-1 (its unit diagonal is implicit).  Then
+//   R = D^{1/2} L^T:       R[i][c]    = W[i][c] / sqrt(D_i)
+//   R^-1 = L^-T D^{-1/2}:  R^-1[i][c] = W[c][i] / sqrt(D_c)   (i < c)
+// Step j reads only row j and writes only rows below it, so one barrier per
+// pivot orders the steps.  A pivot D_j <= tol marks a dependent column: its
+// multipliers and 1/sqrt(D_j) are taken as zero, so row j of R and column j
+// of R^-1 vanish (Q = Y R^-1 gets a zero column) and the count is recorded.
+
+// Diagonal check of G: returns false (after zeroing R, Rinv and raising
+// RSVD_ERR_NONFINITE) on a non-finite diagonal; else the drop tolerance.
+template <typename T>
+__device__ __forceinline__ bool chol_prologue(const T* __restrict__ G, int64_t ldg, int l,
+                                              T* __restrict__ R, T* __restrict__ Rinv,
+                                              DeviceStatus* status, T* tol_out) {
+  __shared__ T s_maxdiag;
+  __shared__ int s_bad;
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid < 32) {
     T mx = T(0);
     int bad = 0;
-    for (int j = 0; j < l; ++j) {
-      T d = W[j + j * l];
+    for (int j = lane; j < l; j += 32) {
+      const T d = G[j + (int64_t)j * ldg];
       if (!isfinite(d)) bad = 1;
       mx = fmax(mx, fabs(d));
     }
-    s_maxdiag = mx;
-    s_bad = bad;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    if (lane == 0) {
+      s_maxdiag = mx;
+      s_bad = bad;
+    }
   }
   __syncthreads();
   if (s_bad) {
-    for (int t = tid; t < l * l; t += nt) {
+    for (int t = tid; t < l * l; t += blockDim.x) {
       R[t] = T(0);
       Rinv[t] = T(0);
     }
     if (tid == 0) set_flag(status, RSVD_ERR_NONFINITE);
-    return;
+    return false;
   }
-  const T tol = Eps<T>::drop_factor(l) * Eps<T>::value * s_maxdiag;
-
-  // ---- Cholesky: G = R^T R on the upper triangle, 32-wide panels ----
-  // Per panel k (rows/columns k0 .. k0+kw-1):
-  //  (i)   warp 0 factors the diagonal block in a padded copy (S, 32 x 33);
-  //  (ii)  the panel rows R[k0:k0+kw, c] = D^-T G[k0:k0+kw, c] for the columns
-  //        right of the block, one thread per column, in a transposed padded
-  //        copy P (c-major, stride 33) so threads touch distinct banks;
-  //  (iii) trailing update G[i][c] -= sum_t P[i][t] P[c][t] for i <= c.
-  T* Dg = S;                 // 32 x 33 diagonal block (column-major, ld 33)
-  T* Dinv = S + 32 * 33;     // 32 reciprocal pivots
-  T* Pp = S + 33 * 33;       // (l - k0 - kw) x 33 transposed panel
-  for (int k0 = 0; k0 < l; k0 += 32) {
-    const int kw = min(32, l - k0);
-    const int c_beg = k0 + kw, nc = l - c_beg;
-    // load the diagonal block (upper) and the panel rows (transposed)
-    for (int t = tid; t < 32 * 32; t += nt) {
-      const int i = t & 31, c = t >> 5;
-      Dg[i + c * 33] = (i < kw && c < kw && i <= c) ? W[k0 + i + (k0 + c) * l] : T(0);
-    }
-    for (int t = tid; t < nc * 32; t += nt) {
-      const int i = t & 31, c = t >> 5;   // i: panel row, c: column offset
-      Pp[c * 33 + i] = (i < kw) ? W[k0 + i + (c_beg + c) * l] : T(0);
-    }
-    __syncthreads();
-    if (ty == 0) {
-      // (i) one warp, lane = column within the block
-      const int c = tx;
-      for (int j = 0; j < kw; ++j) {
-        const T d = Dg[j + j * 33];
-        T r, inv;
-        if (!(d > tol)) {
-          r = T(0);
-          inv = T(0);
-          if (c == 0) s_deficient++;
-        } else {
-          r = sqrt(d);
-          inv = T(1) / r;
-        }
-        __syncwarp();
-        if (c > j && c < kw) Dg[j + c * 33] *= inv;
-        if (c == j) {
-          Dg[j + j * 33] = r;
-          Dinv[j] = inv;
-        }
-        __syncwarp();
-        if (c > j && c < kw) {
-          const T rjc = Dg[j + c * 33];
-          for (int i = j + 1; i <= c; ++i) Dg[i + c * 33] -= Dg[j + i * 33] * rjc;
-        }
-        __syncwarp();
-      }
-    }
-    __syncthreads();
-    // (ii) panel rows: solve D^T x = g per column (forward substitution)
-    for (int c = tid; c < nc; c += nt) {
-      T* x = Pp + c * 33;
-      for (int i = 0; i < kw; ++i) {
-        T acc = x[i];
-        for (int t2 = 0; t2 < i; ++t2) acc -= Dg[t2 + i * 33] * x[t2];
-        x[i] = acc * Dinv[i];   // a dropped pivot (Dinv 0) zeroes the row
-      }
-    }
-    __syncthreads();
-    // write the factored block and panel rows back; (iii) trailing update
-    for (int t = tid; t < 32 * 32; t += nt) {
-      const int i = t & 31, c = t >> 5;
-      if (i < kw && c < kw && i <= c) W[k0 + i + (k0 + c) * l] = Dg[i + c * 33];
-    }
-    for (int t = tid; t < nc * 32; t += nt) {
-      const int i = t & 31, c = t >> 5;
-      if (i < kw) W[k0 + i + (c_beg + c) * l] = Pp[c * 33 + i];
-    }
-    for (int cc = ty; cc < nc; cc += 32) {
-      const T* pc = Pp + cc * 33;
-      for (int ii = tx; ii <= cc; ii += 32) {
-        const T* pi = Pp + ii * 33;
-        T acc = T(0);
-#pragma unroll 8
-        for (int t2 = 0; t2 < kw; ++t2) acc = fma(pi[t2], pc[t2], acc);
-        W[c_beg + ii + (c_beg + cc) * l] -= acc;
-      }
-    }
-    __syncthreads();
-  }
-  for (int t = tid; t < l * l; t += nt) {
-    int i = t % l, j = t / l;
-    R[t] = (i <= j) ? W[t] : T(0);
-  }
-  __syncthreads();
-
-  // ---- Inverse, step 1: diagonal 32 x 32 blocks, one warp each ----
-  const int nb = (l + 31) / 32;
-  // copy every diagonal block to S (block b at S + b*1024, column-major 32 x 32)
-  for (int t = tid; t < nb * 1024; t += nt) {
-    const int b = t >> 10, e = t & 1023, i = e & 31, c = e >> 5;
-    const int gi = b * 32 + i, gc = b * 32 + c;
-    S[t] = (gi < l && gc < l) ? W[gi + gc * l] : T(0);
-  }
-  __syncthreads();
-  for (int b = ty; b < nb; b += 32) {
-    const int c = tx, gc = b * 32 + c;
-    const T* D = S + b * 1024;
-    if (gc < l) {
-      const T dcc = D[c + c * 32];
-      if (dcc == T(0)) {
-        for (int i = 0; i <= c; ++i) W[b * 32 + i + gc * l] = T(0);
-      } else {
-        W[gc + gc * l] = T(1) / dcc;
-        for (int i = c - 1; i >= 0; --i) {
-          const T dii = D[i + i * 32];
-          T acc = T(0);
-          for (int t2 = i + 1; t2 <= c; ++t2) acc = fma(D[i + t2 * 32], W[b * 32 + t2 + gc * l], acc);
-          W[b * 32 + i + gc * l] = (dii == T(0)) ? T(0) : -acc / dii;
-        }
-      }
-    }
-  }
-  __syncthreads();
-
-  // ---- Inverse, step 2: block columns left to right ----
-  for (int bj = 1; bj < nb; ++bj) {
-    const int c0 = bj * 32, cw = min(32, l - c0);
-    const int rows = c0;  // rows 0 .. c0-1
-    // (a) S(r, c) = sum_{u=r}^{c0-1} X[r][u] R[u][c0+c]   (X upper, already final)
-    for (int t = tid; t < rows * cw; t += nt) {
-      const int r = t % rows, c = t / rows;
-      T acc = T(0);
-      for (int u = r; u < c0; ++u) acc = fma(W[r + u * l], W[u + (c0 + c) * l], acc);
-      S[r + c * rows] = acc;
-    }
-    __syncthreads();
-    // (b) X[r][c0+c] = - sum_{s=0}^{c} S(r, s) X[c0+s][c0+c]
-    for (int t = tid; t < rows * cw; t += nt) {
-      const int r = t % rows, c = t / rows;
-      T acc = T(0);
-      for (int s2 = 0; s2 <= c; ++s2) acc = fma(S[r + s2 * rows], W[c0 + s2 + (c0 + c) * l], acc);
-      W[r + (c0 + c) * l] = -acc;
-    }
-    __syncthreads();
-  }
-  for (int t = tid; t < l * l; t += nt) {
-    int i = t % l, j = t / l;
-    Rinv[t] = (i <= j) ? W[t] : T(0);
-  }
-  if (tid == 0 && s_deficient) atomicAdd(&status->deficient, s_deficient);
+  *tol_out = Eps<T>::drop_factor(l) * Eps<T>::value * s_maxdiag;
+  return true;
 }
 
+// 1/D, 1/sqrt(D) and sqrt(D) of a kept pivot.  FP32: rsqrt plus one Newton
+// step (y <- y (3 - D y^2) / 2), a few ulp from the rounded values, which the
+// elimination's own rounding dominates.  FP64: correctly rounded operations.
+__device__ __forceinline__ void pivot_scales(float d, float& invd, float& rs, float& sq) {
+  float y = rsqrtf(d);
+  y = y * (1.5f - 0.5f * d * y * y);
+  rs = y;
+  invd = y * y;
+  sq = d * y;
+}
+__device__ __forceinline__ void pivot_scales(double d, double& invd, double& rs, double& sq) {
+  sq = sqrt(d);
+  rs = 1.0 / sq;
+  invd = 1.0 / d;
+}
+
+// Step A of the blocked Cholesky, run by one warp: eliminates inside the
+// nb x nb diagonal block [p0, p0 + nb)^2 of W.  Lane t holds block column t
+// in registers; row j's value at block column r comes from lane r by a
+// shuffle, so the pivots run without shared-memory round trips.
+template <typename T, int NB>
+__device__ __forceinline__ void chol_block_factor(T* __restrict__ W, int ld, int p0, int nb, T tol,
+                                                  T* s_invd, T* s_rs, T* s_sq, int* s_def) {
+  const int t = threadIdx.x & 31;
+  const bool col_ok = t < nb;
+  const int c = p0 + t;
+  T col[NB];
+#pragma unroll
+  for (int r = 0; r < NB; ++r) col[r] = (col_ok && r < nb) ? W[p0 + r + c * ld] : T(0);
+#pragma unroll
+  for (int jj = 0; jj < NB; ++jj) {
+    if (jj < nb) {
+      const T d = __shfl_sync(0xffffffffu, col[jj], jj);
+      T invd = T(0), rs = T(0), sq = T(0);
+      const bool keep = d > tol;
+      if (sizeof(T) == 4 || t == 0) {
+        if (keep) pivot_scales(d, invd, rs, sq);
+      }
+      if (sizeof(T) == 8) invd = __shfl_sync(0xffffffffu, invd, 0);
+      // one lane records the pivot (FP32: lane jj, every lane has the scales;
+      // FP64: lane 0, which formed them)
+      if (t == (sizeof(T) == 4 ? jj : 0)) {
+        s_invd[p0 + jj] = invd;
+        s_rs[p0 + jj] = rs;
+        s_sq[p0 + jj] = sq;
+        if (!keep) atomicAdd(s_def, 1);
+      }
+      const T wj = col[jj];
+      // per lane (no branches): t == jj starts column j of L^-1; t < jj updates
+      // L^-1 rows below j; t > jj updates the Schur complement rows j < r <= t
+#pragma unroll
+      for (int r = jj + 1; r < NB; ++r) {
+        const T f = __shfl_sync(0xffffffffu, col[jj], r) * invd;   // W[j][p0 + r] * invd
+        const T upd = fma(-f, wj, col[r]);
+        const bool live = col_ok && r < nb;
+        const T nv = (t == jj) ? -f : ((t < jj || r <= t) ? upd : col[r]);
+        col[r] = live ? nv : col[r];
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < NB; ++r)
+    if (col_ok && r < nb) W[p0 + r + c * ld] = col[r];
+}
+
+// Blocked variant (FP64, and FP32 beyond l = 160): panels of NB pivots.  W:
+// chol_work_elems(l) elements (shared memory when it fits, else global).  Per
+// panel P = [p0, p1):
+//  A. one warp eliminates inside the NB x NB diagonal block only (lane =
+//     block column), leaving D_P, (D L^T)_PP and (L^-1)_PP in place;
+//  B. the panel rows' other columns take the panel's row operations:
+//     W[P][c] <- (L^-1)_PP W[P][c]  (c < p0: L^-1 part, c >= p1: G part);
+//  C. every row below the panel takes all NB pivots at once:
+//     W[i][c] -= sum_{j in P} (W[j][i] / D_j) M[j][c]   for c < p1 or c >= i,
+//     with M = the panel rows and, inside the block, L^-1's unit diagonal.
+// The multiplier of row i for pivot j is read from the final panel row j
+// (the Schur complement is symmetric), so the NB pivots commute into one
+// rank-NB update.  Two barriers per panel instead of one per pivot.
+template <typename T, int NB>
+__device__ __forceinline__ void chol_inv_blocked(const T* __restrict__ G, int64_t ldg, int l,
+                                                 T* __restrict__ R, T* __restrict__ Rinv,
+                                                 T* __restrict__ W, DeviceStatus* status) {
+  constexpr int BMAX = 16;  // step B elements per thread: NB * (l - NB) <= BMAX * blockDim.x
+  __shared__ T s_invd[RSVD_L_MAX + 32], s_rs[RSVD_L_MAX + 32], s_sq[RSVD_L_MAX + 32];
+  __shared__ int s_def;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
+  const int ld = chol_ld(l);
+  T tol;
+  for (int t = tid; t < l * l; t += nt) {
+    const int i = t % l, c = t / l;
+    W[i + c * ld] = (i <= c) ? G[i + (int64_t)c * ldg] : T(0);
+  }
+  if (tid == 0) s_def = 0;
+  if (!chol_prologue<T>(G, ldg, l, R, Rinv, status, &tol)) return;
+
+  for (int p0 = 0; p0 < l; p0 += NB) {
+    const int p1 = (p0 + NB < l) ? p0 + NB : l;
+    const int nb = p1 - p0;
+    // ---- A: the diagonal block, one warp, lane = block column ----
+    if (warp == 0) chol_block_factor<T, NB>(W, ld, p0, nb, tol, s_invd, s_rs, s_sq, &s_def);
+    __syncthreads();
+    // ---- B: panel rows, columns outside the block ----
+    const int nco = l - nb;
+    if (nco > 0) {
+      T bv[BMAX];
+#pragma unroll
+      for (int k = 0; k < BMAX; ++k) {
+        const int e = tid + k * nt;
+        if (e < nb * nco) {
+          const int ii = e / nco, cc = e - ii * nco;
+          const int c = cc < p0 ? cc : cc + nb, i = p0 + ii;
+          T acc = W[i + c * ld];
+          for (int r = 0; r < ii; ++r) acc = fma(W[i + (p0 + r) * ld], W[p0 + r + c * ld], acc);
+          bv[k] = acc;
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < BMAX; ++k) {
+        const int e = tid + k * nt;
+        if (e < nb * nco) {
+          const int ii = e / nco, cc = e - ii * nco;
+          const int c = cc < p0 ? cc : cc + nb;
+          W[p0 + ii + c * ld] = bv[k];
+        }
+      }
+      __syncthreads();
+    }
+    // ---- C: rows below the panel, rank-nb update ----
+    for (int rb = p1; rb < l; rb += 32) {
+      const int i = rb + lane;
+      T f[NB];
+#pragma unroll
+      for (int jj = 0; jj < NB; ++jj)
+        f[jj] = (jj < nb && i < l) ? W[p0 + jj + i * ld] * s_invd[p0 + jj] : T(0);
+      if (i < l) {
+        for (int c = warp; c < l; c += nwarps) {
+          if (c >= p1 && c < i) continue;   // row i's L^-1 part beyond the panel is still zero
+          T acc = T(0);
+          if (c >= p0 && c < p1) {          // inside the block: L^-1 with its unit diagonal
+            const int jc = c - p0;
+#pragma unroll
+            for (int jj = 0; jj < NB; ++jj)
+              if (jj >= jc && jj < nb)
+                acc = fma(f[jj], jj == jc ? T(1) : W[p0 + jj + c * ld], acc);
+          } else {
+#pragma unroll
+            for (int jj = 0; jj < NB; ++jj)
+              if (jj < nb) acc = fma(f[jj], W[p0 + jj + c * ld], acc);
+          }
+          W[i + c * ld] -= acc;
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  for (int t = tid; t < l * l; t += nt) {
+    const int i = t % l, c = t / l;
+    T r = T(0), ri = T(0);
+    if (i == c) {
+      r = s_sq[i];
+      ri = s_rs[i];
+    } else if (i < c) {
+      r = W[i + c * ld] * s_rs[i];
+      ri = W[c + i * ld] * s_rs[c];
+    }
+    R[t] = r;
+    Rinv[t] = ri;
+  }
+  if (tid == 0 && s_def) atomicAdd(&status->deficient, s_def);
+}
+
+// Threads of a blocked-Cholesky CTA (NB * (l - NB) <= 16 * CHOL_THREADS for l <= 288).
+constexpr int CHOL_THREADS = 512;
+
+// Panel width of the blocked variant: NB multipliers per thread in step C.
+template <typename T>
+struct CholPanel {
+  static constexpr int value = sizeof(T) == 4 ? 32 : 16;
+};
+
+// Register variant (FP32, l <= 32 E): 1024 threads as a 32 x 32 grid;
+// thread (tr, tc) = (lane, warp) holds W[tr + 32 a][tc + 32 b] (a, b < E) in
+// registers for the whole factorisation.  Row j is published to shared memory
+// by its holders at the end of step j - 1, so a step is: read row j at this
+// thread's rows (distinct per lane) and columns (one per warp: a broadcast),
+// at most E x E multiply-adds, publish row j + 1, one barrier.  Blocks of
+// rows that are final are skipped; with eight warps per scheduler the FMA
+// and shared-memory latencies are hidden.
+constexpr int CHOL_REG_THREADS = 1024;
+
+template <int E>
+__device__ __forceinline__ void chol_inv_regs(const float* __restrict__ G, int64_t ldg, int l,
+                                              float* __restrict__ R, float* __restrict__ Rinv,
+                                              DeviceStatus* status) {
+  constexpr int N = 32 * E;
+  __shared__ float s_row[2][N];
+  __shared__ float s_rs[N], s_sq[N];
+  __shared__ int s_def;
+  const int tid = threadIdx.x;
+  const int tr = tid & 31, tc = tid >> 5;
+  const bool diag_upper = tr <= tc;
+  float w[E][E];
+#pragma unroll
+  for (int a = 0; a < E; ++a)
+#pragma unroll
+    for (int b = 0; b < E; ++b) {
+      const int i = tr + 32 * a, c = tc + 32 * b;
+      w[a][b] = (i < l && c < l && i <= c) ? G[i + (int64_t)c * ldg] : 0.f;
+    }
+  if (tid == 0) s_def = 0;
+  float tol;
+  if (!chol_prologue<float>(G, ldg, l, R, Rinv, status, &tol)) return;
+  // publish row 0 (zeros past l)
+  if (tr == 0) {
+#pragma unroll
+    for (int b = 0; b < E; ++b) s_row[0][tc + 32 * b] = w[0][b];
+  }
+  __syncthreads();
+  for (int j = 0; j < l; ++j) {
+    const float* row = s_row[j & 1];
+    // every thread forms 1/D_j from the published pivot (no divergent
+    // divide on the critical path); thread 0 records the scales
+    const float d = row[j];
+    const bool keep = d > tol;
+    float invd = 0.f, rs = 0.f, sq = 0.f;
+    if (keep) pivot_scales(d, invd, rs, sq);
+    if (tid == 0) {
+      s_rs[j] = rs;
+      s_sq[j] = sq;
+      if (!keep) ++s_def;
+    }
+    const int a0 = (j + 1) >> 5;            // blocks a < a0 hold only final rows
+    float wu[E], wl[E], wd[E];
+#pragma unroll
+    for (int b = 0; b < E; ++b) {
+      const int c = tc + 32 * b;
+      wu[b] = row[c];
+      wl[b] = (c < j) ? wu[b] : (c == j ? 1.f : 0.f);
+      wd[b] = diag_upper ? wu[b] : wl[b];
+    }
+#pragma unroll
+    for (int a = 0; a < E; ++a) {
+      if (a < a0) continue;
+      const int i = tr + 32 * a;
+      const float f = (i > j) ? row[i] * invd : 0.f;
+#pragma unroll
+      for (int b = 0; b < E; ++b)
+        w[a][b] = fmaf(-f, (a < b) ? wu[b] : (a > b ? wl[b] : wd[b]), w[a][b]);
+    }
+    // publish row j + 1 (its holders are the lanes tr == (j + 1) % 32)
+    const int jn = j + 1;
+    if (jn < l && tr == (jn & 31)) {
+      const int an = jn >> 5;
+      float* nrow = s_row[jn & 1];
+#pragma unroll
+      for (int a = 0; a < E; ++a)
+        if (a == an) {
+#pragma unroll
+          for (int b = 0; b < E; ++b) nrow[tc + 32 * b] = w[a][b];
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < E; ++a)
+#pragma unroll
+    for (int b = 0; b < E; ++b) {
+      const int i = tr + 32 * a, c = tc + 32 * b;
+      if (i >= l || c >= l) continue;
+      if (i == c) {
+        R[i + i * l] = s_sq[i];
+        Rinv[i + i * l] = s_rs[i];
+      } else if (i < c) {
+        R[i + c * l] = w[a][b] * s_rs[i];
+        Rinv[c + i * l] = 0.f;
+      } else {
+        R[i + c * l] = 0.f;
+        Rinv[c + i * l] = w[a][b] * s_rs[i];
+      }
+    }
+  if (tid == 0 && s_def) atomicAdd(&status->deficient, s_def);
+}
+
+// Block edge of the register variant for l (0: not covered).
+__host__ __device__ constexpr int chol_reg_edge(int l) { return l <= 160 ? (l + 31) / 32 : 0; }
+
+// Whether (T, l) takes the register variant.
+template <typename T>
+__host__ __device__ constexpr bool chol_in_regs(int l) {
+  return sizeof(T) == 4 && l <= 160;
+}
 
 // ---------------------------------------------------------------------------
 // One-sided Jacobi
@@ -255,113 +411,179 @@ __device__ __forceinline__ int rr_player(int pos, int r, int twoP) {
   return 1 + v;
 }
 
-// Work layout: Wm (l x twoP) and, if V is accumulated, Wv (l x twoP), both
-// column-major with ld l; in dynamic shared memory when they fit, else in
-// `gwork`.  Each round of the round-robin ordering runs in three phases so
-// that the FP64 pipe (2 lanes per clock per SM) is spent on useful work:
-//   A. G threads per column pair form partial |c_p|^2, |c_q|^2, c_p.c_q over
-//      interleaved rows and reduce them with shuffles inside the group;
-//   B. one thread per pair turns (a, b, g) into a rotation (c, s);
-//   C. the G threads of each pair apply it to their rows.
+// Threads a Jacobi CTA runs with: P column pairs x G threads per pair, G a
+// power of two chosen so that P * G <= JACOBI_THREADS.
+constexpr int JACOBI_THREADS = 640;
+
+__host__ __device__ inline int jacobi_group(int l) {
+  const int P = ((l + 1) & ~1) / 2;
+  int G = 32;
+  while (G > 1 && P * G > JACOBI_THREADS) G >>= 1;
+  return G;
+}
+
+// Column stride of the Jacobi work matrix.  FP32 in shared memory: columns
+// padded to a stride of G (mod 32) elements, so the 32/G column pairs a warp
+// works on start in distinct banks.  Otherwise l.
+template <typename T>
+__host__ __device__ inline int jacobi_ld(int l, bool in_smem) {
+  const int G = jacobi_group(l);
+  if (sizeof(T) != 4 || !in_smem || G == 32) return l;
+  return (l + 31) / 32 * 32 + G;
+}
+
+// Rows of a column pair a thread keeps in registers across one round.
+template <typename T>
+struct JacobiRegs {
+  static constexpr int value = sizeof(T) == 4 ? 20 : 10;
+};
+
+// Work layout: Wm (ldw x twoP) and, if V is accumulated, Wv (ldw x twoP),
+// column-major; in dynamic shared memory when they fit, else in `gwork`.
+// Round-robin ordering; in one round the G threads of each column pair load
+// their rows of both columns (into registers when they fit) and form partial
+// |c_p|^2, |c_q|^2, c_p.c_q, butterfly-reduced within the group (every lane
+// ends with the same bits: floating addition is commutative).  FP32: every
+// lane then derives the same rotation (Rutishauser) and applies it to the rows
+// it holds -- one barrier per round.  FP64: the rotation costs tens of FP64
+// operations at 2 per clock per SM, so one thread per pair forms it between
+// two barriers and the group then applies it.
 template <typename T>
 __device__ __forceinline__ void jacobi_body(const T* __restrict__ M, int l, int64_t ldm,
                                             T* __restrict__ sig, T* __restrict__ Um, int64_t ldu,
                                             T* __restrict__ Vm, int64_t ldv,
-                                            T* __restrict__ UsInv, T* __restrict__ Wm,
+                                            T* __restrict__ UsInv, T* __restrict__ Wm, int ldw,
                                             DeviceStatus* status) {
+  constexpr int RMAX = JacobiRegs<T>::value;
+  constexpr bool kFused = sizeof(T) == 4;
   const int twoP = (l + 1) & ~1;  // even number of columns (one zero column if l is odd)
   const int P = twoP / 2;
   const bool want_v = Vm != nullptr;
-  T* Wv = Wm + (int64_t)l * twoP;
+  T* Wv = Wm + (int64_t)ldw * twoP;
   __shared__ int s_rot;
   __shared__ T s_norm[RSVD_L_MAX + 1];
-  __shared__ T s_abg[(RSVD_L_MAX + 1) / 2][3];
-  __shared__ T s_cs[(RSVD_L_MAX + 1) / 2][2];
+  __shared__ T s_abg[kFused ? 1 : (RSVD_L_MAX + 1) / 2][3];
+  __shared__ T s_cs[kFused ? 1 : (RSVD_L_MAX + 1) / 2][2];
   const int tid = threadIdx.x, nt = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, nwarps = nt >> 5;
-  // threads per pair: power of two, at most 16 rows each
-  int G = 1;
-  while (G < 32 && (l + G - 1) / G > 16) G <<= 1;
+  const int G = jacobi_group(l);
   const int items = P * G;
-  const int items_pad = (items + 31) & ~31;
+  const int R = (l + G - 1) / G;          // rows per thread
+  const bool in_regs = R <= RMAX;
 
   for (int t = tid; t < l * twoP; t += nt) {
     int i = t % l, j = t / l;
-    Wm[t] = (j < l) ? M[i + (int64_t)j * ldm] : 0.0;
-    if (want_v) Wv[t] = (i == j) ? 1.0 : 0.0;
+    Wm[i + (int64_t)j * ldw] = (j < l) ? M[i + (int64_t)j * ldm] : T(0);
+    if (want_v) Wv[i + (int64_t)j * ldw] = (i == j) ? T(1) : T(0);
   }
   if (tid == 0) s_rot = 0;
   __syncthreads();
   const T tol = sqrt((T)l) * Eps<T>::value;
+  const int pr = tid / G, sub = tid % G;
+  const bool active = tid < items;
   int sweep = 0;
   const int max_sweeps = 30;
   for (; sweep < max_sweeps; ++sweep) {
     for (int r = 0; r < twoP - 1; ++r) {
-      // A: partial dot products
-      for (int it = tid; it < items_pad; it += nt) {
-        const int pr = it / G, sub = it % G;
-        T a = 0.0, b = 0.0, g = 0.0;
-        if (it < items) {
-          int p = rr_player(pr, r, twoP), q = rr_player(twoP - 1 - pr, r, twoP);
-          if (p > q) { int t = p; p = q; q = t; }
-          const T* cp = Wm + (int64_t)p * l;
-          const T* cq = Wm + (int64_t)q * l;
+      int p = 0, q = 0;
+      if (active) {
+        p = rr_player(pr, r, twoP);
+        q = rr_player(twoP - 1 - pr, r, twoP);
+        if (p > q) { const int t = p; p = q; q = t; }
+      }
+      T* cp = Wm + (int64_t)p * ldw;
+      T* cq = Wm + (int64_t)q * ldw;
+      T x[RMAX], y[RMAX];
+      T a = T(0), b = T(0), g = T(0);
+      if (active) {
+        if (in_regs) {
+#pragma unroll
+          for (int k = 0; k < RMAX; ++k) {
+            const int i = sub + G * k;
+            x[k] = (k < R && i < l) ? cp[i] : T(0);
+            y[k] = (k < R && i < l) ? cq[i] : T(0);
+            a = fma(x[k], x[k], a);
+            b = fma(y[k], y[k], b);
+            g = fma(x[k], y[k], g);
+          }
+        } else {
           for (int i = sub; i < l; i += G) {
-            T x = cp[i], y = cq[i];
-            a = fma(x, x, a);
-            b = fma(y, y, b);
-            g = fma(x, y, g);
+            const T xv = cp[i], yv = cq[i];
+            a = fma(xv, xv, a);
+            b = fma(yv, yv, b);
+            g = fma(xv, yv, g);
           }
         }
-        for (int o = G >> 1; o > 0; o >>= 1) {
-          a += __shfl_xor_sync(0xffffffffu, a, o);
-          b += __shfl_xor_sync(0xffffffffu, b, o);
-          g += __shfl_xor_sync(0xffffffffu, g, o);
-        }
-        if (it < items && sub == 0) {
-          s_abg[pr][0] = a;
-          s_abg[pr][1] = b;
-          s_abg[pr][2] = g;
-        }
       }
-      __syncthreads();
-      // B: rotation parameters (Rutishauser): zeta = (b - a) / (2g),
-      // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1+t^2), s = c t
-      for (int pr = tid; pr < P; pr += nt) {
-        const T a = s_abg[pr][0], b = s_abg[pr][1], g = s_abg[pr][2];
-        T c = T(1), sn = T(0);
-        if (g != 0.0 && fabs(g) > tol * sqrt(a) * sqrt(b)) {
+      for (int o = G >> 1; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        g += __shfl_xor_sync(0xffffffffu, g, o);
+      }
+      // zeta = (b - a) / (2g), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
+      // c = 1/sqrt(1+t^2), s = c t
+      T c = T(1), sn = T(0);
+      bool rotate = false;
+      if constexpr (kFused) {
+        if (active && g != T(0) && fabs(g) > tol * sqrt(a) * sqrt(b)) {
           const T zeta = (b - a) / (T(2) * g);
           const T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, T(1))));
           c = rsqrt(fma(t, t, T(1)));
           sn = c * t;
-          s_rot = 1;
+          rotate = true;
+          if (sub == 0) s_rot = 1;
         }
-        s_cs[pr][0] = c;
-        s_cs[pr][1] = sn;
+      } else {
+        if (active && sub == 0) {
+          s_abg[pr][0] = a;
+          s_abg[pr][1] = b;
+          s_abg[pr][2] = g;
+        }
+        __syncthreads();
+        for (int u = tid; u < P; u += nt) {
+          const T ua = s_abg[u][0], ub = s_abg[u][1], ug = s_abg[u][2];
+          T uc = T(1), us = T(0);
+          if (ug != T(0) && fabs(ug) > tol * sqrt(ua) * sqrt(ub)) {
+            const T zeta = (ub - ua) / (T(2) * ug);
+            const T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, T(1))));
+            uc = rsqrt(fma(t, t, T(1)));
+            us = uc * t;
+            s_rot = 1;
+          }
+          s_cs[u][0] = uc;
+          s_cs[u][1] = us;
+        }
+        __syncthreads();
+        if (active) {
+          c = s_cs[pr][0];
+          sn = s_cs[pr][1];
+          rotate = sn != T(0);
+        }
       }
-      __syncthreads();
-      // C: apply
-      for (int it = tid; it < items; it += nt) {
-        const int pr = it / G, sub = it % G;
-        const T c = s_cs[pr][0], sn = s_cs[pr][1];
-        if (sn == 0.0) continue;
-        int p = rr_player(pr, r, twoP), q = rr_player(twoP - 1 - pr, r, twoP);
-        if (p > q) { int t = p; p = q; q = t; }
-        T* cp = Wm + (int64_t)p * l;
-        T* cq = Wm + (int64_t)q * l;
-        for (int i = sub; i < l; i += G) {
-          T x = cp[i], y = cq[i];
-          cp[i] = c * x - sn * y;
-          cq[i] = sn * x + c * y;
+      if (rotate) {
+        if (in_regs) {
+#pragma unroll
+          for (int k = 0; k < RMAX; ++k) {
+            const int i = sub + G * k;
+            if (k < R && i < l) {
+              cp[i] = c * x[k] - sn * y[k];
+              cq[i] = sn * x[k] + c * y[k];
+            }
+          }
+        } else {
+          for (int i = sub; i < l; i += G) {
+            const T xv = cp[i], yv = cq[i];
+            cp[i] = c * xv - sn * yv;
+            cq[i] = sn * xv + c * yv;
+          }
         }
         if (want_v) {
-          T* vp = Wv + (int64_t)p * l;
-          T* vq = Wv + (int64_t)q * l;
+          T* vp = Wv + (int64_t)p * ldw;
+          T* vq = Wv + (int64_t)q * ldw;
           for (int i = sub; i < l; i += G) {
-            T x = vp[i], y = vq[i];
-            vp[i] = c * x - sn * y;
-            vq[i] = sn * x + c * y;
+            const T xv = vp[i], yv = vq[i];
+            vp[i] = c * xv - sn * yv;
+            vq[i] = sn * xv + c * yv;
           }
         }
       }
@@ -379,7 +601,7 @@ __device__ __forceinline__ void jacobi_body(const T* __restrict__ M, int l, int6
   }
   // column norms
   for (int c = warp; c < l; c += nwarps) {
-    const T* cp = Wm + (int64_t)c * l;
+    const T* cp = Wm + (int64_t)c * ldw;
     T a = 0.0;
     for (int i = lane; i < l; i += 32) a = fma(cp[i], cp[i], a);
     a = warp_sum(a);
@@ -399,10 +621,10 @@ __device__ __forceinline__ void jacobi_body(const T* __restrict__ M, int l, int6
     const T inv = sc > T(0) ? T(1) / sc : T(0);
     if (lane == 0) sig[rank] = sc;
     for (int i = lane; i < l; i += 32) {
-      const T u = Wm[i + (int64_t)c * l] * inv;
+      const T u = Wm[i + (int64_t)c * ldw] * inv;
       Um[i + (int64_t)rank * ldu] = u;
       if (UsInv) UsInv[i + (int64_t)rank * l] = u * inv;
-      if (want_v) Vm[i + (int64_t)rank * ldv] = Wv[i + (int64_t)c * l];
+      if (want_v) Vm[i + (int64_t)rank * ldv] = Wv[i + (int64_t)c * ldw];
     }
   }
 }

@@ -58,23 +58,31 @@ __global__ void vt_kernel(const T* __restrict__ Vk, int64_t n, int k,
 }
 
 template <typename T>
-__global__ void __launch_bounds__(SMALL_THREADS)
+__global__ void __launch_bounds__(CHOL_THREADS)
 chol_inv_kernel(const T* __restrict__ G, int64_t ldg, int l, T* __restrict__ R,
                 T* __restrict__ Rinv, T* __restrict__ gwork, DeviceStatus* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* W = gwork ? gwork : reinterpret_cast<T*>(smem_raw);
-  chol_inv_body<T>(G, ldg, l, R, Rinv, W, status);
+  chol_inv_blocked<T, CholPanel<T>::value>(G, ldg, l, R, Rinv, W, status);
+}
+
+template <int E>
+__global__ void __launch_bounds__(CHOL_REG_THREADS)
+chol_inv_regs_kernel(const float* __restrict__ G, int64_t ldg, int l, float* __restrict__ R,
+                     float* __restrict__ Rinv, DeviceStatus* status) {
+  chol_inv_regs<E>(G, ldg, l, R, Rinv, status);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(SMALL_THREADS)
+__global__ void __launch_bounds__(JACOBI_THREADS)
 jacobi_svd_kernel(const T* __restrict__ M, int l, int64_t ldm, T* __restrict__ sig,
                   T* __restrict__ Um, int64_t ldu, T* __restrict__ Vm, int64_t ldv,
                   T* __restrict__ UsInv, T* __restrict__ gwork, int use_smem,
                   DeviceStatus* status) {
   extern __shared__ __align__(16) unsigned char jsm_raw[];
   T* Wm = use_smem ? reinterpret_cast<T*>(jsm_raw) : gwork;
-  jacobi_body<T>(M, l, ldm, sig, Um, ldu, Vm, ldv, UsInv, Wm, status);
+  jacobi_body<T>(M, l, ldm, sig, Um, ldu, Vm, ldv, UsInv, Wm, jacobi_ld<T>(l, use_smem != 0),
+                 status);
 }
 
 template <typename T>
@@ -87,17 +95,22 @@ __global__ void sign_kernel(T* __restrict__ U, int64_t m, int64_t ldu, T* __rest
 template <typename T>
 cudaError_t launch_chol_inv(const T* G, int64_t ldg, int l, T* R, T* Rinv, T* work,
                             DeviceStatus* status, cudaStream_t st) {
-  const size_t smem = ((size_t)l * l + 33 * (size_t)(l + 64)) * sizeof(T);
-  const size_t cap = 200 * 1024;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(chol_inv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
-    attr_set = true;
-  }
-  if (smem <= cap)
-    chol_inv_kernel<T><<<1, SMALL_THREADS, smem, st>>>(G, ldg, l, R, Rinv, nullptr, status);
+  const size_t smem = chol_work_elems(l) * sizeof(T);
+  if (chol_in_regs<T>(l)) {
+    const float* g = (const float*)G;
+    float *r = (float*)R, *ri = (float*)Rinv;
+    constexpr int nt = CHOL_REG_THREADS;
+    switch (chol_reg_edge(l)) {
+      case 1: chol_inv_regs_kernel<1><<<1, nt, 0, st>>>(g, ldg, l, r, ri, status); break;
+      case 2: chol_inv_regs_kernel<2><<<1, nt, 0, st>>>(g, ldg, l, r, ri, status); break;
+      case 3: chol_inv_regs_kernel<3><<<1, nt, 0, st>>>(g, ldg, l, r, ri, status); break;
+      case 4: chol_inv_regs_kernel<4><<<1, nt, 0, st>>>(g, ldg, l, r, ri, status); break;
+      default: chol_inv_regs_kernel<5><<<1, nt, 0, st>>>(g, ldg, l, r, ri, status);
+    }
+  } else if (smem <= dynamic_smem_cap((const void*)chol_inv_kernel<T>))
+    chol_inv_kernel<T><<<1, CHOL_THREADS, smem, st>>>(G, ldg, l, R, Rinv, nullptr, status);
   else
-    chol_inv_kernel<T><<<1, SMALL_THREADS, 0, st>>>(G, ldg, l, R, Rinv, work, status);
+    chol_inv_kernel<T><<<1, CHOL_THREADS, 0, st>>>(G, ldg, l, R, Rinv, work, status);
   note_launch();
   return cudaGetLastError();
 }
@@ -117,16 +130,9 @@ cudaError_t launch_jacobi_svd(const T* M, int l, int64_t ldm, T* sig, T* Um, int
                               int64_t ldv, T* UsInv, T* work, DeviceStatus* status,
                               cudaStream_t st) {
   const int twoP = (l + 1) & ~1;
-  const size_t need = (size_t)(Vm ? 2 : 1) * l * twoP * sizeof(T);
-  const size_t cap = 200 * 1024;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(jacobi_svd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)cap);
-    attr_set = true;
-  }
-  const bool smem = need <= cap;
-  jacobi_svd_kernel<T><<<1, SMALL_THREADS, smem ? need : 0, st>>>(
+  const size_t need = (size_t)(Vm ? 2 : 1) * jacobi_ld<T>(l, true) * twoP * sizeof(T);
+  const bool smem = need <= dynamic_smem_cap((const void*)jacobi_svd_kernel<T>);
+  jacobi_svd_kernel<T><<<1, JACOBI_THREADS, smem ? need : 0, st>>>(
       M, l, ldm, sig, Um, ldu, Vm, ldv, UsInv, work, smem ? 1 : 0, status);
   note_launch();
   return cudaGetLastError();

@@ -30,4 +30,13 @@ size_t apass_partial_floats(int num_sms, int l);
 // slices too wide for two shared-memory stages --, workspace, CUDA).
 int launch_apass_bf16(const ApassCall& c, int num_sms, int* status, cudaStream_t st);
 
+// Fixup of a stream-K pass: `grid` CTAs shared `total` (tile, k-block)
+// iterations, `kt` k-blocks per tile of `bmt` rows; CTA c wrote the partials of
+// its first and last (split) tiles to part slots 2c and 2c+1 (bmt x l floats
+// each, column-major).  Writes (or adds to, `accumulate`) out for those tiles.
+constexpr int kFixCols = 8;   // output columns per fixup block
+int launch_apass_fixup(const float* part, int grid, int64_t total, int kt, int bmt, int l,
+                       int64_t rows_out, int64_t tiles, float* out, int64_t ldo, int accumulate,
+                       cudaStream_t st);
+
 }  // namespace rsvd

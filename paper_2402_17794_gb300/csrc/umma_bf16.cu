@@ -404,56 +404,6 @@ apass_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   }
 }
 
-// Sums the per-CTA partials of every tile whose k-range was split, in CTA
-// order.  One block per tile; tiles written whole by one CTA are skipped.
-// The (at most a few) CTA boundaries touching the tile are resolved once per
-// block, then every thread sums its elements.
-__global__ void apass_fixup_kernel(const float* __restrict__ part, int grid, int64_t total, int kt,
-                                   int bmt, int l, int64_t rows_out, float* __restrict__ out,
-                                   int64_t ldo, int accumulate) {
-  constexpr int kMaxShare = 32;
-  __shared__ int s_cta[kMaxShare];
-  __shared__ int s_slot[kMaxShare];
-  __shared__ int s_n;
-  const int64_t t = blockIdx.x;
-  if (threadIdx.x == 0) {
-    auto begin = [&](int c) { return (int64_t)((__int128)total * c / grid); };
-    auto cta_of = [&](int64_t g) {
-      int c = (int)((__int128)g * grid / total);
-      while (c + 1 < grid && begin(c + 1) <= g) ++c;
-      while (c > 0 && begin(c) > g) --c;
-      return c;
-    };
-    const int cf = cta_of(t * kt), cl = cta_of((t + 1) * kt - 1);
-    int n = 0;
-    if (cf != cl) {
-      for (int cc = cf; cc <= cl && n < kMaxShare; ++cc) {
-        const int64_t b = begin(cc);
-        if (b >= begin(cc + 1)) continue;
-        s_cta[n] = cc;
-        s_slot[n] = (b / kt == t) ? 0 : 1;
-        ++n;
-      }
-    }
-    s_n = n;
-  }
-  __syncthreads();
-  const int n = s_n;
-  if (n == 0) return;  // written directly by one CTA
-  const int64_t per_tile = (int64_t)bmt * l;
-  for (int c = 0; c < l; ++c) {
-    for (int r = threadIdx.x; r < bmt; r += blockDim.x) {
-      const int64_t row = t * bmt + r;
-      if (row >= rows_out) continue;
-      float s = 0.f;
-      for (int j = 0; j < n; ++j)
-        s += part[((size_t)s_cta[j] * 2 + s_slot[j]) * per_tile + (size_t)c * bmt + r];
-      float* d = out + row + (int64_t)c * ldo;
-      *d = accumulate ? *d + s : s;
-    }
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
@@ -555,11 +505,8 @@ int launch_apass_bf16(const ApassCall& c, int num_sms, int* status, cudaStream_t
 #undef RSVD_LAUNCH_APASS
   note_launch();
   if (cudaGetLastError() != cudaSuccess) return RSVD_ERR_CUDA;
-  apass_fixup_kernel<<<(unsigned)tiles, 256, 0, st>>>(c.part, grid, total, kt, bmt, c.l, rows_out,
-                                                       c.out, c.ldo, a.accumulate);
-  note_launch();
-  if (cudaGetLastError() != cudaSuccess) return RSVD_ERR_CUDA;
-  return RSVD_OK;
+  return launch_apass_fixup(c.part, grid, total, kt, bmt, c.l, rows_out, tiles, c.out, c.ldo,
+                            a.accumulate, st);
 }
 
 }  // namespace rsvd
