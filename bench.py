@@ -49,6 +49,12 @@ WORKLOADS = {
              "bf16x3 final B); FP32 accumulate",
         m=65536, n=16384, k=128, p=32, q=3, spectrum=("exp", 40.0), terms=640, noise=1e-4,
         seed_a=0, seed=2, dtype="bf16"),
+    "mixed-fp8": dict(
+        desc="mixed precision, FP8 storage: the same A 65536x16384 stored as FP8 E4M3 with one "
+             "power-of-two FP32 scale per 128x128 tile; k=128, p=32, q=3 (+1 bf16x2 refinement "
+             "step, bf16x3 final B); FP32 accumulate",
+        m=65536, n=16384, k=128, p=32, q=3, spectrum=("exp", 40.0), terms=640, noise=1e-4,
+        seed_a=0, seed=2, dtype="fp8"),
 }
 
 
@@ -206,8 +212,19 @@ def _sigma(w):
 
 
 def _make_input(w, rank):
+    """The workload's A on the device, column-major as (n, lda); for FP8 the
+    pair (codes, tile scales)."""
     import torch
     from paper_2402_17794_gb300 import synthetic as syn
+    if w["dtype"] == "fp8":
+        at = syn.lowrank_matrix_torch(w["m"], w["n"], _sigma(w), seed=w["seed_a"] + 1000 * rank,
+                                      device="cuda", dtype=torch.float32,
+                                      factor_dtype=torch.float32,
+                                      noise_2norm=w.get("noise", 0.0))
+        codes, scales = syn.quantize_e4m3_tiles(at, w["m"])
+        del at
+        torch.cuda.empty_cache()
+        return codes, scales
     if w["dtype"] == "bf16":
         return syn.lowrank_matrix_torch(w["m"], w["n"], _sigma(w), seed=w["seed_a"] + 1000 * rank,
                                         device="cuda", dtype=torch.bfloat16,
@@ -217,21 +234,27 @@ def _make_input(w, rank):
                                     device="cuda", dtype=torch.float64)
 
 
-def run_mixed(args, world, rank, sampler_uuid):
-    """The mixed-precision workload: solves/s and the tcgen05 passes over A
-    timed alone against the HBM roofline."""
+def run_mixed(args, world, rank, sampler_uuid, wname="mixed-bf16"):
+    """A mixed-precision workload (BF16 or FP8 storage of A): solves/s and
+    the tcgen05 passes over A timed alone against the HBM roofline."""
     import torch
 
     from paper_2402_17794_gb300 import rsvd as R
 
-    w = WORKLOADS["mixed-bf16"]
+    w = WORKLOADS[wname]
+    fp8 = w["dtype"] == "fp8"
     m, n, k, p, q, seed = w["m"], w["n"], w["k"], w["p"], w["q"], w["seed"]
     l = k + p
-    a_bytes = m * n * 2
+    a_bytes = m * n * (1 if fp8 else 2)
     passes = 2 * (q + 1) + 2
-    dA = _make_input(w, rank)
     stream = torch.cuda.current_stream()
-    plan = R.Plan(m, n, l, a_dtype=R.BF16, mode=R.MIXED)
+    if fp8:
+        dA, scales = _make_input(w, rank)
+        plan = R.Plan(m, n, l, a_dtype=R.FP8E4M3, mode=R.MIXED)
+        plan.set_tile_scales(scales)
+    else:
+        dA = _make_input(w, rank)
+        plan = R.Plan(m, n, l, a_dtype=R.BF16, mode=R.MIXED)
     U = torch.empty(k, m, dtype=torch.float32, device="cuda")
     S = torch.empty(k, dtype=torch.float64, device="cuda")
     VT = torch.empty(n, k, dtype=torch.float32, device="cuda")
@@ -287,27 +310,29 @@ def run_mixed(args, world, rank, sampler_uuid):
     peaks, _ = _peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
     dom_ms = max(t_ax, t_atx)
-    dom = "apass_bf16_kernel<true,2> (Y = A X)" if t_ax >= t_atx else \
-        "apass_bf16_kernel<false,2> (Z = A^T X)"
+    f8 = ",fp8" if fp8 else ""
+    dom = f"apass_bf16_kernel<true,2{f8}> (Y = A X)" if t_ax >= t_atx else \
+        f"apass_bf16_kernel<false,2{f8}> (Z = A^T X)"
     achieved = a_bytes / (dom_ms / 1e3) / 1e9
     out = {
         "workload": w["desc"], "value": round(steps * world / (ms / 1e3), 3), "unit": "solves/s",
         "ms_per_solve": round(ms / steps, 4),
         "p50_ms": round(per[len(per) // 2], 4), "p99_ms": round(per[min(len(per) - 1, int(0.99 * len(per)))], 4),
-        "dtype": "bf16 A, fp32 accumulate", "passes_per_solve": passes, "jacobi_sweeps": sweeps,
+        "dtype": ("fp8 e4m3 A (tile scales), bf16 operands" if fp8 else "bf16 A") +
+                 ", fp32 accumulate", "passes_per_solve": passes, "jacobi_sweeps": sweeps,
         "a_pass": {"ms_ax": round(t_ax, 4), "ms_atx": round(t_atx, 4),
                    "gbps_ax": round(a_bytes / (t_ax / 1e3) / 1e9, 1),
                    "gbps_atx": round(a_bytes / (t_atx / 1e3) / 1e9, 1),
                    "gbps_in_solve": round(passes * a_bytes / (ms / steps / 1e3) / 1e9, 1)},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
                      "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-                     "traffic": _traffic_from_profile("mixed-bf16", "ax" if t_ax >= t_atx else "atx"),
+                     "traffic": _traffic_from_profile(wname, "ax" if t_ax >= t_atx else "atx"),
                      "algorithmic_bytes_per_launch": a_bytes,
                      "ms_per_launch": round(dom_ms, 4),
                      "timing": f"{how}: main kernel + split-tile fixup per pass"},
         "clocks": clocks,
     }
-    del dA
+    del dA, plan
     return out
 
 
@@ -582,10 +607,12 @@ def run_ours(args):
         raise RuntimeError(f"e2e solve failed: {R.rsvd_status_string(st)}")
 
     # --- the mixed-precision workload beside it ---
-    mixed = None
+    mixed = mixed_fp8 = None
     if not args.no_mixed:
         del A_h, dA2
         mixed = run_mixed(args, world, rank, uuid)
+        torch.cuda.empty_cache()
+        mixed_fp8 = run_mixed(args, world, rank, uuid, "mixed-fp8")
 
     batched = None if args.no_batched else run_batched(args, stream)
     serving = None if args.no_serving else run_serving(args)
@@ -613,6 +640,7 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "mixed": mixed,
+        "mixed_fp8": mixed_fp8,
         "batched": batched,
         "serving": serving,
         "gpu_launches": int(launches),
@@ -727,6 +755,20 @@ def run_profile_case(args):
     for _ in range(2):
         R.rsvd_apply_a(plan.handle, dA, m, n, m, Xn, n, l, Y, m)
         R.rsvd_apply_at(plan.handle, dA, m, n, m, Xn, m, l, Y, n)
+    st = plan.status()
+    if st != 0:
+        raise RuntimeError(R.rsvd_status_string(st))
+    # the same passes on FP8 E4M3 storage of A (268 MB), tile scales 2^-4
+    codes = dA.view(torch.uint8)[:, :m].contiguous()          # any byte pattern is a valid A
+    codes &= 0x77                                             # keep codes normal and finite
+    codes |= 0x08
+    scales = torch.full(((n + 127) // 128, (m + 127) // 128), 0.0625, device="cuda")
+    del dA, plan
+    plan = R.Plan(m, n, l, a_dtype=R.FP8E4M3, mode=R.MIXED)
+    plan.set_tile_scales(scales)
+    for _ in range(2):
+        R.rsvd_apply_a(plan.handle, codes, m, n, m, Xn, n, l, Y, m)
+        R.rsvd_apply_at(plan.handle, codes, m, n, m, Xn, m, l, Y, n)
     st = plan.status()
     if st != 0:
         raise RuntimeError(R.rsvd_status_string(st))

@@ -53,13 +53,18 @@ extern "C" {
 
 typedef struct rsvd_plan_s* rsvd_plan_t;
 
-/* Element types.  A plan's A is RSVD_F64 (plain mode) or RSVD_BF16 (mixed
- * mode); RSVD_F32 is an output type of rsvd_gaussian and the type of the
- * mixed mode's FP32 buffers. */
+/* Element types.  A plan's A is RSVD_F64 (plain mode), RSVD_BF16 or
+ * RSVD_FP8E4M3 (mixed mode); RSVD_F32 is an output type of rsvd_gaussian and
+ * the type of the mixed mode's FP32 buffers. */
 typedef enum {
-  RSVD_F64 = 0,   /* FP64 A; plain mode computes every step in FP64        */
+  RSVD_F64 = 0,     /* FP64 A; plain mode computes every step in FP64        */
   RSVD_F32 = 1,
-  RSVD_BF16 = 2   /* BF16 A; mixed mode (tensor cores, FP32 accumulation)  */
+  RSVD_BF16 = 2,    /* BF16 A; mixed mode (tensor cores, FP32 accumulation)  */
+  RSVD_FP8E4M3 = 3  /* FP8 E4M3 A (OCP 8-bit format: sign, 4-bit exponent of
+                       bias 7, 3-bit mantissa, no infinities, S.1111.111 NaN)
+                       with one FP32 scale per 128 x 128 tile; mixed mode.
+                       The thesis stores A in full precision; this compressed
+                       storage halves the bytes each pass over A streams. */
 } rsvd_dtype_t;
 
 typedef enum {
@@ -125,6 +130,23 @@ int rsvd_plan_diagnostics(rsvd_plan_t plan, int* jacobi_sweeps, int* dropped_col
 /* Sets the stream later calls enqueue on. */
 int rsvd_plan_set_stream(rsvd_plan_t plan, void* cuda_stream);
 
+/*
+ * rsvd_set_tile_scales (RSVD_FP8E4M3 plans): the scales of A.  Element (i, j)
+ * of A is the E4M3 value of code A[i + j*lda] times scales[I + J*lds] with
+ * I = i / 128, J = j / 128; `scales` is a DEVICE array of rows x cols FP32
+ * values (rows >= ceil(m / 128), cols >= ceil(n / 128) of every later call),
+ * caller-owned, read by every later solve or pass of the plan.  Each scale
+ * must be a positive power of two (then code * scale is exact in BF16, the
+ * tensor cores' operand type); the call copies the scales to the host once to
+ * check that (synchronous).  FP8 calls also need lda a multiple of 16.
+ * Errors: -1 plan; -2 scales NULL or a scale that is not a positive power of
+ * two; -3 rows < 1; -4 cols < 1; -5 lds < rows; RSVD_ERR_UNSUPPORTED if the
+ * plan's A is not FP8; RSVD_ERR_CUDA if the copy fails.  A solve or pass of an
+ * FP8 plan without covering scales returns RSVD_ERR_UNSUPPORTED.
+ */
+int rsvd_set_tile_scales(rsvd_plan_t plan, const float* scales, int64_t rows, int64_t cols,
+                         int64_t lds);
+
 int rsvd_plan_destroy(rsvd_plan_t plan);
 
 const char* rsvd_status_string(int status);
@@ -154,8 +176,8 @@ uint64_t rsvd_kernel_launches(void);
  * Argument errors: -1 plan; -2 A NULL; -3 m; -4 n; -5 lda; -6 k; -7 p;
  * -8 q; -10 U NULL; -11 ldu; -12 S NULL; -13 VT NULL; -14 ldvt.
  * m, n above the plan's maxima or k+p above l_max: RSVD_ERR_WORKSPACE.
- * Mixed mode reads A with TMA: lda must be a multiple of 8 and A 16-byte
- * aligned, else RSVD_ERR_UNSUPPORTED.  Mixed mode runs q power steps with a
+ * Mixed mode reads A with TMA: lda must be a multiple of 8 (16 for FP8 A)
+ * and A 16-byte aligned, else RSVD_ERR_UNSUPPORTED.  Mixed mode runs q power steps with a
  * BF16 copy of the operand, then one more power step with the operand split
  * in two BF16 slices, then B^T = A^T Q with Q split in three BF16 slices.
  */

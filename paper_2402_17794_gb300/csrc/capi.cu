@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "batched.h"
 #include "pipeline.h"
@@ -21,6 +22,20 @@ namespace {
 
 bool ready(rsvd_plan_t P) { return plan_ready(P); }
 
+// FP8 A: scales set and covering m x n, rows 16-byte aligned for TMA.
+bool fp8_ready(rsvd_plan_t P, int64_t m, int64_t n, int64_t lda) {
+  return P->scales && (m + 127) / 128 <= P->scale_rows && (n + 127) / 128 <= P->scale_cols &&
+         lda % 16 == 0;
+}
+
+// x > 0, finite, and a power of two (no mantissa bits).
+bool power_of_two(float x) {
+  uint32_t b;
+  std::memcpy(&b, &x, 4);
+  const uint32_t e = (b >> 23) & 0xFF, mant = b & 0x7FFFFF;
+  return (b >> 31) == 0 && e != 0 && e != 0xFF && mant == 0;
+}
+
 }  // namespace
 
 extern "C" {
@@ -32,7 +47,7 @@ int rsvd_plan_create(rsvd_plan_t* plan, int64_t m_max, int64_t n_max, int l_max,
   if (m_max < 1) return -2;
   if (n_max < 1) return -3;
   if (l_max < 1 || l_max > RSVD_L_MAX) return -4;
-  if (a_dtype != RSVD_F64 && a_dtype != RSVD_BF16) return -5;
+  if (a_dtype != RSVD_F64 && a_dtype != RSVD_BF16 && a_dtype != RSVD_FP8E4M3) return -5;
   if (mode != RSVD_MODE_PLAIN && mode != RSVD_MODE_MIXED) return -6;
   if ((mode == RSVD_MODE_PLAIN) != (a_dtype == RSVD_F64)) return -6;
   if (mode == RSVD_MODE_MIXED && l_max > 256) return -4;
@@ -47,6 +62,8 @@ int rsvd_plan_create(rsvd_plan_t* plan, int64_t m_max, int64_t n_max, int l_max,
   P->ws = nullptr;
   P->ws_bytes = 0;
   P->batched = 0;
+  P->scales = nullptr;
+  P->lds = P->scale_rows = P->scale_cols = 0;
   P->batch_lay = nullptr;
   P->h_ctx = nullptr;
   P->ctx_event = nullptr;
@@ -165,6 +182,30 @@ int rsvd_plan_set_stream(rsvd_plan_t plan, void* cuda_stream) {
   return RSVD_OK;
 }
 
+int rsvd_set_tile_scales(rsvd_plan_t plan, const float* scales, int64_t rows, int64_t cols,
+                         int64_t lds) {
+  if (!plan) return -1;
+  if (plan->dtype != RSVD_FP8E4M3) return RSVD_ERR_UNSUPPORTED;
+  if (!scales) return -2;
+  if (rows < 1) return -3;
+  if (cols < 1) return -4;
+  if (lds < rows) return -5;
+  // the scales are read once here and checked: every one must be a positive
+  // power of two (the tensor-core path folds it into BF16 exactly)
+  std::vector<float> h((size_t)lds * cols);
+  if (cudaMemcpy(h.data(), scales, h.size() * sizeof(float), cudaMemcpyDeviceToHost) !=
+      cudaSuccess)
+    return RSVD_ERR_CUDA;
+  for (int64_t J = 0; J < cols; ++J)
+    for (int64_t I = 0; I < rows; ++I)
+      if (!power_of_two(h[I + J * lds])) return -2;
+  plan->scales = scales;
+  plan->lds = lds;
+  plan->scale_rows = rows;
+  plan->scale_cols = cols;
+  return RSVD_OK;
+}
+
 int rsvd_plan_status(rsvd_plan_t plan) {
   if (!plan) return -1;
   if (!plan->ws) return RSVD_ERR_WORKSPACE;
@@ -240,6 +281,7 @@ int rsvd_solve(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t ld
     return RSVD_ERR_WORKSPACE;
   if (plan->mode == RSVD_MODE_MIXED && (lda % 8 || ((uintptr_t)A % 16)))
     return RSVD_ERR_UNSUPPORTED;
+  if (plan->dtype == RSVD_FP8E4M3 && !fp8_ready(plan, m, n, lda)) return RSVD_ERR_UNSUPPORTED;
   if (plan->mode == RSVD_MODE_PLAIN)
     return solve_plain(plan, (const double*)A, m, n, lda, k, p, q, seed, (double*)U, ldu, S,
                        (double*)VT, ldvt);
@@ -272,6 +314,7 @@ int rsvd_apply_a(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t 
   if (ldy < m) return -10;
   if (!ready(plan) || m > plan->m_max || n > plan->n_max || l > plan->l_max)
     return RSVD_ERR_WORKSPACE;
+  if (plan->dtype == RSVD_FP8E4M3 && !fp8_ready(plan, m, n, lda)) return RSVD_ERR_UNSUPPORTED;
   if (plan->mode == RSVD_MODE_PLAIN)
     return gemm<double>(plan, (const double*)A, lda, false, (const double*)X, ldx, (double*)Y, ldy,
                         m, n, l);
@@ -292,6 +335,7 @@ int rsvd_apply_at(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t
   if (ldz < n) return -10;
   if (!ready(plan) || m > plan->m_max || n > plan->n_max || l > plan->l_max)
     return RSVD_ERR_WORKSPACE;
+  if (plan->dtype == RSVD_FP8E4M3 && !fp8_ready(plan, m, n, lda)) return RSVD_ERR_UNSUPPORTED;
   if (plan->mode == RSVD_MODE_PLAIN)
     return gemm<double>(plan, (const double*)A, lda, true, (const double*)X, ldx, (double*)Z, ldz,
                         n, m, l);

@@ -62,6 +62,9 @@ struct rsvd_plan_s {
   rsvd::Layout lay;
   int* h_status;     // pinned host copy of DeviceStatus.flags
   int num_sms;
+  // FP8 A (rsvd_set_tile_scales): per-tile scales, tile (I, J) at scales[I + J * lds]
+  const float* scales;
+  int64_t lds, scale_rows, scale_cols;
   // batch plans (rsvd_batch_plan_create)
   int batched;
   int max_count;

@@ -82,6 +82,9 @@ int mixed_pass(rsvd_plan_t P, bool ax, const void* A, int64_t m, int64_t n, int6
   c.ldo = ldo;
   c.part = MW.apart;
   c.part_floats = MW.apart_floats;
+  c.fp8 = P->dtype == RSVD_FP8E4M3;
+  c.scales = P->scales;
+  c.lds = P->lds;
   rc = launch_apass_bf16(c, P->num_sms, &dstatus(P)->flags, P->stream);
   if (rc != RSVD_ERR_UNSUPPORTED || slices == 1) return rc;
   // the slices do not fit two shared-memory stages at this l: run the leading
@@ -327,6 +330,9 @@ int mixed_apply(rsvd_plan_t P, const void* A, int64_t m, int64_t n, int64_t lda,
   c.ldo = ldo;
   c.part = MW.apart;
   c.part_floats = MW.apart_floats;
+  c.fp8 = P->dtype == RSVD_FP8E4M3;
+  c.scales = P->scales;
+  c.lds = P->lds;
   return launch_apass_bf16(c, P->num_sms, &dstatus(P)->flags, P->stream);
 }
 

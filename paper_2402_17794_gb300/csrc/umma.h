@@ -7,7 +7,8 @@ namespace rsvd {
 
 struct ApassCall {
   bool ax;              // true: Y = A X (contracts n); false: Z = A^T X (contracts m)
-  const void* A;        // BF16 m x n, column-major, lda % 8 == 0, 16-byte aligned
+  const void* A;        // BF16 (or FP8, see fp8) m x n, column-major, lda % 8 == 0,
+                        // 16-byte aligned
   int64_t m, n, lda;
   const void* X;        // BF16 operand: (n for ax, m otherwise) x x_cols, ldx % 8 == 0
   int64_t ldx;
@@ -20,6 +21,11 @@ struct ApassCall {
   float* part;          // partial slots
   size_t part_floats;
   bool accumulate = false;  // out += A X instead of out = A X
+  // FP8 A: E4M3 codes (lda % 16 == 0) with FP32 power-of-two scales, one per
+  // 128 x 128 tile, tile (I, J) at scales[I + J * lds]
+  bool fp8 = false;
+  const float* scales = nullptr;
+  int64_t lds = 0;
 };
 
 // Floats of partial-slot workspace a pass with `l` output columns needs.

@@ -18,7 +18,7 @@ import torch
 
 from . import _lib
 
-F64, F32, BF16 = 0, 1, 2
+F64, F32, BF16, FP8E4M3 = 0, 1, 2, 3
 PLAIN, MIXED = 0, 1
 STATUS = {0: "ok", 1: "cholesky", 2: "jacobi", 3: "timeout", 4: "workspace", 5: "cuda",
           6: "nonfinite", 7: "unsupported"}
@@ -106,6 +106,10 @@ def rsvd_plan_diagnostics(plan):
 
 def rsvd_plan_set_stream(plan, stream=None) -> None:
     _check(_lib.load().rsvd_plan_set_stream(plan, _stream_handle(stream)), "rsvd_plan_set_stream")
+
+
+def rsvd_set_tile_scales(plan, scales, rows, cols, lds) -> int:
+    return _lib.load().rsvd_set_tile_scales(plan, _ptr(scales), rows, cols, lds)
 
 
 def rsvd_plan_destroy(plan) -> None:
@@ -248,6 +252,13 @@ class Plan:
 
     def status(self) -> int:
         return rsvd_plan_status(self.handle)
+
+    def set_tile_scales(self, scales):
+        """FP8 plans: scales is the FP32 device tensor (n_tiles, m_tiles) whose
+        row J holds column J of the column-major scale matrix."""
+        self.scales = scales   # the plan reads it on every later call
+        _check(rsvd_set_tile_scales(self.handle, scales, scales.shape[1], scales.shape[0],
+                                    scales.shape[1]), "rsvd_set_tile_scales")
 
     def solve(self, A, m, n, k, p, q, seed, lda=None, out=None):
         """A: column-major device tensor (n, lda).  Returns (U, S, VT) as

@@ -184,3 +184,45 @@ def lowrank_matrix_torch(m: int, n: int, sigma: np.ndarray, seed: int, *,
     out = torch.zeros(n, lda, dtype=dtype, device=device)
     out[:, :m] = at.to(dtype)
     return out
+
+
+# ---------------------------------------------------------------------------
+# FP8 E4M3 storage with one power-of-two scale per 128 x 128 tile
+# ---------------------------------------------------------------------------
+
+FP8_TILE = 128
+FP8_MAX = 448.0
+
+
+def quantize_e4m3_tiles(at, m: int, lda_q: int | None = None):
+    """Stores a column-major matrix as E4M3 codes with per-tile scales.
+
+    ``at``: torch tensor (n, >= m) whose row j is column j of A (any float
+    dtype, any device).  Each 128 x 128 tile (I, J) gets the scale
+    2^ceil(log2(amax / 448)) (1 for an all-zero tile), a power of two, so
+    code * scale is exact in BF16 and FP32; codes are A / scale rounded to
+    nearest even.  Returns (codes, scales): codes a uint8 tensor (n, lda_q)
+    with lda_q a multiple of 16 (zero padded), scales an FP32 tensor
+    (n_tiles, m_tiles) whose row J holds column J of the column-major
+    m_tiles x n_tiles scale matrix (ld m_tiles)."""
+    import torch
+
+    n = at.shape[0]
+    lda_q = lda_q or (m + 15) // 16 * 16
+    mt, nt = (m + FP8_TILE - 1) // FP8_TILE, (n + FP8_TILE - 1) // FP8_TILE
+    codes = torch.zeros(n, lda_q, dtype=torch.uint8, device=at.device)
+    scales = torch.ones(nt, mt, dtype=torch.float32, device=at.device)
+    for J in range(nt):
+        j0, j1 = J * FP8_TILE, min(n, (J + 1) * FP8_TILE)
+        blk = at[j0:j1, :m].to(torch.float64)
+        # per-tile amax over the 128-row groups of A
+        pad = mt * FP8_TILE - m
+        absb = torch.nn.functional.pad(blk.abs(), (0, pad))
+        amax = absb.reshape(j1 - j0, mt, FP8_TILE).amax(dim=(0, 2))
+        e = torch.ceil(torch.log2(torch.clamp(amax, min=1e-300) / FP8_MAX))
+        sc = torch.where(amax > 0, torch.pow(2.0, e), torch.ones_like(amax))
+        scales[J] = sc.to(torch.float32)
+        rows_scale = sc.repeat_interleave(FP8_TILE)[:m]
+        q = (blk / rows_scale).to(torch.float8_e4m3fn)
+        codes[j0:j1, :m] = q.view(torch.uint8)
+    return codes, scales
