@@ -606,6 +606,9 @@ def run_ours(args):
     if st != 0:
         raise RuntimeError(f"e2e solve failed: {R.rsvd_status_string(st)}")
 
+    # --- Algorithm 6 (single pass) on the same matrix ---
+    singlepass = run_singlepass(args, world, dA, w, plan)
+
     # --- the mixed-precision workload beside it ---
     mixed = mixed_fp8 = None
     if not args.no_mixed:
@@ -639,6 +642,7 @@ def run_ours(args):
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "singlepass": singlepass,
         "mixed": mixed,
         "mixed_fp8": mixed_fp8,
         "batched": batched,
@@ -654,6 +658,45 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_singlepass(args, world, dA, w, plan):
+    """Algorithm 6 (single-pass RSVD) on the plain workload's matrix: A is
+    read by the two sketches only (2 passes instead of 2q + 2)."""
+    import torch
+
+    from paper_2402_17794_gb300 import rsvd as R
+
+    m, n, k, p, seed = w["m"], w["n"], w["k"], w["p"], w["seed"]
+    U = torch.empty(k, m, dtype=torch.float64, device="cuda")
+    S = torch.empty(k, dtype=torch.float64, device="cuda")
+    VT = torch.empty(n, k, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        R._check(R.rsvd_solve_singlepass(plan.handle, dA, m, n, m, k, p, seed, U, m, S, VT, k),
+                 "rsvd_solve_singlepass")
+
+    for _ in range(args.warmup):
+        step()
+    steps = max(args.steps, 5)
+    _barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    st = plan.status()
+    if st != 0:
+        raise RuntimeError(f"single-pass solve failed: {R.rsvd_status_string(st)}")
+    ms = _max_over_ranks(e0.elapsed_time(e1), world)
+    return {"workload": "Algorithm 6 (single-pass RSVD) on " + w["desc"].split(";")[0] +
+                        f"; k={k}, p={p}",
+            "value": round(steps * world / (ms / 1e3), 4), "unit": "solves/s",
+            "ms_per_solve": round(ms / steps, 4), "passes_per_solve": 2, "dtype": "f64"}
 
 
 def _traffic_from_profile(key="plain-fp64", pas="atx"):

@@ -185,6 +185,26 @@ int rsvd_solve(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t ld
                int k, int p, int q, uint64_t seed,
                void* U, int64_t ldu, double* S, void* VT, int64_t ldvt);
 
+/*
+ * rsvd_solve_singlepass: rank-k randomized SVD by Algorithm 6 ("Single-Pass
+ * Randomized SVD for a General Matrix", Section 3.4.2): A is read by exactly
+ * two sketching products, Y_c = A Omega_c and Y_r = A^T Omega_r (Omega_c
+ * n x (k+p) from Philox stream 0 of `seed`, Omega_r m x (k+p) from stream 1),
+ * and never again.  Q_c, Q_r are the k dominant left singular vectors of Y_c
+ * and Y_r; C (k x k) is the least-squares solution of the joint system
+ * (Omega_r^T Q_c) C = Y_r^T Q_r, C (Q_r^T Omega_c) = Q_c^T Y_c, both
+ * equations weighted equally; C = U^ Sigma V^^T; U = Q_c U^, V = Q_r V^.
+ * Less accurate than Algorithm 4 (the thesis notes it), but A is streamed
+ * only in Stage 1.  Plain (FP64) plans; outputs and signs as rsvd_solve.
+ * Argument errors: -1 plan; -2 A NULL; -3 m; -4 n; -5 lda; -6 k; -7 p (or
+ * k+p > min(m, n)); -9 U NULL; -10 ldu; -11 S NULL; -12 VT NULL; -13 ldvt.
+ * RSVD_ERR_WORKSPACE as rsvd_solve; RSVD_ERR_UNSUPPORTED for mixed or batch
+ * plans.
+ */
+int rsvd_solve_singlepass(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t lda,
+                          int k, int p, uint64_t seed, void* U, int64_t ldu, double* S,
+                          void* VT, int64_t ldvt);
+
 /* ---------------------------------------------------------------------- */
 /* Step-level entry points (the rows of the hot path, one call per step).   */
 /* In plain mode every buffer is FP64; the mixed-mode types are noted.     */

@@ -288,6 +288,30 @@ int rsvd_solve(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t ld
   return solve_mixed(plan, A, m, n, lda, k, p, q, seed, (float*)U, ldu, S, (float*)VT, ldvt);
 }
 
+int rsvd_solve_singlepass(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t lda,
+                          int k, int p, uint64_t seed, void* U, int64_t ldu, double* S, void* VT,
+                          int64_t ldvt) {
+  if (!plan) return -1;
+  if (!A) return -2;
+  if (m < 1) return -3;
+  if (n < 1) return -4;
+  if (lda < m) return -5;
+  if (k < 1) return -6;
+  if (p < 0) return -7;
+  if (!U) return -9;
+  if (ldu < m) return -10;
+  if (!S) return -11;
+  if (!VT) return -12;
+  if (ldvt < k) return -13;
+  const int l = k + p;
+  if (l > (m < n ? m : n)) return -7;
+  if (!ready(plan) || m > plan->m_max || n > plan->n_max || l > plan->l_max)
+    return RSVD_ERR_WORKSPACE;
+  if (plan->mode != RSVD_MODE_PLAIN || plan->batched) return RSVD_ERR_UNSUPPORTED;
+  return solve_singlepass(plan, (const double*)A, m, n, lda, k, p, seed, (double*)U, ldu, S,
+                          (double*)VT, ldvt);
+}
+
 int rsvd_gaussian(rsvd_plan_t plan, int64_t n, int l, uint64_t seed, uint32_t stream, int out_dtype,
                   void* out, int64_t ldo) {
   if (!plan) return -1;

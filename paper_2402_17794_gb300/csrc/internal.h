@@ -41,6 +41,7 @@ inline int status_from_flags(int flags) {
 // Workspace carve-up (offsets in bytes from the workspace base).
 struct Layout {
   size_t status, om, y, qm, tmp, z, qb, part, small, total;
+  size_t sp;            // l x l slots of the single-pass solve (Algorithm 6)
   // mixed-mode extras: BF16 operand slices (om16), tcgen05 partial slots (y32)
   size_t om16, y32;
   size_t small_stride;  // bytes of one l x l FP64 matrix (padded)

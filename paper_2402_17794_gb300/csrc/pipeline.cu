@@ -151,6 +151,7 @@ Layout make_layout(int64_t m, int64_t n, int l, int mode, int num_sms) {
   L.small = take(L.small_stride * 8 + align_up(2 * (size_t)l * lpad * e) +
                  align_up(2 * (size_t)l * e) +
                  align_up(((size_t)l * l + 33 * (size_t)(l + 64)) * e));
+  L.sp = take(L.small_stride * kSinglePassSlots + align_up(kSinglePassVecs * (size_t)l * e));
   if (mode == RSVD_MODE_MIXED) {
     const int l16 = (l + 15) / 16 * 16;
     L.om16 = take((size_t)round8(mn) * 3 * l16 * sizeof(__nv_bfloat16));

@@ -16,6 +16,8 @@ namespace rsvd {
   } while (0)
 
 constexpr int kPartSplits = 16;  // SIMT split-K partial slices held in workspace
+constexpr int kSinglePassSlots = 24;  // l x l matrices of the single-pass solve
+constexpr int kSinglePassVecs = 8;    // l-vectors of the single-pass solve
 
 // Views of the workspace for the element type T of the path (double for the
 // plain path, float for the mixed path).
@@ -63,6 +65,11 @@ int solve_plain(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t ld
                 int64_t ldvt);
 int solve_mixed(rsvd_plan_t P, const void* A, int64_t m, int64_t n, int64_t lda, int k, int p,
                 int q, uint64_t seed, float* U, int64_t ldu, double* S, float* VT, int64_t ldvt);
+
+// Algorithm 6 (single-pass randomized SVD of a general matrix), FP64.
+int solve_singlepass(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t lda, int k,
+                     int p, uint64_t seed, double* U, int64_t ldu, double* S, double* VT,
+                     int64_t ldvt);
 
 // Step entry: one tcgen05 pass with a BF16 operand X (ldx) of `l` columns.
 int mixed_apply(rsvd_plan_t P, const void* A, int64_t m, int64_t n, int64_t lda, const void* X,

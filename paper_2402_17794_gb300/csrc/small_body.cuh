@@ -471,14 +471,30 @@ __device__ __forceinline__ void jacobi_body(const T* __restrict__ M, int l, int6
   const int R = (l + G - 1) / G;          // rows per thread
   const bool in_regs = R <= RMAX;
 
+  __shared__ T s_fro[32];
+  T fro = T(0);
   for (int t = tid; t < l * twoP; t += nt) {
     int i = t % l, j = t / l;
-    Wm[i + (int64_t)j * ldw] = (j < l) ? M[i + (int64_t)j * ldm] : T(0);
+    const T v = (j < l) ? M[i + (int64_t)j * ldm] : T(0);
+    Wm[i + (int64_t)j * ldw] = v;
+    fro = fma(v, v, fro);
     if (want_v) Wv[i + (int64_t)j * ldw] = (i == j) ? T(1) : T(0);
   }
+  fro = warp_sum(fro);
+  if (lane == 0) s_fro[warp] = fro;
   if (tid == 0) s_rot = 0;
   __syncthreads();
+  if (tid < 32) {
+    T f = tid < nwarps ? s_fro[tid] : T(0);
+    f = warp_sum(f);
+    if (tid == 0) s_fro[0] = f;
+  }
+  __syncthreads();
   const T tol = sqrt((T)l) * Eps<T>::value;
+  // a column whose squared norm is below (eps ||M||_F)^2 is numerically zero
+  // (a rank-deficient M): pairs with one are left alone, as rotating rounding
+  // noise against itself would never meet the relative test
+  const T tiny = Eps<T>::value * Eps<T>::value * s_fro[0];
   const int pr = tid / G, sub = tid % G;
   const bool active = tid < items;
   int sweep = 0;
@@ -525,7 +541,7 @@ __device__ __forceinline__ void jacobi_body(const T* __restrict__ M, int l, int6
       T c = T(1), sn = T(0);
       bool rotate = false;
       if constexpr (kFused) {
-        if (active && g != T(0) && fabs(g) > tol * sqrt(a) * sqrt(b)) {
+        if (active && g != T(0) && fmin(a, b) > tiny && fabs(g) > tol * sqrt(a) * sqrt(b)) {
           const T zeta = (b - a) / (T(2) * g);
           const T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, T(1))));
           c = rsqrt(fma(t, t, T(1)));
@@ -543,7 +559,7 @@ __device__ __forceinline__ void jacobi_body(const T* __restrict__ M, int l, int6
         for (int u = tid; u < P; u += nt) {
           const T ua = s_abg[u][0], ub = s_abg[u][1], ug = s_abg[u][2];
           T uc = T(1), us = T(0);
-          if (ug != T(0) && fabs(ug) > tol * sqrt(ua) * sqrt(ub)) {
+          if (ug != T(0) && fmin(ua, ub) > tiny && fabs(ug) > tol * sqrt(ua) * sqrt(ub)) {
             const T zeta = (ub - ua) / (T(2) * ug);
             const T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, T(1))));
             uc = rsqrt(fma(t, t, T(1)));

@@ -129,6 +129,11 @@ def rsvd_solve(plan, A, m, n, lda, k, p, q, seed, U, ldu, S, VT, ldvt) -> int:
                                   _ptr(VT), ldvt)
 
 
+def rsvd_solve_singlepass(plan, A, m, n, lda, k, p, seed, U, ldu, S, VT, ldvt) -> int:
+    return _lib.load().rsvd_solve_singlepass(plan, _ptr(A), m, n, lda, k, p, seed, _ptr(U), ldu,
+                                             _ptr(S), _ptr(VT), ldvt)
+
+
 def rsvd_gaussian(plan, n, l, seed, stream_id, out_dtype, out, ldo) -> int:
     return _lib.load().rsvd_gaussian(plan, n, l, seed, stream_id, out_dtype, _ptr(out), ldo)
 
@@ -259,6 +264,16 @@ class Plan:
         self.scales = scales   # the plan reads it on every later call
         _check(rsvd_set_tile_scales(self.handle, scales, scales.shape[1], scales.shape[0],
                                     scales.shape[1]), "rsvd_set_tile_scales")
+
+    def solve_singlepass(self, A, m, n, k, p, seed, lda=None):
+        """Algorithm 6 on a plain plan: (U, S, VT) as solve(); enqueued only."""
+        lda = lda or A.shape[1]
+        U = torch.empty(k, m, dtype=torch.float64, device=A.device)
+        S = torch.empty(k, dtype=torch.float64, device=A.device)
+        VT = torch.empty(n, k, dtype=torch.float64, device=A.device)
+        _check(rsvd_solve_singlepass(self.handle, A, m, n, lda, k, p, seed, U, m, S, VT, k),
+               "rsvd_solve_singlepass")
+        return U, S, VT
 
     def solve(self, A, m, n, k, p, q, seed, lda=None, out=None):
         """A: column-major device tensor (n, lda).  Returns (U, S, VT) as
