@@ -4,6 +4,8 @@
 
 #include <cfloat>
 
+#include <cooperative_groups.h>
+
 #include "internal.h"
 
 namespace rsvd {
@@ -643,6 +645,221 @@ __device__ __forceinline__ void jacobi_body(const T* __restrict__ M, int l, int6
       if (want_v) Vm[i + (int64_t)rank * ldv] = Wv[i + (int64_t)c * ldw];
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// One-sided Jacobi over a cluster of CTAs
+// ---------------------------------------------------------------------------
+//
+// The same rotations as jacobi_body, spread over a thread-block cluster of
+// JACOBI_CLUSTER CTAs (distributed shared memory): CTA r holds rows
+// [r R, (r+1) R) of every column (R = ceil(l / JACOBI_CLUSTER)).  A round of
+// the round-robin ordering:
+//   1. each CTA forms the partial |c_p|^2, |c_q|^2, c_p.c_q of every pair over
+//      its rows (a warp per pair, lanes over rows) into its own buffer;
+//   2. cluster barrier; one thread per pair sums the JACOBI_CLUSTER partials,
+//      read from each CTA's buffer in rank order, so every CTA forms the same
+//      sums, the same rotation and the same convergence decision;
+//   3. each CTA rotates its own rows.
+// The partial buffers alternate between rounds, so one cluster barrier per
+// round orders both the writes and the reads.  Per CTA, a round moves only
+// R rows of each pair through shared memory and the FP64 work of a round is
+// split over the cluster's SMs.  A CTA of the cluster never leaves before
+// the others (a final cluster barrier): its shared memory is read remotely.
+constexpr int JACOBI_CLUSTER = 8;
+constexpr int JACOBI_CL_THREADS = 256;
+
+// {a, b, g, 0} to a 16-byte aligned slot (possibly another CTA's), as vectors
+__device__ __forceinline__ void store_triple(float* d, float a, float b, float g) {
+  *reinterpret_cast<float4*>(d) = make_float4(a, b, g, 0.f);
+}
+__device__ __forceinline__ void store_triple(double* d, double a, double b, double g) {
+  reinterpret_cast<double2*>(d)[0] = make_double2(a, b);
+  reinterpret_cast<double2*>(d)[1] = make_double2(g, 0.0);
+}
+
+__host__ __device__ inline int jacobi_cluster_rows(int l) {
+  return (l + JACOBI_CLUSTER - 1) / JACOBI_CLUSTER;
+}
+// Shared-memory elements of one CTA: its rows of W (and of V), ld rows + 1.
+__host__ __device__ inline size_t jacobi_cluster_elems(int l, bool want_v) {
+  const int twoP = (l + 1) & ~1;
+  return (size_t)(want_v ? 2 : 1) * (jacobi_cluster_rows(l) + 1) * twoP;
+}
+
+template <typename T>
+__device__ __forceinline__ void jacobi_cluster_body(const T* __restrict__ M, int l, int64_t ldm,
+                                                    T* __restrict__ sig, T* __restrict__ Um,
+                                                    int64_t ldu, T* __restrict__ Vm, int64_t ldv,
+                                                    T* __restrict__ UsInv, T* __restrict__ Wl,
+                                                    DeviceStatus* status) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int twoP = (l + 1) & ~1;
+  const int P = twoP / 2;
+  const bool want_v = Vm != nullptr;
+  const int R = jacobi_cluster_rows(l);
+  const int ld = R + 1;
+  const int r0 = rank * R;
+  const int nr = max(0, min(l, r0 + R) - r0);
+  T* Wv = Wl + (int64_t)ld * twoP;
+  // partials pushed by every CTA of the cluster: [round parity][source rank][pair]
+  // as {a, b, g, 0}, so one pair costs one (FP32) or two (FP64) 16-byte remote
+  // stores per destination (a remote store costs the SM ~1.5 clocks)
+  __shared__ __align__(16) T s_part[2][JACOBI_CLUSTER][(RSVD_L_MAX + 1) / 2][4];
+  __shared__ T s_cs[(RSVD_L_MAX + 1) / 2][2];
+  __shared__ T s_norm[RSVD_L_MAX + 1];
+  __shared__ T s_fro[JACOBI_CL_THREADS / 32];
+  __shared__ int s_rot;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nwarps = nt >> 5;
+
+  T fro = T(0);
+  for (int t = tid; t < ld * twoP; t += nt) {
+    const int i = t % ld, j = t / ld;
+    const T v = (i < nr && j < l) ? M[r0 + i + (int64_t)j * ldm] : T(0);
+    Wl[t] = v;
+    fro = fma(v, v, fro);
+    if (want_v) Wv[t] = (i < nr && r0 + i == j) ? T(1) : T(0);
+  }
+  fro = warp_sum(fro);
+  if (lane == 0) s_fro[warp] = fro;
+  if (tid == 0) s_rot = 0;
+  __syncthreads();
+  if (tid < JACOBI_CLUSTER) {   // this CTA's share of ||M||_F^2, pushed to CTA tid
+    T f = T(0);
+    for (int w = 0; w < nwarps; ++w) f += s_fro[w];
+    *cluster.map_shared_rank(&s_part[1][rank][0][0], tid) = f;
+  }
+  cluster.sync();
+  T fro_all = T(0);
+  for (int q = 0; q < JACOBI_CLUSTER; ++q) fro_all += s_part[1][q][0][0];
+  const T tol = sqrt((T)l) * Eps<T>::value;
+  const T tiny = Eps<T>::value * Eps<T>::value * fro_all;
+
+  int par = 0, sweep = 0;
+  const int max_sweeps = 30;
+  for (; sweep < max_sweeps; ++sweep) {
+    for (int r = 0; r < twoP - 1; ++r) {
+      // 1. partial dots over this CTA's rows, a thread per pair (no cross-lane
+      //    reductions: FP64 additions through shuffles cost the slow pipe)
+      for (int pr = tid; pr < P; pr += nt) {
+        int p = rr_player(pr, r, twoP), q = rr_player(twoP - 1 - pr, r, twoP);
+        if (p > q) { const int t = p; p = q; q = t; }
+        const T* cp = Wl + (int64_t)p * ld;
+        const T* cq = Wl + (int64_t)q * ld;
+        T a = T(0), b = T(0), g = T(0);
+        for (int i = 0; i < nr; ++i) {
+          const T x = cp[i], y = cq[i];
+          a = fma(x, x, a);
+          b = fma(y, y, b);
+          g = fma(x, y, g);
+        }
+#pragma unroll
+        for (int dst = 0; dst < JACOBI_CLUSTER; ++dst) {   // push into every CTA's buffer
+          T* d = cluster.map_shared_rank(&s_part[par][rank][pr][0], dst);
+          store_triple(d, a, b, g);
+        }
+      }
+      cluster.sync();
+      // 2. the cluster's sums, in rank order, and the rotations
+      for (int pr = tid; pr < P; pr += nt) {
+        T a = T(0), b = T(0), g = T(0);
+#pragma unroll
+        for (int q = 0; q < JACOBI_CLUSTER; ++q) {
+          a += s_part[par][q][pr][0];
+          b += s_part[par][q][pr][1];
+          g += s_part[par][q][pr][2];
+        }
+        T c = T(1), sn = T(0);
+        if (g != T(0) && fmin(a, b) > tiny && fabs(g) > tol * sqrt(a) * sqrt(b)) {
+          const T zeta = (b - a) / (T(2) * g);
+          const T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, T(1))));
+          c = rsqrt(fma(t, t, T(1)));
+          sn = c * t;
+          s_rot = 1;
+        }
+        s_cs[pr][0] = c;
+        s_cs[pr][1] = sn;
+      }
+      __syncthreads();
+      // 3. rotate this CTA's rows: warps over pairs, lanes over rows
+      for (int pr = warp; pr < P; pr += nwarps) {
+        const T c = s_cs[pr][0], sn = s_cs[pr][1];
+        if (sn == T(0)) continue;
+        int p = rr_player(pr, r, twoP), q = rr_player(twoP - 1 - pr, r, twoP);
+        if (p > q) { const int t = p; p = q; q = t; }
+        T* cp = Wl + (int64_t)p * ld;
+        T* cq = Wl + (int64_t)q * ld;
+        for (int i = lane; i < nr; i += 32) {
+          const T x = cp[i], y = cq[i];
+          cp[i] = c * x - sn * y;
+          cq[i] = sn * x + c * y;
+        }
+        if (want_v) {
+          T* vp = Wv + (int64_t)p * ld;
+          T* vq = Wv + (int64_t)q * ld;
+          for (int i = lane; i < nr; i += 32) {
+            const T xv = vp[i], yv = vq[i];
+            vp[i] = c * xv - sn * yv;
+            vq[i] = sn * xv + c * yv;
+          }
+        }
+      }
+      par ^= 1;
+      // the next round's partials go to the other buffer; the rotations of
+      // this round are read only locally, so a CTA barrier suffices
+      __syncthreads();
+    }
+    const int rot = s_rot;   // the same in every CTA (same sums)
+    __syncthreads();
+    if (tid == 0) s_rot = 0;
+    __syncthreads();
+    if (!rot) break;
+  }
+  if (rank == 0 && tid == 0) {
+    status->jacobi_sweeps = sweep + 1;
+    if (sweep >= max_sweeps) set_flag(status, RSVD_ERR_JACOBI);
+  }
+  // every CTA has read the last round's partials before they are overwritten
+  cluster.sync();
+  // column norms: partial over this CTA's rows, then the cluster's sum
+  for (int c = warp; c < l; c += nwarps) {
+    const T* cp = Wl + (int64_t)c * ld;
+    T a = T(0);
+    for (int i = lane; i < nr; i += 32) a = fma(cp[i], cp[i], a);
+    a = warp_sum(a);
+    if (lane < JACOBI_CLUSTER) *cluster.map_shared_rank(&s_part[0][rank][c >> 1][c & 1], lane) = a;
+  }
+  cluster.sync();
+  for (int c = tid; c < l; c += nt) {
+    T a = T(0);
+#pragma unroll
+    for (int q = 0; q < JACOBI_CLUSTER; ++q) a += s_part[0][q][c >> 1][c & 1];
+    s_norm[c] = sqrt(a);
+  }
+  __syncthreads();
+  // sort descending by rank (ties keep column order); write this CTA's rows
+  for (int c = warp; c < l; c += nwarps) {
+    const T sc = s_norm[c];
+    int rk = 0;
+    for (int d = lane; d < l; d += 32) {
+      const T sd = s_norm[d];
+      rk += (sd > sc || (sd == sc && d < c)) ? 1 : 0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rk += __shfl_xor_sync(0xffffffffu, rk, o);
+    const T inv = sc > T(0) ? T(1) / sc : T(0);
+    if (rank == 0 && lane == 0) sig[rk] = sc;
+    for (int i = lane; i < nr; i += 32) {
+      const T u = Wl[i + (int64_t)c * ld] * inv;
+      Um[r0 + i + (int64_t)rk * ldu] = u;
+      if (UsInv) UsInv[r0 + i + (int64_t)rk * l] = u * inv;
+      if (want_v) Vm[r0 + i + (int64_t)rk * ldv] = Wv[i + (int64_t)c * ld];
+    }
+  }
+  cluster.sync();   // no CTA leaves while another may still read its buffers
 }
 
 // ---------------------------------------------------------------------------

@@ -86,6 +86,16 @@ jacobi_svd_kernel(const T* __restrict__ M, int l, int64_t ldm, T* __restrict__ s
 }
 
 template <typename T>
+__global__ void __cluster_dims__(JACOBI_CLUSTER, 1, 1) __launch_bounds__(JACOBI_CL_THREADS)
+jacobi_cluster_kernel(const T* __restrict__ M, int l, int64_t ldm, T* __restrict__ sig,
+                      T* __restrict__ Um, int64_t ldu, T* __restrict__ Vm, int64_t ldv,
+                      T* __restrict__ UsInv, DeviceStatus* status) {
+  extern __shared__ __align__(16) unsigned char jcl_raw[];
+  jacobi_cluster_body<T>(M, l, ldm, sig, Um, ldu, Vm, ldv, UsInv, reinterpret_cast<T*>(jcl_raw),
+                         status);
+}
+
+template <typename T>
 __global__ void sign_kernel(T* __restrict__ U, int64_t m, int64_t ldu, T* __restrict__ sign) {
   sign_body<T>(U + (int64_t)blockIdx.x * ldu, m, sign + blockIdx.x);
 }
@@ -129,6 +139,20 @@ template <typename T>
 cudaError_t launch_jacobi_svd(const T* M, int l, int64_t ldm, T* sig, T* Um, int64_t ldu, T* Vm,
                               int64_t ldv, T* UsInv, T* work, DeviceStatus* status,
                               cudaStream_t st) {
+  // FP64, l >= 24: the cluster version (rows over JACOBI_CLUSTER SMs), as one
+  // SM's FP64 pipe (2 FMA per clock) bounds the one-CTA kernel; measured
+  // 3.9 ms against 6.7 ms at l = 80.  FP32 (and small l) stay on one CTA: a
+  // cluster round's barrier and remote stores (~1.3k clocks) cost as much as
+  // the one-CTA round itself.
+  if (sizeof(T) == 8 && l >= 24) {
+    const size_t cneed = jacobi_cluster_elems(l, Vm != nullptr) * sizeof(T);
+    if (cneed <= dynamic_smem_cap((const void*)jacobi_cluster_kernel<T>)) {
+      jacobi_cluster_kernel<T><<<JACOBI_CLUSTER, JACOBI_CL_THREADS, cneed, st>>>(
+          M, l, ldm, sig, Um, ldu, Vm, ldv, UsInv, status);
+      note_launch();
+      return cudaGetLastError();
+    }
+  }
   const int twoP = (l + 1) & ~1;
   const size_t need = (size_t)(Vm ? 2 : 1) * jacobi_ld<T>(l, true) * twoP * sizeof(T);
   const bool smem = need <= dynamic_smem_cap((const void*)jacobi_svd_kernel<T>);
