@@ -607,7 +607,8 @@ def run_ours(args):
         raise RuntimeError(f"e2e solve failed: {R.rsvd_status_string(st)}")
 
     # --- Algorithm 6 (single pass) on the same matrix ---
-    singlepass = run_singlepass(args, world, dA, w, plan)
+    singlepass = run_singlepass(args, world, dA, w, plan, 6)
+    algorithm3 = run_singlepass(args, world, dA, w, plan, 3)
 
     # --- the mixed-precision workload beside it ---
     mixed = mixed_fp8 = None
@@ -643,6 +644,7 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "singlepass": singlepass,
+        "algorithm3": algorithm3,
         "mixed": mixed,
         "mixed_fp8": mixed_fp8,
         "batched": batched,
@@ -660,22 +662,23 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_singlepass(args, world, dA, w, plan):
-    """Algorithm 6 (single-pass RSVD) on the plain workload's matrix: A is
-    read by the two sketches only (2 passes instead of 2q + 2)."""
+def run_singlepass(args, world, dA, w, plan, algorithm=6):
+    """Algorithm 6 (single-pass RSVD: A read by the two sketches only, 2
+    passes instead of 2q + 2) or Algorithm 3 (q power steps without
+    re-orthonormalisation, 2q + 2 passes) on the plain workload's matrix."""
     import torch
 
     from paper_2402_17794_gb300 import rsvd as R
 
-    m, n, k, p, seed = w["m"], w["n"], w["k"], w["p"], w["seed"]
+    m, n, k, p, q, seed = w["m"], w["n"], w["k"], w["p"], w["q"], w["seed"]
     U = torch.empty(k, m, dtype=torch.float64, device="cuda")
     S = torch.empty(k, dtype=torch.float64, device="cuda")
     VT = torch.empty(n, k, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
 
     def step():
-        R._check(R.rsvd_solve_singlepass(plan.handle, dA, m, n, m, k, p, seed, U, m, S, VT, k),
-                 "rsvd_solve_singlepass")
+        R._check(R.rsvd_solve_algorithm(plan.handle, algorithm, dA, m, n, m, k, p, q, seed, U, m, S,
+                                        VT, k), "rsvd_solve_algorithm")
 
     for _ in range(args.warmup):
         step()
@@ -691,12 +694,15 @@ def run_singlepass(args, world, dA, w, plan):
     torch.cuda.synchronize()
     st = plan.status()
     if st != 0:
-        raise RuntimeError(f"single-pass solve failed: {R.rsvd_status_string(st)}")
+        raise RuntimeError(f"algorithm {algorithm} solve failed: {R.rsvd_status_string(st)}")
     ms = _max_over_ranks(e0.elapsed_time(e1), world)
-    return {"workload": "Algorithm 6 (single-pass RSVD) on " + w["desc"].split(";")[0] +
-                        f"; k={k}, p={p}",
+    name = {6: "Algorithm 6 (single-pass RSVD)",
+            3: "Algorithm 3 (power steps without re-orthonormalisation, shifted CholeskyQR3)"}
+    return {"workload": name[algorithm] + " on " + w["desc"].split(";")[0] +
+                        (f"; k={k}, p={p}" if algorithm == 6 else f"; k={k}, p={p}, q={q}"),
             "value": round(steps * world / (ms / 1e3), 4), "unit": "solves/s",
-            "ms_per_solve": round(ms / steps, 4), "passes_per_solve": 2, "dtype": "f64"}
+            "ms_per_solve": round(ms / steps, 4),
+            "passes_per_solve": 2 if algorithm == 6 else 2 * q + 2, "dtype": "f64"}
 
 
 def _traffic_from_profile(key="plain-fp64", pas="atx"):

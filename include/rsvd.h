@@ -186,6 +186,29 @@ int rsvd_solve(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t ld
                void* U, int64_t ldu, double* S, void* VT, int64_t ldvt);
 
 /*
+ * rsvd_solve_algorithm: the rank-k randomized SVD by one of the thesis'
+ * algorithms, all truncated to rank k (Section 3.1) with outputs and signs as
+ * rsvd_solve:
+ *   2  Algorithm 2 (Section 3.1): Algorithm 4 with q = 0 (q is ignored);
+ *   3  Algorithm 3 (Section 3.2, "Accuracy Enhanced Randomized SVD"): q power
+ *      steps Z = A^T Y, Y = A Z with no orthonormalisation in between, then
+ *      one orth(Y).  The sample's condition number grows like
+ *      (sigma_1/sigma_l)^(2q+1), so orth is shifted CholeskyQR3 (a Cholesky
+ *      QR with the Gram shifted by 11 (m l + l (l+1)) u ||Y||_F^2, then
+ *      CholeskyQR2), defined up to condition numbers near 1/u; the thesis
+ *      notes that round-off limits this algorithm's accuracy.  Plain plans.
+ *   4  Algorithm 4 (Section 3.3): rsvd_solve.
+ *   6  Algorithm 6 (Section 3.4.2): rsvd_solve_singlepass (q is ignored).
+ * Argument errors: -1 plan; -2 algorithm; -3 A NULL; -4 m; -5 n; -6 lda;
+ * -7 k; -8 p (or k+p > min(m, n)); -9 q; -11 U NULL; -12 ldu; -13 S NULL;
+ * -14 VT NULL; -15 ldvt.  RSVD_ERR_WORKSPACE as rsvd_solve;
+ * RSVD_ERR_UNSUPPORTED for batch plans, and for 3 or 6 on a mixed plan.
+ */
+int rsvd_solve_algorithm(rsvd_plan_t plan, int algorithm, const void* A, int64_t m, int64_t n,
+                         int64_t lda, int k, int p, int q, uint64_t seed, void* U, int64_t ldu,
+                         double* S, void* VT, int64_t ldvt);
+
+/*
  * rsvd_solve_singlepass: rank-k randomized SVD by Algorithm 6 ("Single-Pass
  * Randomized SVD for a General Matrix", Section 3.4.2): A is read by exactly
  * two sketching products, Y_c = A Omega_c and Y_r = A^T Omega_r (Omega_c

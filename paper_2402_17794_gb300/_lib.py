@@ -37,6 +37,9 @@ SIGNATURES = {
     "rsvd_kernel_launches": (c_uint64, []),
     "rsvd_solve": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_int64, c_int, c_int, c_int,
                            c_uint64, c_void_p, c_int64, P_double, c_void_p, c_int64]),
+    "rsvd_solve_algorithm": (c_int, [c_void_p, c_int, c_void_p, c_int64, c_int64, c_int64, c_int,
+                                     c_int, c_int, c_uint64, c_void_p, c_int64, c_void_p, c_void_p,
+                                     c_int64]),
     "rsvd_solve_singlepass": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_int64, c_int, c_int,
                                       c_uint64, c_void_p, c_int64, c_void_p, c_void_p, c_int64]),
     "rsvd_gaussian": (c_int, [c_void_p, c_int64, c_int, c_uint64, c_uint32, c_int, c_void_p,

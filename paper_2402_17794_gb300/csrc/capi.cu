@@ -288,6 +288,39 @@ int rsvd_solve(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t ld
   return solve_mixed(plan, A, m, n, lda, k, p, q, seed, (float*)U, ldu, S, (float*)VT, ldvt);
 }
 
+int rsvd_solve_algorithm(rsvd_plan_t plan, int algorithm, const void* A, int64_t m, int64_t n,
+                         int64_t lda, int k, int p, int q, uint64_t seed, void* U, int64_t ldu,
+                         double* S, void* VT, int64_t ldvt) {
+  if (!plan) return -1;
+  if (algorithm != 2 && algorithm != 3 && algorithm != 4 && algorithm != 6) return -2;
+  if (!A) return -3;
+  if (m < 1) return -4;
+  if (n < 1) return -5;
+  if (lda < m) return -6;
+  if (k < 1) return -7;
+  if (p < 0) return -8;
+  if (q < 0) return -9;
+  if (!U) return -11;
+  if (ldu < m) return -12;
+  if (!S) return -13;
+  if (!VT) return -14;
+  if (ldvt < k) return -15;
+  const int l = k + p;
+  if (l > (m < n ? m : n)) return -8;
+  if (!ready(plan) || m > plan->m_max || n > plan->n_max || l > plan->l_max)
+    return RSVD_ERR_WORKSPACE;
+  if (plan->batched) return RSVD_ERR_UNSUPPORTED;
+  if (algorithm == 2) q = 0;   // Algorithm 2 is Algorithm 4 without power steps
+  if (algorithm == 2 || algorithm == 4)
+    return rsvd_solve(plan, A, m, n, lda, k, p, q, seed, U, ldu, S, VT, ldvt);
+  if (plan->mode != RSVD_MODE_PLAIN) return RSVD_ERR_UNSUPPORTED;
+  if (algorithm == 3)
+    return solve_plain_alg3(plan, (const double*)A, m, n, lda, k, p, q, seed, (double*)U, ldu, S,
+                            (double*)VT, ldvt);
+  return solve_singlepass(plan, (const double*)A, m, n, lda, k, p, seed, (double*)U, ldu, S,
+                          (double*)VT, ldvt);
+}
+
 int rsvd_solve_singlepass(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t lda,
                           int k, int p, uint64_t seed, void* U, int64_t ldu, double* S, void* VT,
                           int64_t ldvt) {

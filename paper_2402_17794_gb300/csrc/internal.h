@@ -123,6 +123,11 @@ template <typename T>
 cudaError_t launch_chol_inv(const T* G, int64_t ldg, int l, T* R, T* Rinv, T* work,
                             DeviceStatus* status, cudaStream_t st);
 
+// G_ii += coeff * trace(G) for i < l: the diagonal shift of shifted
+// CholeskyQR (one block; the trace is summed in FP64).
+template <typename T>
+cudaError_t launch_shift_diag(T* G, int l, int64_t ldg, double coeff, cudaStream_t st);
+
 // out (l x l, ld l) = R2 * R1 for upper triangular R1, R2 (ld l); if
 // transpose_out, out = (R2 R1)^T.
 template <typename T>

@@ -262,9 +262,51 @@ template int orth<double>(rsvd_plan_t, const double*, int64_t, int, int64_t, dou
 template int orth<float>(rsvd_plan_t, const float*, int64_t, int, int64_t, float*, int64_t, float*,
                          bool);
 
+// Shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa, Yamamoto, Yanagisawa,
+// SIAM J. Sci. Comput. 2020): one Cholesky QR of Y with the Gram shifted by
+// s = 11 (rows l + l (l+1)) u ||Y||_F^2, which keeps the factorisation defined
+// for condition numbers up to about 1/u, then CholeskyQR2 of the result.  Q
+// may not alias Y.  Used where the sample is far worse conditioned than the
+// power steps of Algorithm 4 leave it (Algorithm 3).
+template <typename T>
+int orth_shifted(rsvd_plan_t P, const T* Y, int64_t rows, int l, int64_t ldy, T* Q, int64_t ldq) {
+  Work<T> W = work_of<T>(P);
+  DeviceStatus* st = dstatus(P);
+  int rc;
+  if ((rc = gram<T>(P, Y, ldy, rows, l, W.G))) return rc;
+  const double u = (sizeof(T) == 8) ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
+  RSVD_CK(launch_shift_diag<T>(W.G, l, l, 11.0 * ((double)rows * l + (double)l * (l + 1)) * u,
+                               P->stream));
+  RSVD_CK(launch_chol_inv<T>(W.G, l, l, W.R1, W.R1i, W.cholw, st, P->stream));
+  if ((rc = gemm<T>(P, Y, ldy, false, W.R1i, l, Q, ldq, rows, l, l, true))) return rc;
+  return orth<T>(P, Q, rows, l, ldq, Q, ldq, nullptr, false);
+}
+template int orth_shifted<double>(rsvd_plan_t, const double*, int64_t, int, int64_t, double*,
+                                  int64_t);
+
 // ---------------------------------------------------------------------------
 // Full solves
 // ---------------------------------------------------------------------------
+
+int solve_plain_alg3(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t lda, int k,
+                     int p, int q, uint64_t seed, double* U, int64_t ldu, double* S, double* VT,
+                     int64_t ldvt) {
+  const int l = k + p;
+  Work<double> W = work_of<double>(P);
+  int rc;
+  // Algorithm 3 (Section 3.2): 1. Omega;  2. Y = A Omega;  3-4. q times
+  // Z = A^T Y, Y = A Z, with no orthonormalisation in between;  5. Q = orth(Y)
+  RSVD_CK(launch_gaussian(n, l, seed, 0u, RSVD_F64, W.om, n, P->stream));
+  if ((rc = gemm<double>(P, A, lda, false, W.om, n, W.y, m, m, n, l))) return rc;
+  for (int j = 0; j < q; ++j) {
+    if ((rc = gemm<double>(P, A, lda, true, W.y, m, W.z, n, n, m, l))) return rc;
+    if ((rc = gemm<double>(P, A, lda, false, W.z, n, W.y, m, m, n, l))) return rc;
+  }
+  if ((rc = orth_shifted<double>(P, W.y, m, l, m, W.qm, m))) return rc;
+  // 6. B^T = A^T Q;  7-8. small SVD and lift
+  if ((rc = gemm<double>(P, A, lda, true, W.qm, m, W.z, n, n, m, l))) return rc;
+  return finish<double>(P, W, m, n, l, k, U, ldu, S, VT, ldvt);
+}
 
 int solve_plain(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t lda, int k, int p,
                 int q, uint64_t seed, double* U, int64_t ldu, double* S, double* VT,

@@ -66,6 +66,16 @@ int solve_plain(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t ld
 int solve_mixed(rsvd_plan_t P, const void* A, int64_t m, int64_t n, int64_t lda, int k, int p,
                 int q, uint64_t seed, float* U, int64_t ldu, double* S, float* VT, int64_t ldvt);
 
+// Algorithm 3 (power steps without re-orthonormalisation), FP64; the sample
+// is orthonormalised once by shifted CholeskyQR3.
+int solve_plain_alg3(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t lda, int k,
+                     int p, int q, uint64_t seed, double* U, int64_t ldu, double* S, double* VT,
+                     int64_t ldvt);
+
+// Shifted CholeskyQR3: Q = orth(Y) for ill-conditioned Y (Q must not alias Y).
+template <typename T>
+int orth_shifted(rsvd_plan_t P, const T* Y, int64_t rows, int l, int64_t ldy, T* Q, int64_t ldq);
+
 // Algorithm 6 (single-pass randomized SVD of a general matrix), FP64.
 int solve_singlepass(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t lda, int k,
                      int p, uint64_t seed, double* U, int64_t ldu, double* S, double* VT,

@@ -95,6 +95,23 @@ jacobi_cluster_kernel(const T* __restrict__ M, int l, int64_t ldm, T* __restrict
                          status);
 }
 
+// G_ii += coeff * trace(G): the shift of shifted CholeskyQR (one block).
+template <typename T>
+__global__ void shift_diag_kernel(T* __restrict__ G, int l, int64_t ldg, double coeff) {
+  __shared__ double s_part[32];
+  double tr = 0.0;
+  for (int i = threadIdx.x; i < l; i += blockDim.x) tr += (double)G[i + (int64_t)i * ldg];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+  if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = tr;
+  __syncthreads();
+  double total = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) total += s_part[w];
+  const T s = (T)(coeff * total);
+  __syncthreads();
+  for (int i = threadIdx.x; i < l; i += blockDim.x) G[i + (int64_t)i * ldg] += s;
+}
+
 template <typename T>
 __global__ void sign_kernel(T* __restrict__ U, int64_t m, int64_t ldu, T* __restrict__ sign) {
   sign_body<T>(U + (int64_t)blockIdx.x * ldu, m, sign + blockIdx.x);
@@ -121,6 +138,13 @@ cudaError_t launch_chol_inv(const T* G, int64_t ldg, int l, T* R, T* Rinv, T* wo
     chol_inv_kernel<T><<<1, CHOL_THREADS, smem, st>>>(G, ldg, l, R, Rinv, nullptr, status);
   else
     chol_inv_kernel<T><<<1, CHOL_THREADS, 0, st>>>(G, ldg, l, R, Rinv, work, status);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_shift_diag(T* G, int l, int64_t ldg, double coeff, cudaStream_t st) {
+  shift_diag_kernel<T><<<1, 256, 0, st>>>(G, l, ldg, coeff);
   note_launch();
   return cudaGetLastError();
 }
@@ -181,6 +205,7 @@ cudaError_t launch_finalize(T* U, int64_t m, int64_t ldu, int k, const T* Vk, in
   template cudaError_t launch_chol_inv<T>(const T*, int64_t, int, T*, T*, T*, DeviceStatus*,   \
                                           cudaStream_t);                                       \
   template cudaError_t launch_tri_product<T>(const T*, const T*, int, T*, bool, cudaStream_t); \
+  template cudaError_t launch_shift_diag<T>(T*, int, int64_t, double, cudaStream_t);           \
   template cudaError_t launch_jacobi_svd<T>(const T*, int, int64_t, T*, T*, int64_t, T*,       \
                                             int64_t, T*, T*, DeviceStatus*, cudaStream_t);     \
   template cudaError_t launch_finalize<T>(T*, int64_t, int64_t, int, const T*, int64_t, T*,    \

@@ -129,6 +129,12 @@ def rsvd_solve(plan, A, m, n, lda, k, p, q, seed, U, ldu, S, VT, ldvt) -> int:
                                   _ptr(VT), ldvt)
 
 
+def rsvd_solve_algorithm(plan, algorithm, A, m, n, lda, k, p, q, seed, U, ldu, S, VT,
+                         ldvt) -> int:
+    return _lib.load().rsvd_solve_algorithm(plan, algorithm, _ptr(A), m, n, lda, k, p, q, seed,
+                                            _ptr(U), ldu, _ptr(S), _ptr(VT), ldvt)
+
+
 def rsvd_solve_singlepass(plan, A, m, n, lda, k, p, seed, U, ldu, S, VT, ldvt) -> int:
     return _lib.load().rsvd_solve_singlepass(plan, _ptr(A), m, n, lda, k, p, seed, _ptr(U), ldu,
                                              _ptr(S), _ptr(VT), ldvt)
@@ -264,6 +270,17 @@ class Plan:
         self.scales = scales   # the plan reads it on every later call
         _check(rsvd_set_tile_scales(self.handle, scales, scales.shape[1], scales.shape[0],
                                     scales.shape[1]), "rsvd_set_tile_scales")
+
+    def solve_algorithm(self, algorithm, A, m, n, k, p, q, seed, lda=None):
+        """Algorithm 2, 3, 4 or 6 of the thesis: (U, S, VT) as solve(); enqueued only."""
+        lda = lda or A.shape[1]
+        odt = torch.float64 if self.mode == PLAIN else torch.float32
+        U = torch.empty(k, m, dtype=odt, device=A.device)
+        S = torch.empty(k, dtype=torch.float64, device=A.device)
+        VT = torch.empty(n, k, dtype=odt, device=A.device)
+        _check(rsvd_solve_algorithm(self.handle, algorithm, A, m, n, lda, k, p, q, seed, U, m, S,
+                                    VT, k), "rsvd_solve_algorithm")
+        return U, S, VT
 
     def solve_singlepass(self, A, m, n, k, p, seed, lda=None):
         """Algorithm 6 on a plain plan: (U, S, VT) as solve(); enqueued only."""
