@@ -149,7 +149,8 @@ grouped_jacobi_kernel(const Ctx<T>* __restrict__ ctx, int use_smem) {
   extern __shared__ __align__(16) unsigned char jsm_raw[];
   const Ctx<T>& P = ctx[blockIdx.x];
   T* Wm = use_smem ? reinterpret_cast<T*>(jsm_raw) : P.jw;
-  dense::jacobi_body<T>(P.Mt, P.l, P.l, P.sig, P.Um, P.l, nullptr, P.l, P.UsInv, Wm,
+  dense::jacobi_body<T, dense::JACOBI_REGS_SMALL>(P.Mt, P.l, P.l, P.sig, P.Um, P.l, nullptr, P.l,
+                                                  P.UsInv, Wm,
                         dense::jacobi_ld<T>(P.l, use_smem != 0), P.status);
 }
 

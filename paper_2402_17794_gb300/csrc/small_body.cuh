@@ -434,11 +434,14 @@ __host__ __device__ inline int jacobi_ld(int l, bool in_smem) {
   return (l + 31) / 32 * 32 + G;
 }
 
-// Rows of a column pair a thread keeps in registers across one round.
+// Rows of a column pair a thread keeps in registers across one round (a
+// kernel serving only small l takes fewer, and so no spills).
 template <typename T>
 struct JacobiRegs {
   static constexpr int value = sizeof(T) == 4 ? 20 : 10;
 };
+// ... for the grouped kernels (l <= 80: 16 threads per pair leave <= 5 rows)
+constexpr int JACOBI_REGS_SMALL = 6;
 
 // Work layout: Wm (ldw x twoP) and, if V is accumulated, Wv (ldw x twoP),
 // column-major; in dynamic shared memory when they fit, else in `gwork`.
@@ -450,13 +453,12 @@ struct JacobiRegs {
 // it holds -- one barrier per round.  FP64: the rotation costs tens of FP64
 // operations at 2 per clock per SM, so one thread per pair forms it between
 // two barriers and the group then applies it.
-template <typename T>
+template <typename T, int RMAX = JacobiRegs<T>::value>
 __device__ __forceinline__ void jacobi_body(const T* __restrict__ M, int l, int64_t ldm,
                                             T* __restrict__ sig, T* __restrict__ Um, int64_t ldu,
                                             T* __restrict__ Vm, int64_t ldv,
                                             T* __restrict__ UsInv, T* __restrict__ Wm, int ldw,
                                             DeviceStatus* status) {
-  constexpr int RMAX = JacobiRegs<T>::value;
   constexpr bool kFused = sizeof(T) == 4;
   const int twoP = (l + 1) & ~1;  // even number of columns (one zero column if l is odd)
   const int P = twoP / 2;
