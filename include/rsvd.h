@@ -82,6 +82,9 @@ typedef enum {
 #define RSVD_ERR_CUDA 5        /* a CUDA runtime call or launch failed      */
 #define RSVD_ERR_NONFINITE 6   /* NaN or Inf met in A (through Y = A Omega) */
 #define RSVD_ERR_UNSUPPORTED 7 /* dtype/mode/size not built into this library */
+#define RSVD_ERR_NOT_REACHED 8 /* adaptive range finder: the tolerance was not
+                                  met within l_cap columns (the result holds
+                                  l_cap columns and is otherwise valid)      */
 
 /* Largest k+p the library accepts (the l x l steps keep l x l FP64 tiles). */
 #define RSVD_L_MAX 288
@@ -227,6 +230,54 @@ int rsvd_solve_algorithm(rsvd_plan_t plan, int algorithm, const void* A, int64_t
 int rsvd_solve_singlepass(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t lda,
                           int k, int p, uint64_t seed, void* U, int64_t ldu, double* S,
                           void* VT, int64_t ldvt);
+
+/*
+ * rsvd_range_adaptive: the adaptive randomized range finder ("Adaptive_randRF"
+ * in Section 4's function list, which names Algorithm 4.2 of Halko,
+ * Martinsson and Tropp, SIAM Review 53 (2011) as its source).  Given A, a
+ * tolerance eps and an integer r, it builds Q with orthonormal columns such
+ * that ||(I - Q Q^T) A||_2 <= eps with probability at least
+ * 1 - min(m, n) 10^-r.  Samples A omega_1, A omega_2, ... (omega_i = column
+ * i-1 of the Gaussian of rsvd_gaussian, stream 0 of `seed`) are
+ * orthonormalised in order (Gram-Schmidt order, so q_j is fixed by the first
+ * j samples); the search stops at the first j where the next r samples'
+ * residuals against Q_j are all at most eps / (10 sqrt(2/pi)).  The rank j is
+ * then written to *rank (host int) and Q's first j columns are valid.
+ * Work is done in blocks of up to 64 samples (one pass over A each); the
+ * call WAITS on the plan's stream once per block to read the stopping test,
+ * and returns with the last column copy still enqueued.  Plain (FP64) plans.
+ *   eps    > 0, absolute (the norm of A is not applied).  Below about 1e-12
+ *          of ||A|| the residuals are rounding noise: the search then stops
+ *          where CholeskyQR finds the sample numerically dependent.
+ *   r      1 <= r < min(64, plan l_max); r = 10 is the usual choice.
+ *   l_cap  1 <= l_cap <= min(m, n, plan l_max): the most columns accepted.
+ *   Q      m x l_cap, ldq >= m (device, FP64).
+ * Returns RSVD_OK when the test passed, RSVD_ERR_NOT_REACHED when l_cap
+ * columns were accepted first (Q then holds l_cap valid columns), or the
+ * status (RSVD_ERR_NONFINITE, ...) that the device work of this call set.
+ * Argument errors: -1 plan; -2 A NULL; -3 m; -4 n; -5 lda; -6 eps; -7 r;
+ * -8 l_cap; -10 Q NULL; -11 ldq; -12 rank NULL.  RSVD_ERR_WORKSPACE if the
+ * plan's sizes do not cover m, n, l_cap; RSVD_ERR_UNSUPPORTED for mixed or
+ * batch plans.
+ */
+int rsvd_range_adaptive(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t lda,
+                        double eps, int r, int l_cap, uint64_t seed, void* Q, int64_t ldq,
+                        int* rank);
+
+/*
+ * rsvd_solve_adaptive: rsvd_range_adaptive, then Stage B of the prototype
+ * (Algorithm 1 / Section 2.2) with every column of Q kept: B = Q^T A (as
+ * B^T = A^T Q), B = U~ Sigma V^T, U = Q U~.  The tolerance, not k, fixes the
+ * rank j = *rank; U (m x j, ldu >= m), S (j, descending) and VT (j x n,
+ * ldvt >= l_cap) are FP64 with the signs of rsvd_solve.  Returns as
+ * rsvd_range_adaptive (the outputs are valid for RSVD_OK and
+ * RSVD_ERR_NOT_REACHED; nothing is written when j = 0).
+ * Argument errors: -1 .. -8 as rsvd_range_adaptive; -10 U NULL; -11 ldu;
+ * -12 S NULL; -13 VT NULL; -14 ldvt; -15 rank NULL.
+ */
+int rsvd_solve_adaptive(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t lda,
+                        double eps, int r, int l_cap, uint64_t seed, void* U, int64_t ldu,
+                        double* S, void* VT, int64_t ldvt, int* rank);
 
 /* ---------------------------------------------------------------------- */
 /* Step-level entry points (the rows of the hot path, one call per step).   */

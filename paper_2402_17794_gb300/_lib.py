@@ -42,6 +42,12 @@ SIGNATURES = {
                                      c_int64]),
     "rsvd_solve_singlepass": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_int64, c_int, c_int,
                                       c_uint64, c_void_p, c_int64, c_void_p, c_void_p, c_int64]),
+    "rsvd_range_adaptive": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_int64, ctypes.c_double,
+                                    c_int, c_int, c_uint64, c_void_p, c_int64,
+                                    ctypes.POINTER(c_int)]),
+    "rsvd_solve_adaptive": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_int64, ctypes.c_double,
+                                    c_int, c_int, c_uint64, c_void_p, c_int64, c_void_p,
+                                    c_void_p, c_int64, ctypes.POINTER(c_int)]),
     "rsvd_gaussian": (c_int, [c_void_p, c_int64, c_int, c_uint64, c_uint32, c_int, c_void_p,
                               c_int64]),
     "rsvd_apply_a": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_int64, c_void_p, c_int64,

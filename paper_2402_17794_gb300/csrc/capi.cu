@@ -5,6 +5,7 @@
 // GPU except rsvd_plan_status().  The workspace is one caller-owned device
 // block carved into fixed regions at plan creation; no call after
 // rsvd_plan_create() allocates.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -70,12 +71,12 @@ int rsvd_plan_create(rsvd_plan_t* plan, int64_t m_max, int64_t n_max, int l_max,
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaMallocHost((void**)&P->h_status, sizeof(int) * 4) != cudaSuccess) {
+      cudaMallocHost((void**)&P->h_status, sizeof(int) * 8) != cudaSuccess) {
     delete P;
     return RSVD_ERR_CUDA;
   }
   P->lay = make_layout(m_max, n_max, l_max, mode, P->num_sms);
-  std::memset(P->h_status, 0, sizeof(int) * 4);
+  std::memset(P->h_status, 0, sizeof(int) * 8);
   *plan = P;
   return RSVD_OK;
 }
@@ -254,6 +255,7 @@ const char* rsvd_status_string(int status) {
     case RSVD_ERR_CUDA: return "CUDA error";
     case RSVD_ERR_NONFINITE: return "non-finite value in the input";
     case RSVD_ERR_UNSUPPORTED: return "unsupported dtype, mode or size";
+    case RSVD_ERR_NOT_REACHED: return "tolerance not reached within l_cap columns";
     default: break;
   }
   if (status < 0) return "invalid argument";
@@ -343,6 +345,57 @@ int rsvd_solve_singlepass(rsvd_plan_t plan, const void* A, int64_t m, int64_t n,
   if (plan->mode != RSVD_MODE_PLAIN || plan->batched) return RSVD_ERR_UNSUPPORTED;
   return solve_singlepass(plan, (const double*)A, m, n, lda, k, p, seed, (double*)U, ldu, S,
                           (double*)VT, ldvt);
+}
+
+namespace {
+
+// Shared argument checks of the two adaptive entry points (positions of
+// A .. seed are the same in both); returns 0 or the error code.
+int adaptive_args(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t lda, double eps,
+                  int r, int l_cap, const int* rank) {
+  if (!plan) return -1;
+  if (!A) return -2;
+  if (m < 1) return -3;
+  if (n < 1) return -4;
+  if (lda < m) return -5;
+  if (!(eps > 0.0) || !std::isfinite(eps)) return -6;
+  if (r < 1) return -7;
+  if (l_cap < 1 || l_cap > (m < n ? m : n)) return -8;
+  if (!rank) return -20;
+  if (!ready(plan) || m > plan->m_max || n > plan->n_max || l_cap > plan->l_max)
+    return RSVD_ERR_WORKSPACE;
+  if (r >= (plan->l_max < 64 ? plan->l_max : 64)) return -7;
+  if (plan->mode != RSVD_MODE_PLAIN || plan->batched) return RSVD_ERR_UNSUPPORTED;
+  return 0;
+}
+
+}  // namespace
+
+int rsvd_range_adaptive(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t lda,
+                        double eps, int r, int l_cap, uint64_t seed, void* Q, int64_t ldq,
+                        int* rank) {
+  int rc = adaptive_args(plan, A, m, n, lda, eps, r, l_cap, rank);
+  if (rc == -20) return -12;
+  if (rc) return rc;
+  if (!Q) return -10;
+  if (ldq < m) return -11;
+  return range_adaptive(plan, (const double*)A, m, n, lda, eps, r, l_cap, seed, (double*)Q, ldq,
+                        rank);
+}
+
+int rsvd_solve_adaptive(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t lda,
+                        double eps, int r, int l_cap, uint64_t seed, void* U, int64_t ldu,
+                        double* S, void* VT, int64_t ldvt, int* rank) {
+  int rc = adaptive_args(plan, A, m, n, lda, eps, r, l_cap, rank);
+  if (rc == -20) return -15;
+  if (rc) return rc;
+  if (!U) return -10;
+  if (ldu < m) return -11;
+  if (!S) return -12;
+  if (!VT) return -13;
+  if (ldvt < l_cap) return -14;
+  return solve_adaptive(plan, (const double*)A, m, n, lda, eps, r, l_cap, seed, (double*)U, ldu,
+                        S, (double*)VT, ldvt, rank);
 }
 
 int rsvd_gaussian(rsvd_plan_t plan, int64_t n, int l, uint64_t seed, uint32_t stream, int out_dtype,

@@ -27,7 +27,9 @@ struct DeviceStatus {
   int flags;        // bit (1 << RSVD_ERR_*) set by kernels
   int jacobi_sweeps;
   int deficient;    // number of dropped (deficient) columns in the last orth
-  int pad[61];
+  int ad_stop;      // adaptive range finder: accepted columns at the stop, or -1
+  int ad_dropped;   // adaptive range finder: first dropped column of the block
+  int pad[59];
 };
 
 inline int status_from_flags(int flags) {
@@ -42,6 +44,7 @@ inline int status_from_flags(int flags) {
 struct Layout {
   size_t status, om, y, qm, tmp, z, qb, part, small, total;
   size_t sp;            // l x l slots of the single-pass solve (Algorithm 6)
+  size_t ad;            // second m x l sample buffer of the adaptive range finder
   // mixed-mode extras: BF16 operand slices (om16), tcgen05 partial slots (y32)
   size_t om16, y32;
   size_t small_stride;  // bytes of one l x l FP64 matrix (padded)
@@ -80,13 +83,14 @@ namespace rsvd {
 // ---- kernels' host launchers (all enqueue on `st`) ----
 
 // Omega (n x l) for (seed, stream): FP64, FP32 or BF16 output, each rounded
-// from the FP64 value.  kOutF32Fast (internal, mixed path): FP32 Box-Muller on
+// from the FP64 value; columns col0 .. col0+l-1 of the generator's matrix.  kOutF32Fast (internal, mixed path): FP32 Box-Muller on
 // 24-bit uniforms from the same Philox words (the FP64 transcendental
 // functions run at the FP64 rate, 1/64 of FP32 on this GPU).
 constexpr int kOutF32 = RSVD_F32;
 constexpr int kOutF32Fast = 101;
 cudaError_t launch_gaussian(int64_t n, int l, uint64_t seed, uint32_t stream_id,
-                            int out_dtype, void* out, int64_t ldo, cudaStream_t st);
+                            int out_dtype, void* out, int64_t ldo, cudaStream_t st,
+                            int64_t col0 = 0);
 
 // Tall-skinny GEMM on the CUDA cores:  C (M x N) = op(A) X,  op(A) = A (M x K,
 // lda) or A^T (A stored K x M, lda).  X is K x N (ldx).  Split-K partials go

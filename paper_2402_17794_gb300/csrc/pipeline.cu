@@ -99,28 +99,6 @@ int mixed_pass(rsvd_plan_t P, bool ax, const void* A, int64_t m, int64_t n, int6
   return launch_apass_bf16(c, P->num_sms, &dstatus(P)->flags, P->stream);
 }
 
-template <typename T>
-int finish(rsvd_plan_t P, const Work<T>& W, int64_t m, int64_t n, int l, int k, T* U, int64_t ldu,
-           double* S, T* VT, int64_t ldvt) {
-  int rc;
-  // B^T (in W.z) = Q_B R_B: only R_B is formed; Mt = R_B^T
-  if ((rc = orth<T>(P, W.z, n, l, n, nullptr, n, W.Mt, true))) return rc;
-  // one-sided Jacobi on R_B^T = U~ Sigma V_R^T; U~ are B's left singular vectors
-  T* us_inv = W.Vm;
-  RSVD_CK(launch_jacobi_svd<T>(W.Mt, l, l, W.sig, W.Um, l, nullptr, l, us_inv, W.jw, dstatus(P),
-                               P->stream));
-  // step 8: U = Q U~ (first k columns)
-  if ((rc = gemm<T>(P, W.qm, m, false, W.Um, l, U, ldu, m, l, k))) return rc;
-  // V_k = B^T U~_k Sigma_k^-1, then one CholeskyQR pass restores orthonormality
-  // to rounding (the product carries relative errors ~ eps sigma_1/sigma_i)
-  if ((rc = gemm<T>(P, W.z, n, false, us_inv, l, W.tmp, n, n, l, k))) return rc;
-  if ((rc = gram<T>(P, W.tmp, n, n, k, W.G))) return rc;
-  RSVD_CK(launch_chol_inv<T>(W.G, k, k, W.R1, W.R1i, W.cholw, dstatus(P), P->stream));
-  if ((rc = gemm<T>(P, W.tmp, n, false, W.R1i, k, W.qb, n, n, k, k, true))) return rc;
-  RSVD_CK(launch_finalize<T>(U, m, ldu, k, W.qb, n, VT, ldvt, W.sig, S, W.sign, P->stream));
-  return RSVD_OK;
-}
-
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -152,6 +130,7 @@ Layout make_layout(int64_t m, int64_t n, int l, int mode, int num_sms) {
                  align_up(2 * (size_t)l * e) +
                  align_up(((size_t)l * l + 33 * (size_t)(l + 64)) * e));
   L.sp = take(L.small_stride * kSinglePassSlots + align_up(kSinglePassVecs * (size_t)l * e));
+  L.ad = take((size_t)m * l * e);
   if (mode == RSVD_MODE_MIXED) {
     const int l16 = (l + 15) / 16 * 16;
     L.om16 = take((size_t)round8(mn) * 3 * l16 * sizeof(__nv_bfloat16));
@@ -283,6 +262,31 @@ int orth_shifted(rsvd_plan_t P, const T* Y, int64_t rows, int l, int64_t ldy, T*
 }
 template int orth_shifted<double>(rsvd_plan_t, const double*, int64_t, int, int64_t, double*,
                                   int64_t);
+
+template <typename T>
+int finish(rsvd_plan_t P, const Work<T>& W, int64_t m, int64_t n, int l, int k, T* U, int64_t ldu,
+           double* S, T* VT, int64_t ldvt) {
+  int rc;
+  // B^T (in W.z) = Q_B R_B: only R_B is formed; Mt = R_B^T
+  if ((rc = orth<T>(P, W.z, n, l, n, nullptr, n, W.Mt, true))) return rc;
+  // one-sided Jacobi on R_B^T = U~ Sigma V_R^T; U~ are B's left singular vectors
+  T* us_inv = W.Vm;
+  RSVD_CK(launch_jacobi_svd<T>(W.Mt, l, l, W.sig, W.Um, l, nullptr, l, us_inv, W.jw, dstatus(P),
+                               P->stream));
+  // step 8: U = Q U~ (first k columns)
+  if ((rc = gemm<T>(P, W.qm, m, false, W.Um, l, U, ldu, m, l, k))) return rc;
+  // V_k = B^T U~_k Sigma_k^-1, then one CholeskyQR pass restores orthonormality
+  // to rounding (the product carries relative errors ~ eps sigma_1/sigma_i)
+  if ((rc = gemm<T>(P, W.z, n, false, us_inv, l, W.tmp, n, n, l, k))) return rc;
+  if ((rc = gram<T>(P, W.tmp, n, n, k, W.G))) return rc;
+  RSVD_CK(launch_chol_inv<T>(W.G, k, k, W.R1, W.R1i, W.cholw, dstatus(P), P->stream));
+  if ((rc = gemm<T>(P, W.tmp, n, false, W.R1i, k, W.qb, n, n, k, k, true))) return rc;
+  RSVD_CK(launch_finalize<T>(U, m, ldu, k, W.qb, n, VT, ldvt, W.sig, S, W.sign, P->stream));
+  return RSVD_OK;
+}
+
+template int finish<double>(rsvd_plan_t, const Work<double>&, int64_t, int64_t, int, int,
+                           double*, int64_t, double*, double*, int64_t);
 
 // ---------------------------------------------------------------------------
 // Full solves

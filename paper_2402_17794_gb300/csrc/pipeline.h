@@ -60,6 +60,12 @@ template <typename T>
 int orth(rsvd_plan_t P, const T* Y, int64_t rows, int l, int64_t ldy, T* Q, int64_t ldq,
          T* Rprod, bool transpose_R);
 
+// Steps 6-8 after B^T = A^T Q is in W.z and Q in W.qm (m x l): small SVD of
+// B, U = Q U~ and V, truncated to k columns, signs and output layout.
+template <typename T>
+int finish(rsvd_plan_t P, const Work<T>& W, int64_t m, int64_t n, int l, int k, T* U, int64_t ldu,
+           double* S, T* VT, int64_t ldvt);
+
 int solve_plain(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t lda, int k, int p,
                 int q, uint64_t seed, double* U, int64_t ldu, double* S, double* VT,
                 int64_t ldvt);
@@ -80,6 +86,17 @@ int orth_shifted(rsvd_plan_t P, const T* Y, int64_t rows, int l, int64_t ldy, T*
 int solve_singlepass(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t lda, int k,
                      int p, uint64_t seed, double* U, int64_t ldu, double* S, double* VT,
                      int64_t ldvt);
+
+// Adaptive randomized range finder (Halko, Martinsson, Tropp 2011, Algorithm
+// 4.2), FP64, blocked: Q (ldq) gets rank <= l_cap orthonormal columns.
+// Synchronous.  RSVD_OK when the tolerance test passed, RSVD_ERR_NOT_REACHED
+// when l_cap columns were reached first.
+int range_adaptive(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t lda, double eps,
+                   int r, int l_cap, uint64_t seed, double* Q, int64_t ldq, int* rank);
+// The adaptive range followed by B = Q^T A, its SVD and U = Q U~ (all columns).
+int solve_adaptive(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t lda, double eps,
+                   int r, int l_cap, uint64_t seed, double* U, int64_t ldu, double* S, double* VT,
+                   int64_t ldvt, int* rank);
 
 // Step entry: one tcgen05 pass with a BF16 operand X (ldx) of `l` columns.
 int mixed_apply(rsvd_plan_t P, const void* A, int64_t m, int64_t n, int64_t lda, const void* X,

@@ -19,6 +19,7 @@ import torch
 from . import _lib
 
 F64, F32, BF16, FP8E4M3 = 0, 1, 2, 3
+ERR_NOT_REACHED = 8
 PLAIN, MIXED = 0, 1
 STATUS = {0: "ok", 1: "cholesky", 2: "jacobi", 3: "timeout", 4: "workspace", 5: "cuda",
           6: "nonfinite", 7: "unsupported"}
@@ -133,6 +134,23 @@ def rsvd_solve_algorithm(plan, algorithm, A, m, n, lda, k, p, q, seed, U, ldu, S
                          ldvt) -> int:
     return _lib.load().rsvd_solve_algorithm(plan, algorithm, _ptr(A), m, n, lda, k, p, q, seed,
                                             _ptr(U), ldu, _ptr(S), _ptr(VT), ldvt)
+
+
+def rsvd_range_adaptive(plan, A, m, n, lda, eps, r, l_cap, seed, Q, ldq):
+    """(code, rank); waits on the plan's stream once per block of samples."""
+    rank = ctypes.c_int(0)
+    code = _lib.load().rsvd_range_adaptive(plan, _ptr(A), m, n, lda, float(eps), r, l_cap, seed,
+                                           _ptr(Q), ldq, ctypes.byref(rank))
+    return code, rank.value
+
+
+def rsvd_solve_adaptive(plan, A, m, n, lda, eps, r, l_cap, seed, U, ldu, S, VT, ldvt):
+    """(code, rank); waits on the plan's stream once per block of samples."""
+    rank = ctypes.c_int(0)
+    code = _lib.load().rsvd_solve_adaptive(plan, _ptr(A), m, n, lda, float(eps), r, l_cap, seed,
+                                           _ptr(U), ldu, _ptr(S), _ptr(VT), ldvt,
+                                           ctypes.byref(rank))
+    return code, rank.value
 
 
 def rsvd_solve_singlepass(plan, A, m, n, lda, k, p, seed, U, ldu, S, VT, ldvt) -> int:
@@ -291,6 +309,29 @@ class Plan:
         _check(rsvd_solve_singlepass(self.handle, A, m, n, lda, k, p, seed, U, m, S, VT, k),
                "rsvd_solve_singlepass")
         return U, S, VT
+
+    def range_adaptive(self, A, m, n, eps, r, l_cap, seed, lda=None):
+        """Adaptive range finder on a plain plan: (Q (rank, m) column-major,
+        converged).  Waits on the plan's stream once per block of samples."""
+        lda = lda or A.shape[1]
+        Q = torch.empty(l_cap, m, dtype=torch.float64, device=A.device)
+        code, rank = rsvd_range_adaptive(self.handle, A, m, n, lda, eps, r, l_cap, seed, Q, m)
+        if code not in (0, ERR_NOT_REACHED):
+            _check(code, "rsvd_range_adaptive")
+        return Q[:rank], code == 0
+
+    def solve_adaptive(self, A, m, n, eps, r, l_cap, seed, lda=None):
+        """Adaptive range finder + small SVD: (U (rank, m), S (rank,),
+        VT (n, l_cap)[:, :rank] view, converged); the rank is S.numel()."""
+        lda = lda or A.shape[1]
+        U = torch.empty(l_cap, m, dtype=torch.float64, device=A.device)
+        S = torch.empty(l_cap, dtype=torch.float64, device=A.device)
+        VT = torch.empty(n, l_cap, dtype=torch.float64, device=A.device)
+        code, rank = rsvd_solve_adaptive(self.handle, A, m, n, lda, eps, r, l_cap, seed, U, m, S,
+                                         VT, l_cap)
+        if code not in (0, ERR_NOT_REACHED):
+            _check(code, "rsvd_solve_adaptive")
+        return U[:rank], S[:rank], VT[:, :rank], code == 0
 
     def solve(self, A, m, n, k, p, q, seed, lda=None, out=None):
         """A: column-major device tensor (n, lda).  Returns (U, S, VT) as
