@@ -662,6 +662,7 @@ def run_ours(args):
     # --- Algorithm 6 (single pass) on the same matrix ---
     singlepass = run_singlepass(args, world, dA, w, plan, 6)
     algorithm3 = run_singlepass(args, world, dA, w, plan, 3)
+    adaptive = run_adaptive(args, world, dA, w)
 
     # --- the mixed-precision workload beside it ---
     mixed = mixed_fp8 = None
@@ -698,6 +699,7 @@ def run_ours(args):
         "e2e": e2e,
         "singlepass": singlepass,
         "algorithm3": algorithm3,
+        "adaptive": adaptive,
         "mixed": mixed,
         "mixed_fp8": mixed_fp8,
         "batched": batched,
@@ -756,6 +758,58 @@ def run_singlepass(args, world, dA, w, plan, algorithm=6):
             "value": round(steps * world / (ms / 1e3), 4), "unit": "solves/s",
             "ms_per_solve": round(ms / steps, 4),
             "passes_per_solve": 2 if algorithm == 6 else 2 * q + 2, "dtype": "f64"}
+
+
+ADAPTIVE = dict(eps=0.25, r=10, l_cap=128)
+
+
+def run_adaptive(args, world, dA, w):
+    """The adaptive range finder + SVD (Halko et al. Algorithm 4.2, the
+    toolbox's Adaptive_randRF) on the plain workload's matrix: the tolerance
+    eps (absolute; sigma_1 = 1) fixes the rank.  The host waits once per
+    block of up to 64 samples to read the stopping test."""
+    import torch
+
+    from paper_2402_17794_gb300 import rsvd as R
+
+    m, n, seed = w["m"], w["n"], w["seed"]
+    eps, r, cap = ADAPTIVE["eps"], ADAPTIVE["r"], ADAPTIVE["l_cap"]
+    plan = R.Plan(m, n, cap)
+    U = torch.empty(cap, m, dtype=torch.float64, device="cuda")
+    S = torch.empty(cap, dtype=torch.float64, device="cuda")
+    VT = torch.empty(n, cap, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    rank = [0]
+
+    def step():
+        code, rank[0] = R.rsvd_solve_adaptive(plan.handle, dA, m, n, m, eps, r, cap, seed, U, m,
+                                              S, VT, cap)
+        if code not in (0, R.ERR_NOT_REACHED):
+            R._check(code, "rsvd_solve_adaptive")
+        return code
+
+    for _ in range(args.warmup):
+        step()
+    steps = max(args.steps, 5)
+    _barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        code = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    st = plan.status()
+    if st != 0:
+        raise RuntimeError(f"adaptive solve failed: {R.rsvd_status_string(st)}")
+    ms = _max_over_ranks(e0.elapsed_time(e1), world)
+    del plan
+    return {"workload": "adaptive range finder + SVD (Halko et al. Alg. 4.2) on " +
+                        w["desc"].split(";")[0] + f"; eps={eps}, r={r}, l_cap={cap}",
+            "value": round(steps * world / (ms / 1e3), 4), "unit": "solves/s",
+            "ms_per_solve": round(ms / steps, 4), "rank": rank[0],
+            "tolerance_met": code == 0, "dtype": "f64"}
 
 
 def _traffic_from_profile(key="plain-fp64", pas="atx"):

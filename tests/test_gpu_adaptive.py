@@ -153,3 +153,28 @@ def test_adaptive_argument_errors():
     # A = 0: the first r samples already meet any tolerance, rank 0
     code, rank = f(plan.handle, A, 100, 80, 100, 1e-3, 5, 20, 0, Q, 100)
     assert code == 0 and rank == 0
+
+
+def test_adaptive_config_full_size_fp64():
+    """The benchmark's adaptive solve: A 16384 x 8192 FP64, Haar factors,
+    sigma_i = i^-1.5, eps = 0.25, r = 10, l_cap = 128, in the launch
+    configuration the benchmark times."""
+    m, n = 16384, 8192
+    eps, r, cap = 0.25, 10, 128
+    dA = syn.lowrank_matrix_torch(m, n, syn.spectrum("poly", n, alpha=1.5), seed=0)
+    A = np.asfortranarray(dA.cpu().numpy().T)
+    ref = ad.adaptive_rsvd(A, eps, r, seed=2, l_max=cap)
+    assert _margin_ok(ref.range) and ref.range.converged
+    plan = R.Plan(m, n, cap)
+    U, S, VT, conv = plan.solve_adaptive(dA, m, n, eps, r, cap, seed=2)
+    assert plan.status() == 0 and conv
+    j = ref.range.rank
+    assert S.numel() == j
+    s = S.cpu().numpy()
+    rel = np.abs(s - ref.S) / ref.S
+    assert rel.max() <= 1e-10, rel.max()
+    u, vt = R.to_numpy_f(U), R.to_numpy_f(VT)
+    r_gpu = analysis.lowrank_residual(A, u, s, vt)
+    r_orc = analysis.lowrank_residual(A, ref.U, ref.S, ref.Vt)
+    assert r_gpu <= 1.0001 * r_orc, (r_gpu, r_orc)
+    assert r_gpu <= eps
