@@ -24,4 +24,4 @@ from .philox import philox4x32_10, gaussian_matrix  # noqa: F401
 from .randsvd import (  # noqa: F401
     RsvdResult, orth, range_finder, rsvd, sign_normalise,
 )
-from . import adaptive, analysis  # noqa: F401
+from . import adaptive, analysis, srft  # noqa: F401
