@@ -279,6 +279,39 @@ int rsvd_solve_adaptive(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, i
                         double eps, int r, int l_cap, uint64_t seed, void* U, int64_t ldu,
                         double* S, void* VT, int64_t ldvt, int* rank);
 
+/*
+ * rsvd_range_srft: the fast randomized range finder ("FastRandRF" in Section
+ * 4's function list, Algorithm 4.5 of Halko, Martinsson and Tropp 2011) with
+ * the subsampled random Fourier transform the thesis defines ("SRFT"):
+ *   Omega = sqrt(n/l) D F R  (n x l, complex), Y = A Omega, Q = orth(Y),
+ *   D  diagonal, d_j = exp(2 pi i u_j), u_j the 52-bit Philox uniform of
+ *      counter j on stream 2 of `seed` (uniform on the unit circle);
+ *   F  the unitary DFT, f_pq = n^-1/2 exp(-2 pi i p q / n) (0-based p, q);
+ *   R  l distinct coordinates of [0, n) drawn by Floyd's algorithm (step s,
+ *      j = n-l+s: t = min(floor(u_s (j+1)), j) with u_s the Philox uniform of
+ *      counter s on stream 3; add t, or j if t is taken), used in ascending
+ *      order.
+ * Q (m x l, complex, orthonormal columns; column c is the Gram-Schmidt vector
+ * of Y's column c, normalised so that q_c^H y_c > 0) is written PLANAR: the
+ * real m x 2l matrix [Re Q | Im Q] with leading dimension ldq >= m.
+ * Plain (FP64) plans whose l_max is at least 2l (the complex sample is held
+ * as 2l real columns); 2l <= RSVD_L_MAX.  Enqueued on the plan's stream.
+ * Argument errors: -1 plan; -2 A NULL; -3 m; -4 n (also n > INT32_MAX);
+ * -5 lda; -6 l (1 <= l <= min(m, n), 2l <= RSVD_L_MAX); -8 Q NULL; -9 ldq.
+ * RSVD_ERR_WORKSPACE if the plan does not cover m, n or 2l;
+ * RSVD_ERR_UNSUPPORTED for mixed or batch plans.
+ */
+int rsvd_range_srft(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t lda, int l,
+                    uint64_t seed, void* Q, int64_t ldq);
+
+/*
+ * rsvd_srft_sketch: the sketch alone, Y = A Omega with the SRFT Omega of
+ * rsvd_range_srft (same seed, same D and R), written planar to Y (real
+ * m x 2l, ldy >= m).  Arguments and errors as rsvd_range_srft (Y for Q).
+ */
+int rsvd_srft_sketch(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t lda, int l,
+                     uint64_t seed, void* Y, int64_t ldy);
+
 /* ---------------------------------------------------------------------- */
 /* Step-level entry points (the rows of the hot path, one call per step).   */
 /* In plain mode every buffer is FP64; the mixed-mode types are noted.     */

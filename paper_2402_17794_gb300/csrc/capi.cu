@@ -5,6 +5,7 @@
 // GPU except rsvd_plan_status().  The workspace is one caller-owned device
 // block carved into fixed regions at plan creation; no call after
 // rsvd_plan_create() allocates.
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -396,6 +397,40 @@ int rsvd_solve_adaptive(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, i
   if (ldvt < l_cap) return -14;
   return solve_adaptive(plan, (const double*)A, m, n, lda, eps, r, l_cap, seed, (double*)U, ldu,
                         S, (double*)VT, ldvt, rank);
+}
+
+namespace {
+
+int srft_args(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t lda, int l,
+              const void* out, int64_t ldo) {
+  if (!plan) return -1;
+  if (!A) return -2;
+  if (m < 1) return -3;
+  if (n < 1 || n > INT32_MAX) return -4;
+  if (lda < m) return -5;
+  if (l < 1 || l > (m < n ? m : n) || 2 * l > RSVD_L_MAX) return -6;
+  if (!out) return -8;
+  if (ldo < m) return -9;
+  if (!ready(plan) || m > plan->m_max || n > plan->n_max || 2 * l > plan->l_max)
+    return RSVD_ERR_WORKSPACE;
+  if (plan->mode != RSVD_MODE_PLAIN || plan->batched) return RSVD_ERR_UNSUPPORTED;
+  return 0;
+}
+
+}  // namespace
+
+int rsvd_range_srft(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t lda, int l,
+                    uint64_t seed, void* Q, int64_t ldq) {
+  const int rc = srft_args(plan, A, m, n, lda, l, Q, ldq);
+  if (rc) return rc;
+  return range_srft(plan, (const double*)A, m, n, lda, l, seed, (double*)Q, ldq);
+}
+
+int rsvd_srft_sketch(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t lda, int l,
+                     uint64_t seed, void* Y, int64_t ldy) {
+  const int rc = srft_args(plan, A, m, n, lda, l, Y, ldy);
+  if (rc) return rc;
+  return sketch_srft(plan, (const double*)A, m, n, lda, l, seed, (double*)Y, ldy);
 }
 
 int rsvd_gaussian(rsvd_plan_t plan, int64_t n, int l, uint64_t seed, uint32_t stream, int out_dtype,

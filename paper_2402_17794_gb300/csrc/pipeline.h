@@ -98,6 +98,26 @@ int solve_adaptive(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t
                    int r, int l_cap, uint64_t seed, double* U, int64_t ldu, double* S, double* VT,
                    int64_t ldvt, int* rank);
 
+// SRFT test matrix and FastRandRF (Halko, Martinsson, Tropp 2011, Algorithm
+// 4.5), FP64.  Complex matrices are planar: m x l complex = real m x 2l
+// [Re | Im].  The plan needs l_max >= 2l.
+// srft_setup: D's diagonal (d_re, d_im, n each) and R's l coordinates r.
+int srft_setup(rsvd_plan_t P, int64_t n, int l, uint64_t seed, double* d_re, double* d_im, int* r);
+// Y (m x 2l planar, ldy) = A Omega: by explicit Omega and one real product.
+int srft_sketch_dense(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t lda, int l,
+                      const double* d_re, const double* d_im, const int* r, double* Y,
+                      int64_t ldy);
+int srft_sketch(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t lda, int l,
+                const double* d_re, const double* d_im, const int* r, double* Y, int64_t ldy);
+// Complex CholeskyQR2 of planar Y (rows x l complex) through real kernels;
+// Q (planar, ldq) may alias Y.
+int orth_complex(rsvd_plan_t P, const double* Y, int64_t rows, int l, int64_t ldy, double* Q,
+                 int64_t ldq);
+int range_srft(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t lda, int l,
+               uint64_t seed, double* Q, int64_t ldq);
+int sketch_srft(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t lda, int l,
+                uint64_t seed, double* Y, int64_t ldy);
+
 // Step entry: one tcgen05 pass with a BF16 operand X (ldx) of `l` columns.
 int mixed_apply(rsvd_plan_t P, const void* A, int64_t m, int64_t n, int64_t lda, const void* X,
                 int64_t ldx, int l, float* out, int64_t ldo, bool trans);

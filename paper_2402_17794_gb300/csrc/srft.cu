@@ -1,0 +1,219 @@
+// The subsampled random Fourier transform (SRFT) test matrix and the fast
+// randomized range finder built on it (the toolbox's SRFT and FastRandRF,
+// Section 4; Algorithm 4.5 of Halko, Martinsson and Tropp 2011), FP64.
+//
+//   Omega = sqrt(n/l) D F R   (n x l, complex)
+//     D  diagonal, d_j = exp(2 pi i u_j)  (u_j: Philox stream 2, counter j)
+//     F  the unitary DFT, f_pq = n^-1/2 exp(-2 pi i p q / n)
+//     R  l distinct coordinates r_0 < ... < r_{l-1} drawn by Floyd's algorithm
+//        (Bentley and Floyd 1987; Philox stream 3, counter = step)
+//   Y = A Omega,  Q = orth(Y)
+//
+// so Y(i, c) = l^-1/2 sum_j A(i, j) d_j exp(-2 pi i j r_c / n).
+//
+// Complex matrices are stored planar: an m x l complex matrix is the real
+// m x 2l matrix [Re | Im] (one leading dimension).  A is real, so the sketch
+// is one real product A [Re Omega | Im Omega] (dense form), or the two-level
+// FFT of srft_fft.cu.
+//
+// orth of a complex Y without complex kernels: the complex Cholesky factor
+// R of G = Y^H Y (real positive diagonal) realified in interleaved order --
+// each entry z as the 2 x 2 block [[Re z, -Im z], [Im z, Re z]] -- is real,
+// upper triangular with positive diagonal, and its normal product is the
+// realified G.  By uniqueness it IS the real Cholesky factor of the
+// realified G.  So each CholeskyQR pass is: the real Gram of [Re Y | Im Y]
+// (2l x 2l), G's realification, the real one-CTA Cholesky + inverse, and
+// [Re Q | Im Q] = [Re Y | Im Y] [[S_re, S_im], [-S_im, S_re]] with
+// S = R^-1 read from the even columns of the real inverse.
+#include <algorithm>
+#include <cmath>
+
+#include "omega_body.cuh"
+#include "pipeline.h"
+
+namespace rsvd {
+namespace {
+
+constexpr uint32_t kPhaseStream = 2;
+constexpr uint32_t kSampleStream = 3;
+
+// d_j = (cos 2 pi u_j, sin 2 pi u_j), j < n
+__global__ void srft_phase_kernel(int64_t n, uint32_t k0, uint32_t k1, double* __restrict__ d_re,
+                                  double* __restrict__ d_im) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t c0, c1, c2, c3;
+    omega::philox10((uint64_t)j, kPhaseStream, k0, k1, c0, c1, c2, c3);
+    const double u = omega::uniform52(c0, c1);
+    double s, c;
+    sincospi(2.0 * u, &s, &c);
+    d_re[j] = c;
+    d_im[j] = s;
+  }
+}
+
+// Floyd's sample of l distinct coordinates of [0, n), written ascending to r
+// (one warp): step s (j = n-l+s) draws t = min(floor(u_s (j+1)), j) and adds
+// t, or j when t is already in the set.
+__global__ void srft_sample_kernel(int64_t n, int l, uint32_t k0, uint32_t k1,
+                                   int* __restrict__ r) {
+  __shared__ int set[RSVD_L_MAX];
+  const int lane = threadIdx.x;
+  for (int s = 0; s < l; ++s) {
+    const int64_t j = n - l + s;
+    int t = 0;
+    if (lane == 0) {
+      uint32_t c0, c1, c2, c3;
+      omega::philox10((uint64_t)s, kSampleStream, k0, k1, c0, c1, c2, c3);
+      const double u = omega::uniform52(c0, c1);
+      const int64_t tt = (int64_t)floor(__dmul_rn(u, (double)(j + 1)));
+      t = (int)(tt < j ? tt : j);
+    }
+    t = __shfl_sync(0xffffffffu, t, 0);
+    bool found = false;
+    for (int k = lane; k < s; k += 32) found |= (set[k] == t);
+    found = __any_sync(0xffffffffu, found);
+    if (lane == 0) set[s] = found ? (int)j : t;
+    __syncwarp();
+  }
+  // ascending order: each value goes to its rank (values are distinct)
+  for (int a = lane; a < l; a += 32) {
+    int rank = 0;
+    for (int b = 0; b < l; ++b) rank += set[b] < set[a];
+    r[rank] = set[a];
+  }
+}
+
+// Dense Omega, planar: Om(:, c) = Re, Om(:, l + c) = Im of
+// l^-1/2 d_j exp(-2 pi i (j r_c mod n) / n).
+__global__ void srft_omega_kernel(int64_t n, int l, const double* __restrict__ d_re,
+                                  const double* __restrict__ d_im, const int* __restrict__ r,
+                                  double* __restrict__ Om, int64_t ldo) {
+  const double scale = rsqrt((double)l);
+  const int64_t total = n * (int64_t)l;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(t / n);
+    const int64_t j = t - (int64_t)c * n;
+    const int64_t q = (j * (int64_t)r[c]) % n;
+    double s, co;
+    sincospi(2.0 * (double)q / (double)n, &s, &co);   // F's entry is co - i s
+    const double fr = co, fi = -s;
+    Om[j + (int64_t)c * ldo] = scale * (d_re[j] * fr - d_im[j] * fi);
+    Om[j + (int64_t)(l + c) * ldo] = scale * (d_re[j] * fi + d_im[j] * fr);
+  }
+}
+
+// Realification of the complex Gram G = Y^H Y from the real Gram Gr of
+// [Re Y | Im Y] (2l x 2l, ld 2l): G_re = Gr11 + Gr22, G_im = Gr12 - Gr21,
+// written interleaved: out(2i+a, 2j+b) = [[G_re, -G_im], [G_im, G_re]](a, b).
+__global__ void realify_gram_kernel(const double* __restrict__ Gr, int l,
+                                    double* __restrict__ out) {
+  const int L = 2 * l;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < L * L; t += gridDim.x * blockDim.x) {
+    const int a = t % L, b = t / L;
+    const int i = a >> 1, j = b >> 1;
+    const double gre = Gr[i + j * L] + Gr[(l + i) + (l + j) * L];
+    const double gim = Gr[i + (l + j) * L] - Gr[(l + i) + j * L];
+    const int pa = a & 1, pb = b & 1;
+    out[t] = (pa == pb) ? gre : (pa ? gim : -gim);
+  }
+}
+
+// M (2l x 2l, ld 2l) = [[S_re, S_im], [-S_im, S_re]] with S = R^-1 read from
+// the even columns of the realified inverse Ri (ld 2l).
+__global__ void complex_coef_kernel(const double* __restrict__ Ri, int l, double* __restrict__ M) {
+  const int L = 2 * l;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < l * l; t += gridDim.x * blockDim.x) {
+    const int i = t % l, j = t / l;
+    const double sre = Ri[2 * i + (2 * j) * L];
+    const double sim = Ri[(2 * i + 1) + (2 * j) * L];
+    M[i + j * L] = sre;
+    M[i + (l + j) * L] = sim;
+    M[(l + i) + j * L] = -sim;
+    M[(l + i) + (l + j) * L] = sre;
+  }
+}
+
+}  // namespace
+
+int srft_setup(rsvd_plan_t P, int64_t n, int l, uint64_t seed, double* d_re, double* d_im,
+               int* r) {
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)P->num_sms * 4);
+  srft_phase_kernel<<<blocks, 256, 0, P->stream>>>(n, k0, k1, d_re, d_im);
+  note_launch();
+  RSVD_CK(cudaGetLastError());
+  srft_sample_kernel<<<1, 32, 0, P->stream>>>(n, l, k0, k1, r);
+  note_launch();
+  RSVD_CK(cudaGetLastError());
+  return RSVD_OK;
+}
+
+int srft_sketch_dense(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t lda, int l,
+                      const double* d_re, const double* d_im, const int* r, double* Y,
+                      int64_t ldy) {
+  Work<double> W = work_of<double>(P);
+  const int64_t total = n * (int64_t)l;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)P->num_sms * 8);
+  srft_omega_kernel<<<blocks, 256, 0, P->stream>>>(n, l, d_re, d_im, r, W.om, n);
+  note_launch();
+  RSVD_CK(cudaGetLastError());
+  return gemm<double>(P, A, lda, false, W.om, n, Y, ldy, m, n, 2 * l);
+}
+
+int srft_sketch(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t lda, int l,
+                const double* d_re, const double* d_im, const int* r, double* Y, int64_t ldy) {
+  return srft_sketch_dense(P, A, m, n, lda, l, d_re, d_im, r, Y, ldy);
+}
+
+int orth_complex(rsvd_plan_t P, const double* Y, int64_t rows, int l, int64_t ldy, double* Q,
+                 int64_t ldq) {
+  Work<double> W = work_of<double>(P);
+  DeviceStatus* st = dstatus(P);
+  const int L = 2 * l;
+  int rc;
+  const double* src = Y;
+  int64_t lds = ldy;
+  for (int pass = 0; pass < 2; ++pass) {
+    if ((rc = gram<double>(P, src, lds, rows, L, W.G))) return rc;
+    realify_gram_kernel<<<(L * L + 255) / 256, 256, 0, P->stream>>>(W.G, l, W.Mt);
+    note_launch();
+    RSVD_CK(cudaGetLastError());
+    RSVD_CK(launch_chol_inv<double>(W.Mt, L, L, W.R1, W.R1i, W.cholw, st, P->stream));
+    complex_coef_kernel<<<(l * l + 255) / 256, 256, 0, P->stream>>>(W.R1i, l, W.Um);
+    note_launch();
+    RSVD_CK(cudaGetLastError());
+    double* dst = pass == 0 ? W.tmp : Q;
+    const int64_t ldd = pass == 0 ? rows : ldq;
+    if ((rc = gemm<double>(P, src, lds, false, W.Um, L, dst, ldd, rows, L, L))) return rc;
+    src = dst;
+    lds = ldd;
+  }
+  return RSVD_OK;
+}
+
+int range_srft(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t lda, int l,
+               uint64_t seed, double* Q, int64_t ldq) {
+  Work<double> W = work_of<double>(P);
+  double* d_re = W.qb;
+  double* d_im = W.qb + n;
+  int* r = (int*)W.z;
+  int rc;
+  if ((rc = srft_setup(P, n, l, seed, d_re, d_im, r))) return rc;
+  if ((rc = srft_sketch(P, A, m, n, lda, l, d_re, d_im, r, W.y, m))) return rc;
+  return orth_complex(P, W.y, m, l, m, Q, ldq);
+}
+
+int sketch_srft(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t lda, int l,
+                uint64_t seed, double* Y, int64_t ldy) {
+  Work<double> W = work_of<double>(P);
+  double* d_re = W.qb;
+  double* d_im = W.qb + n;
+  int* r = (int*)W.z;
+  int rc;
+  if ((rc = srft_setup(P, n, l, seed, d_re, d_im, r))) return rc;
+  return srft_sketch(P, A, m, n, lda, l, d_re, d_im, r, Y, ldy);
+}
+
+}  // namespace rsvd

@@ -153,6 +153,14 @@ def rsvd_solve_adaptive(plan, A, m, n, lda, eps, r, l_cap, seed, U, ldu, S, VT, 
     return code, rank.value
 
 
+def rsvd_range_srft(plan, A, m, n, lda, l, seed, Q, ldq) -> int:
+    return _lib.load().rsvd_range_srft(plan, _ptr(A), m, n, lda, l, seed, _ptr(Q), ldq)
+
+
+def rsvd_srft_sketch(plan, A, m, n, lda, l, seed, Y, ldy) -> int:
+    return _lib.load().rsvd_srft_sketch(plan, _ptr(A), m, n, lda, l, seed, _ptr(Y), ldy)
+
+
 def rsvd_solve_singlepass(plan, A, m, n, lda, k, p, seed, U, ldu, S, VT, ldvt) -> int:
     return _lib.load().rsvd_solve_singlepass(plan, _ptr(A), m, n, lda, k, p, seed, _ptr(U), ldu,
                                              _ptr(S), _ptr(VT), ldvt)
@@ -332,6 +340,22 @@ class Plan:
         if code not in (0, ERR_NOT_REACHED):
             _check(code, "rsvd_solve_adaptive")
         return U[:rank], S[:rank], VT[:, :rank], code == 0
+
+    def range_srft(self, A, m, n, l, seed, lda=None):
+        """FastRandRF with the SRFT on a plain plan (l_max >= 2l): Q as a
+        column-major planar tensor (2l, m): rows 0..l-1 Re Q, l..2l-1 Im Q.
+        Enqueued only."""
+        lda = lda or A.shape[1]
+        Q = torch.empty(2 * l, m, dtype=torch.float64, device=A.device)
+        _check(rsvd_range_srft(self.handle, A, m, n, lda, l, seed, Q, m), "rsvd_range_srft")
+        return Q
+
+    def srft_sketch(self, A, m, n, l, seed, lda=None):
+        """Y = A Omega with the SRFT Omega, planar (2l, m).  Enqueued only."""
+        lda = lda or A.shape[1]
+        Y = torch.empty(2 * l, m, dtype=torch.float64, device=A.device)
+        _check(rsvd_srft_sketch(self.handle, A, m, n, lda, l, seed, Y, m), "rsvd_srft_sketch")
+        return Y
 
     def solve(self, A, m, n, k, p, q, seed, lda=None, out=None):
         """A: column-major device tensor (n, lda).  Returns (U, S, VT) as
