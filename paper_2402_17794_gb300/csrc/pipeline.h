@@ -107,6 +107,11 @@ int srft_setup(rsvd_plan_t P, int64_t n, int l, uint64_t seed, double* d_re, dou
 int srft_sketch_dense(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t lda, int l,
                       const double* d_re, const double* d_im, const int* r, double* Y,
                       int64_t ldy);
+// The same product through length-64 FFTs (n a multiple of 64); see srft_fft.cu.
+bool srft_fft_supported(int64_t n, int l);
+int srft_sketch_fft(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t lda, int l,
+                    const double* d_re, const double* d_im, const int* r, double* Y, int64_t ldy);
+// The FFT form when n allows it, else the dense form.
 int srft_sketch(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t lda, int l,
                 const double* d_re, const double* d_im, const int* r, double* Y, int64_t ldy);
 // Complex CholeskyQR2 of planar Y (rows x l complex) through real kernels;

@@ -164,6 +164,7 @@ int srft_sketch_dense(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int6
 
 int srft_sketch(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t lda, int l,
                 const double* d_re, const double* d_im, const int* r, double* Y, int64_t ldy) {
+  if (srft_fft_supported(n, l)) return srft_sketch_fft(P, A, m, n, lda, l, d_re, d_im, r, Y, ldy);
   return srft_sketch_dense(P, A, m, n, lda, l, d_re, d_im, r, Y, ldy);
 }
 
