@@ -663,6 +663,7 @@ def run_ours(args):
     singlepass = run_singlepass(args, world, dA, w, plan, 6)
     algorithm3 = run_singlepass(args, world, dA, w, plan, 3)
     adaptive = run_adaptive(args, world, dA, w)
+    srft = run_srft(args, world, dA, w, t_an)
 
     # --- the mixed-precision workload beside it ---
     mixed = mixed_fp8 = None
@@ -700,6 +701,7 @@ def run_ours(args):
         "singlepass": singlepass,
         "algorithm3": algorithm3,
         "adaptive": adaptive,
+        "srft": srft,
         "mixed": mixed,
         "mixed_fp8": mixed_fp8,
         "batched": batched,
@@ -758,6 +760,62 @@ def run_singlepass(args, world, dA, w, plan, algorithm=6):
             "value": round(steps * world / (ms / 1e3), 4), "unit": "solves/s",
             "ms_per_solve": round(ms / steps, 4),
             "passes_per_solve": 2 if algorithm == 6 else 2 * q + 2, "dtype": "f64"}
+
+
+def run_srft(args, world, dA, w, gaussian_pass_ms):
+    """FastRandRF (Halko et al. Algorithm 4.5) with the SRFT test matrix on
+    the plain workload's matrix, l = k + p: the sketch through length-64
+    FFTs (FP64 ALU-bound) and the complex CholeskyQR2 after it."""
+    import torch
+
+    from paper_2402_17794_gb300 import rsvd as R
+
+    m, n, k, p, seed = w["m"], w["n"], w["k"], w["p"], w["seed"]
+    l = k + p
+    plan = R.Plan(m, n, 2 * l)
+    Y = torch.empty(2 * l, m, dtype=torch.float64, device="cuda")
+    Q = torch.empty(2 * l, m, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, steps):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        _barrier(world)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return _max_over_ranks(e0.elapsed_time(e1), world) / steps
+
+    steps = max(args.steps, 10)
+    rng_ms = timed(lambda: R._check(R.rsvd_range_srft(plan.handle, dA, m, n, m, l, seed, Q, m),
+                                    "rsvd_range_srft"), steps)
+    sk_ms = timed(lambda: R._check(R.rsvd_srft_sketch(plan.handle, dA, m, n, m, l, seed, Y, m),
+                                   "rsvd_srft_sketch"), steps)
+    st = plan.status()
+    if st != 0:
+        raise RuntimeError(f"SRFT range finder failed: {R.rsvd_status_string(st)}")
+    del plan
+    # arithmetic of the FFT form per element of A: the phase (2), the 8 x 8
+    # length-64 DFT (16 eight-point DFTs of 56 flops + 64 twiddles of 6,
+    # per 64 elements: 20) and one complex multiply-add per sample per 64
+    # columns (8 l / 64)
+    flops = m * n * (2 + 20 + 8 * l / 64)
+    peaks, _ = _peaks()
+    fp64_peak = 152 * 2 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    return {"workload": "FastRandRF (Halko et al. Alg. 4.5) with the SRFT Omega = sqrt(n/l) D F R "
+                        "on " + w["desc"].split(";")[0] + f"; l={l}",
+            "value": round(steps * world / (rng_ms * steps / 1e3), 4), "unit": "ranges/s",
+            "ms_per_range": round(rng_ms, 4), "ms_sketch": round(sk_ms, 4),
+            "ms_gaussian_sketch_same_l": round(gaussian_pass_ms, 4),
+            "sketch_roofline": {"bound": "alu", "achieved": round(flops / (sk_ms / 1e3) / 1e12, 4),
+                                "peak": round(fp64_peak, 4), "unit": "TFLOP/s (FP64)",
+                                "frac": round(flops / (sk_ms / 1e3) / 1e12 / fp64_peak, 4)},
+            "dtype": "f64 (complex sample, planar)"}
 
 
 ADAPTIVE = dict(eps=0.25, r=10, l_cap=128)

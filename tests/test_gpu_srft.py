@@ -89,3 +89,22 @@ def test_srft_argument_errors():
     assert f(plan.handle, A, 100, 80, 100, 11, 0, Q, 100) == 4   # 2l > plan l_max
     assert f(plan.handle, A, 100, 80, 100, 10, 0, Q, 100) == 0
     assert plan.status() == 0
+
+
+def test_srft_config_full_size_fp64():
+    """The benchmark's FastRandRF: A 16384 x 8192 FP64, Haar factors,
+    sigma_i = i^-1.5, l = 80, through the FFT form of the sketch."""
+    m, n, l, seed = 16384, 8192, 80, 2
+    dA = syn.lowrank_matrix_torch(m, n, syn.spectrum("poly", n, alpha=1.5), seed=0)
+    A = np.asfortranarray(dA.cpu().numpy().T)
+    Om = srft.srft_matrix(n, l, seed)
+    Yo = A @ Om.real + 1j * (A @ Om.imag)
+    Qo = srft.gram_schmidt_phases(np.linalg.qr(Yo)[0], Yo)
+    plan = R.Plan(m, n, 2 * l)
+    Y = plan.srft_sketch(dA, m, n, l, seed)
+    Q = plan.range_srft(dA, m, n, l, seed)
+    assert plan.status() == 0
+    y, q = _complex(Y, l), _complex(Q, l)
+    assert np.abs(y - Yo).max() <= 1e-12 * np.abs(Yo).max()
+    assert np.abs(q.conj().T @ q - np.eye(l)).max() <= 1e-12
+    assert np.abs(q - Qo).max() <= 1e-9, np.abs(q - Qo).max()
