@@ -84,6 +84,55 @@ __device__ __forceinline__ void dft8(double (&xr)[8], double (&xi)[8]) {
   }
 }
 
+// dft8 of x_a = v_a (cr_a + i ci_a) for real v: the phase products are
+// folded into the first butterflies (x_a +- x_{a+4} by one multiply and two
+// fused multiply-adds per component).
+__device__ __forceinline__ void dft8_phased(const double (&v)[8], const double (&cr)[8],
+                                            const double (&ci)[8], double (&xr)[8],
+                                            double (&xi)[8]) {
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const double pr = v[a] * cr[a], pi = v[a] * ci[a];
+    xr[a] = fma(v[a + 4], cr[a + 4], pr);
+    xi[a] = fma(v[a + 4], ci[a + 4], pi);
+    xr[a + 4] = fma(-v[a + 4], cr[a + 4], pr);
+    xi[a + 4] = fma(-v[a + 4], ci[a + 4], pi);
+  }
+  const double h = 0.70710678118654752440;
+  double ar[4], ai[4], br[4], bi[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    ar[a] = xr[a];
+    ai[a] = xi[a];
+    br[a] = xr[a + 4];
+    bi[a] = xi[a + 4];
+  }
+  {
+    const double t = br[1];
+    br[1] = h * (t + bi[1]);
+    bi[1] = h * (bi[1] - t);
+  }
+  {
+    const double t = br[2];
+    br[2] = bi[2];
+    bi[2] = -t;
+  }
+  {
+    const double t = br[3];
+    br[3] = h * (bi[3] - t);
+    bi[3] = -h * (t + bi[3]);
+  }
+  dft4(ar[0], ai[0], ar[1], ai[1], ar[2], ai[2], ar[3], ai[3]);
+  dft4(br[0], bi[0], br[1], bi[1], br[2], bi[2], br[3], bi[3]);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    xr[2 * k] = ar[k];
+    xi[2 * k] = ai[k];
+    xr[2 * k + 1] = br[k];
+    xi[2 * k + 1] = bi[k];
+  }
+}
+
 __device__ __forceinline__ double pick8(const double (&v)[8], int k) {
   double x = v[0];
 #pragma unroll
@@ -161,22 +210,25 @@ srft_fft_kernel(const double* __restrict__ A, int64_t lda, int64_t m, int64_t n,
   if (j2_begin < j2_end) load(j2_begin);
   const int my_cnt = cnt[w];
   for (int64_t j2 = j2_begin; j2 < j2_end; ++j2) {
-    double xr[8], xi[8];
+    double xr[8], xi[8], v[8], dr[8], di[8];
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
       const int64_t j = n2 * (8 * a + w) + j2;
-      const double dr = __ldg(d_re + j), di = __ldg(d_im + j);
-      xr[a] = nr[a] * dr;
-      xi[a] = nr[a] * di;
+      dr[a] = __ldg(d_re + j);
+      di[a] = __ldg(d_im + j);
+      v[a] = nr[a];
     }
     if (j2 + 1 < j2_end) load(j2 + 1);
-    // pass 1: DFT over a, twiddle exp(-2 pi i w k1 / 64), transpose
-    dft8(xr, xi);
+    // pass 1: DFT over a of A d, twiddle exp(-2 pi i w k1 / 64) (1 at
+    // k1 = 0), transpose
+    dft8_phased(v, dr, di, xr, xi);
+    s_re[w * kRows + lane] = xr[0];
+    s_im[w * kRows + lane] = xi[0];
 #pragma unroll
-    for (int k1 = 0; k1 < 8; ++k1) {
+    for (int k1 = 1; k1 < 8; ++k1) {
       const double cr = w64_re[w * k1], ci = w64_im[w * k1];
-      const double ur = xr[k1] * cr - xi[k1] * ci;
-      const double ui = xr[k1] * ci + xi[k1] * cr;
+      const double ur = fma(xr[k1], cr, -xi[k1] * ci);
+      const double ui = fma(xr[k1], ci, xi[k1] * cr);
       s_re[(k1 * 8 + w) * kRows + lane] = ur;
       s_im[(k1 * 8 + w) * kRows + lane] = ui;
     }
@@ -261,16 +313,37 @@ int srft_sketch_fft(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_
     note_launch();
     RSVD_CK(cudaGetLastError());
   }
-  // split the j2 range when the row tiles alone do not fill the GPU
+  // Split the j2 range so that the CTAs fill whole waves: the split with
+  // the best fraction of busy CTA slots (ties to fewer splits), since every
+  // CTA does the same work.
   const int64_t row_tiles = (m + kRows - 1) / kRows;
   const size_t slice = (size_t)m * 2 * l;
-  int64_t splits = std::max<int64_t>(1, ((int64_t)P->num_sms * 2 + row_tiles - 1) / row_tiles);
-  splits = std::min<int64_t>(splits, std::min<int64_t>(n2, 16));
-  splits = std::min<int64_t>(splits, (int64_t)(W.part_elems / slice));
-  if (splits < 1) splits = 1;
+  const size_t smem = fft_smem_bytes(l);
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, srft_fft_kernel, kThreads, smem) !=
+          cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  const int64_t slots = (int64_t)P->num_sms * per_sm;
+  const int64_t max_splits =
+      std::max<int64_t>(1, std::min<int64_t>({n2, 16, (int64_t)(W.part_elems / slice)}));
+  int64_t splits = 1;
+  double best = 0.0;
+  for (int64_t s = 1; s <= max_splits; ++s) {
+    const int64_t per_s = (n2 + s - 1) / s;
+    const int64_t eff_s = (n2 + per_s - 1) / per_s;
+    const int64_t ctas = row_tiles * eff_s;
+    const int64_t waves = (ctas + slots - 1) / slots;
+    // busy fraction, discounted by the work imbalance of uneven j2 ranges
+    const double fill = (double)ctas / (double)(waves * slots) * (double)n2 /
+                        (double)(per_s * eff_s);
+    if (fill > best + 0.02) {
+      best = fill;
+      splits = eff_s;
+    }
+  }
   const int64_t per = (n2 + splits - 1) / splits;
   splits = (n2 + per - 1) / per;
-  const size_t smem = fft_smem_bytes(l);
   dim3 grid((unsigned)row_tiles, (unsigned)splits);
   const double scale = 1.0 / std::sqrt((double)l);
   if (splits == 1) {
