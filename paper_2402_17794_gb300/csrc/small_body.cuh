@@ -272,6 +272,341 @@ __device__ __forceinline__ void chol_inv_blocked(const T* __restrict__ G, int64_
   if (tid == 0 && s_def) atomicAdd(&status->deficient, s_def);
 }
 
+// Panel variant: the Cholesky factor and its inverse as separate blocked
+// computations, every pass between barriers a small dense product in 4 x 4
+// register tiles (about 25 barriers at l = 160, against one per pivot).
+// Sizes are padded to lp = 32 ceil(l / 32) with zeros.  W (lp x ld, ld a
+// multiple of 4 with ld / 4 odd, so 16-byte accesses down a column or along
+// a stride-ld row are conflict-free) holds R in its upper triangle and
+// X = R^-1 transposed in its strict lower triangle (X[i][c] at W[c][i]);
+// X's diagonal is s_rs.  S (32 x ldt) holds a panel's rows with the column
+// index contiguous; Xs / Xt (32 x 36) a diagonal block of X and its
+// transpose.  Per panel P = [p0, p0 + 32):
+//  a. one warp eliminates [G_PP | I] (chol_block_factor); scaling its result
+//     gives R_PP = D^1/2 L^T and X_PP = L^-T D^-1/2;
+//  b. R[P][t] = X_PP^T G[P][t] for the later columns t (the panel's rows of R);
+//  c. G[t1][t2] -= sum_{k in P} R[k][t1] R[k][t2] for later t1 <= t2.
+// Then, panel rows from the last but one up:
+//  d. T[i][c] = sum_{p1 <= s <= c} R[p0 + i][s] X[s][c]   (c >= p1 = p0 + 32),
+//  e. X[p0 + i][c] = -sum_{k >= i} X_PP[i][k] T[k][c].
+// A dropped pivot (D_j <= tol) gives a zero row of R and a zero row and
+// column of X, as in the other variants.
+__host__ __device__ constexpr int chol_pad(int l) { return (l + 31) / 32 * 32; }
+__host__ __device__ constexpr int chol_tld(int l) {
+  return (chol_pad(l) / 4) % 2 ? chol_pad(l) : chol_pad(l) + 4;
+}
+__host__ __device__ constexpr size_t chol_panel_elems(int l) {
+  return (size_t)chol_pad(l) * chol_tld(l) + 2 * 32 * (size_t)chol_tld(l) + 2 * 32 * 36;
+}
+
+
+
+template <typename T>
+__device__ __forceinline__ void ld4(const T* p, T (&v)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 x = *reinterpret_cast<const float4*>(p);
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+  } else {
+    const double2 x = *reinterpret_cast<const double2*>(p);
+    const double2 y = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
+  }
+}
+template <typename T>
+__device__ __forceinline__ void st4(T* p, const T (&v)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+    *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
+  }
+}
+
+// Step a of the panel variant, one warp: the same elimination of
+// [G_PP | I] as chol_block_factor, with lane t holding ROW t of the block.
+// At pivot j lane j writes its row to shared memory and every lane reads the
+// whole row back with 16-byte loads, all issued before the first use (the
+// shuffle-per-value exchange of chol_block_factor waits on each value in
+// turn); then each lane updates its own row.  buf: 32 elements of 16-byte
+// aligned shared memory for this warp.
+template <typename T>
+__device__ __forceinline__ void chol_block_rows(T* W, int ld, int p0, int nb, T tol, T* s_invd,
+                                                T* s_rs, T* s_sq, int* s_def, T* buf) {
+  const int t = threadIdx.x & 31;
+  T w[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) w[c] = (t < nb && c < nb) ? W[p0 + t + (p0 + c) * ld] : T(0);
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    if (j < nb) {
+      if (t == j) {
+#pragma unroll
+        for (int c = 0; c < 32; c += 4) {
+          const T v[4] = {w[c], w[c + 1], w[c + 2], w[c + 3]};
+          st4(buf + c, v);
+        }
+      }
+      __syncwarp();
+      asm volatile("" ::: "memory");   // every lane reloads the new pivot row
+      T row[32];
+      const T gt = buf[t];   // G[t][j]: the pivot row's value at column t
+#pragma unroll
+      for (int c = 0; c < 32; c += 4) {
+        T v[4];
+        ld4(buf + c, v);
+        row[c] = v[0];
+        row[c + 1] = v[1];
+        row[c + 2] = v[2];
+        row[c + 3] = v[3];
+      }
+      const T d = row[j];
+      T invd = T(0), rs = T(0), sq = T(0);
+      const bool keep = d > tol;
+      if (keep) pivot_scales(d, invd, rs, sq);
+      if (t == j) {
+        s_invd[p0 + j] = invd;
+        s_rs[p0 + j] = rs;
+        s_sq[p0 + j] = sq;
+        if (!keep) atomicAdd(s_def, 1);
+      }
+      if (t > j && t < nb) {
+        const T f = gt * invd;
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          if (c < j) w[c] = fma(-f, row[c], w[c]);          // L^-1 part of row t
+          else if (c == j) w[c] = -f;                       // I part starts at column j
+          else w[c] = (c >= t) ? fma(-f, row[c], w[c]) : w[c];   // Schur complement
+        }
+      }
+      __syncwarp();
+      asm volatile("" ::: "memory");
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 32; ++c)
+    if (t < nb && c < nb) W[p0 + t + (p0 + c) * ld] = w[c];
+}
+
+template <typename T>
+__device__ __forceinline__ void chol_inv_panels(const T* __restrict__ G, int64_t ldg, int l,
+                                                T* __restrict__ R, T* __restrict__ Rinv,
+                                                T* __restrict__ W, DeviceStatus* status) {
+  __shared__ T s_invd[RSVD_L_MAX + 32], s_rs[RSVD_L_MAX + 32], s_sq[RSVD_L_MAX + 32];
+  __shared__ __align__(16) T s_buf[32];
+  __shared__ int s_def;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lp = chol_pad(l), ld = chol_tld(l), ldt = ld;
+  T* S = W + (size_t)lp * ld;   // 32 x ldt
+  T* Xs = S + 32 * ldt;         // Xs[k * 36 + i] = X_PP[k][i]
+  T* Xt = Xs + 32 * 36;         // Xt[k * 36 + i] = X_PP[i][k]
+  T tol;
+  const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
+  for (int c = warp; c < lp; c += nwarps) {   // one column per warp, coalesced
+#pragma unroll 4
+    for (int i = lane; i < lp; i += 32)
+      W[i + c * ld] = (i <= c && c < l) ? G[i + (int64_t)c * ldg] : T(0);
+  }
+  for (int t = tid; t < lp; t += nt) {
+    s_invd[t] = T(0);
+    s_rs[t] = T(0);
+    s_sq[t] = T(0);
+  }
+  if (tid == 0) s_def = 0;
+  if (!chol_prologue<T>(G, ldg, l, R, Rinv, status, &tol)) return;
+
+  // X_PP of the panel at p0 into Xs (k-major) and Xt (transposed)
+  auto build_x = [&](int p0) {
+    for (int e = tid; e < 32 * 32; e += nt) {
+      const int k = e >> 5, i = e & 31;
+      T v = T(0);
+      if (k < i) v = W[p0 + i + (p0 + k) * ld];
+      else if (k == i) v = s_rs[p0 + i];
+      Xs[k * 36 + i] = v;   // X_PP[k][i]
+      Xt[i * 36 + k] = v;   // Xt[i][k] = X_PP[k][i]
+    }
+  };
+
+  for (int p0 = 0; p0 < l; p0 += 32) {
+    const int nb = min(32, l - p0), p1 = p0 + 32, nt2 = lp - p1;
+    // a. the diagonal block
+    if (tid < 32) chol_block_rows<T>(W, ld, p0, nb, tol, s_invd, s_rs, s_sq, &s_def, s_buf);
+    __syncthreads();
+    for (int e = tid; e < nb * nb; e += nt) {
+      const int i = e % nb, c = e / nb;
+      const int gi = p0 + i, gc = p0 + c;
+      if (i != c) W[gi + gc * ld] *= s_rs[gi];   // R_PP above, X_PP^T below
+      else W[gi + gc * ld] = s_sq[gi];
+    }
+    __syncthreads();
+    if (nt2 <= 0) break;
+    build_x(p0);
+    for (int e = tid; e < 32 * nt2; e += nt) {     // G[P][t] with t contiguous
+      const int k = e % 32, t = e / 32;
+      S[k * ldt + t] = W[p0 + k + (p1 + t) * ld];
+    }
+    __syncthreads();
+    // b. R[P][t] = X_PP^T G[P][t]: tiles (4 rows i, 4 columns t); at most
+    //    8 (lp - 32) / 4 <= 2 lp <= 384 tiles, one per thread
+    {
+      const int ttiles = nt2 / 4, ntile = 8 * ttiles;
+      T acc[4][4] = {};
+      const int i0 = (tid / ttiles) * 4, t0 = (tid % ttiles) * 4;
+      if (tid < ntile) {
+        for (int k = 0; k < i0 + 4; ++k) {
+          T x[4], g[4];
+          ld4(Xs + k * 36 + i0, x);
+          ld4(S + k * ldt + t0, g);
+#pragma unroll
+          for (int a2 = 0; a2 < 4; ++a2)
+#pragma unroll
+            for (int b2 = 0; b2 < 4; ++b2) acc[a2][b2] = fma(x[a2], g[b2], acc[a2][b2]);
+        }
+      }
+      __syncthreads();
+      if (tid < ntile) {
+#pragma unroll
+        for (int a2 = 0; a2 < 4; ++a2) st4(S + (i0 + a2) * ldt + t0, acc[a2]);
+#pragma unroll
+        for (int b2 = 0; b2 < 4; ++b2) {
+          T col[4] = {acc[0][b2], acc[1][b2], acc[2][b2], acc[3][b2]};
+          st4(W + p0 + i0 + (p1 + t0 + b2) * ld, col);
+        }
+      }
+      __syncthreads();
+    }
+    // c. trailing upper triangle, tiles (u <= v) of 4 x 4
+    {
+      const int nt4 = nt2 / 4, ntile = nt4 * (nt4 + 1) / 2;
+      for (int tile = tid; tile < ntile; tile += nt) {
+        int u = 0, rem = tile;   // row u of the tile triangle holds nt4 - u tiles
+        while (rem >= nt4 - u) {
+          rem -= nt4 - u;
+          ++u;
+        }
+        const int v = u + rem;
+        const int t1 = u * 4, t2 = v * 4;
+        T acc[4][4];
+#pragma unroll
+        for (int b2 = 0; b2 < 4; ++b2) {
+          T col[4];
+          ld4(W + p1 + t1 + (p1 + t2 + b2) * ld, col);
+#pragma unroll
+          for (int a2 = 0; a2 < 4; ++a2) acc[a2][b2] = col[a2];
+        }
+        for (int k = 0; k < nb; ++k) {
+          T r1[4], r2[4];
+          ld4(S + k * ldt + t1, r1);
+          ld4(S + k * ldt + t2, r2);
+#pragma unroll
+          for (int a2 = 0; a2 < 4; ++a2)
+#pragma unroll
+            for (int b2 = 0; b2 < 4; ++b2) acc[a2][b2] = fma(-r1[a2], r2[b2], acc[a2][b2]);
+        }
+#pragma unroll
+        for (int b2 = 0; b2 < 4; ++b2) {
+          if (u == v) {   // diagonal tile: the upper part only (W's lower part holds X)
+#pragma unroll
+            for (int a2 = 0; a2 < 4; ++a2)
+              if (a2 <= b2) W[p1 + t1 + a2 + (p1 + t2 + b2) * ld] = acc[a2][b2];
+          } else {
+            T col[4] = {acc[0][b2], acc[1][b2], acc[2][b2], acc[3][b2]};
+            st4(W + p1 + t1 + (p1 + t2 + b2) * ld, col);
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // d, e: X's off-diagonal blocks, last panel row first.  Step d's sums run
+  // in two halves over s (threads tid and tid + 256 of a tile) into S and
+  // S2, which step e adds.
+  T* S2 = Xt + 32 * 36;   // 32 x ldt
+  for (int p0 = lp - 64; p0 >= 0; p0 -= 32) {
+    const int p1 = p0 + 32, nt2 = lp - p1, ctiles = nt2 / 4, ntile = 8 * ctiles;
+    build_x(p0);
+    // d. T[i][c] = sum_{p1 <= s <= c} R[p0 + i][s] X[s][c]  -> S + S2 (i-major)
+    for (int tt = tid; tt < 2 * ntile; tt += nt) {
+      const int tile = tt % ntile, half = tt / ntile;
+      const int i0 = (tile / ctiles) * 4, c0 = p1 + (tile % ctiles) * 4;
+      const int smid = p1 + ((c0 - p1) / 8) * 4;   // the first half's end (a multiple of 4)
+      T acc[4][4] = {};
+      const int sb = half ? smid : p1, se = half ? c0 : smid;
+      for (int s2 = sb; s2 < se; ++s2) {
+        T r[4], x[4];
+        ld4(W + p0 + i0 + s2 * ld, r);   // R[p0 + i0 + a][s2]
+        ld4(W + c0 + s2 * ld, x);        // X[s2][c0 + b]
+#pragma unroll
+        for (int a2 = 0; a2 < 4; ++a2)
+#pragma unroll
+          for (int b2 = 0; b2 < 4; ++b2) acc[a2][b2] = fma(r[a2], x[b2], acc[a2][b2]);
+      }
+      if (half) {
+#pragma unroll
+        for (int d2 = 0; d2 < 4; ++d2) {   // s2 = c0 + d2: X[s2][c0 + b] for b >= d2
+          const int s2 = c0 + d2;
+          T r[4];
+          ld4(W + p0 + i0 + s2 * ld, r);
+#pragma unroll
+          for (int b2 = 0; b2 < 4; ++b2) {
+            const T x = (b2 == d2) ? s_rs[s2] : (b2 > d2 ? W[c0 + b2 + s2 * ld] : T(0));
+#pragma unroll
+            for (int a2 = 0; a2 < 4; ++a2) acc[a2][b2] = fma(r[a2], x, acc[a2][b2]);
+          }
+        }
+      }
+      T* dst = half ? S2 : S;
+#pragma unroll
+      for (int a2 = 0; a2 < 4; ++a2) st4(dst + (i0 + a2) * ldt + (c0 - p1), acc[a2]);
+    }
+    __syncthreads();
+    // e. X[p0 + i][c] = -sum_k X_PP[i][k] T[k][c]
+    for (int tile = tid; tile < ntile; tile += nt) {
+      const int i0 = (tile / ctiles) * 4, c0 = p1 + (tile % ctiles) * 4;
+      T acc[4][4] = {};
+      for (int k = i0; k < 32; ++k) {
+        T x[4], t4[4], u4[4];
+        ld4(Xt + k * 36 + i0, x);   // X_PP[i0 + a][k]
+        ld4(S + k * ldt + (c0 - p1), t4);
+        ld4(S2 + k * ldt + (c0 - p1), u4);
+#pragma unroll
+        for (int b2 = 0; b2 < 4; ++b2) t4[b2] += u4[b2];
+#pragma unroll
+        for (int a2 = 0; a2 < 4; ++a2)
+#pragma unroll
+          for (int b2 = 0; b2 < 4; ++b2) acc[a2][b2] = fma(x[a2], t4[b2], acc[a2][b2]);
+      }
+#pragma unroll
+      for (int a2 = 0; a2 < 4; ++a2) {
+        T v[4] = {-acc[a2][0], -acc[a2][1], -acc[a2][2], -acc[a2][3]};
+        st4(W + c0 + (p0 + i0 + a2) * ld, v);
+      }
+    }
+    __syncthreads();
+  }
+  for (int c = warp; c < l; c += nwarps) {
+#pragma unroll 4
+    for (int i = lane; i < l; i += 32) {
+      T r = T(0), ri = T(0);
+      if (i == c) {
+        r = W[i + i * ld];
+        ri = s_rs[i];
+      } else if (i < c) {
+        r = W[i + c * ld];
+        ri = W[c + i * ld];
+      }
+      R[i + (int64_t)c * l] = r;
+      Rinv[i + (int64_t)c * l] = ri;
+    }
+  }
+  if (tid == 0 && s_def) atomicAdd(&status->deficient, s_def);
+}
+
+// Whether the panel variant covers (T, l) in shared memory.
+template <typename T>
+__host__ __device__ constexpr bool chol_panels_fit(int l) {
+  return chol_panel_elems(l) * sizeof(T) <= 200 * 1024;
+}
+
 // Threads of a blocked-Cholesky CTA (NB * (l - NB) <= 16 * CHOL_THREADS for l <= 288).
 constexpr int CHOL_THREADS = 512;
 

@@ -66,6 +66,14 @@ chol_inv_kernel(const T* __restrict__ G, int64_t ldg, int l, T* __restrict__ R,
   chol_inv_blocked<T, CholPanel<T>::value>(G, ldg, l, R, Rinv, W, status);
 }
 
+template <typename T>
+__global__ void __launch_bounds__(CHOL_THREADS)
+chol_inv_panels_kernel(const T* __restrict__ G, int64_t ldg, int l, T* __restrict__ R,
+                       T* __restrict__ Rinv, DeviceStatus* status) {
+  extern __shared__ __align__(16) unsigned char cpan_raw[];
+  chol_inv_panels<T>(G, ldg, l, R, Rinv, reinterpret_cast<T*>(cpan_raw), status);
+}
+
 template <int E>
 __global__ void __launch_bounds__(CHOL_REG_THREADS)
 chol_inv_regs_kernel(const float* __restrict__ G, int64_t ldg, int l, float* __restrict__ R,
@@ -123,7 +131,13 @@ template <typename T>
 cudaError_t launch_chol_inv(const T* G, int64_t ldg, int l, T* R, T* Rinv, T* work,
                             DeviceStatus* status, cudaStream_t st) {
   const size_t smem = chol_work_elems(l) * sizeof(T);
-  if (chol_in_regs<T>(l)) {
+  const size_t pan = chol_panel_elems(l) * sizeof(T);
+  // FP32: the panel variant (its one-warp pivot blocks run at the FP32 rate;
+  // in FP64 the blocked variant's narrower panels are faster)
+  if (sizeof(T) == 4 && chol_panels_fit<T>(l) &&
+      pan <= dynamic_smem_cap((const void*)chol_inv_panels_kernel<T>)) {
+    chol_inv_panels_kernel<T><<<1, CHOL_THREADS, pan, st>>>(G, ldg, l, R, Rinv, status);
+  } else if (chol_in_regs<T>(l)) {
     const float* g = (const float*)G;
     float *r = (float*)R, *ri = (float*)Rinv;
     constexpr int nt = CHOL_REG_THREADS;
