@@ -323,12 +323,13 @@ __device__ __forceinline__ void st4(T* p, const T (&v)[4]) {
 }
 
 // Step a of the panel variant, one warp: the same elimination of
-// [G_PP | I] as chol_block_factor, with lane t holding ROW t of the block.
-// At pivot j lane j writes its row to shared memory and every lane reads the
-// whole row back with 16-byte loads, all issued before the first use (the
-// shuffle-per-value exchange of chol_block_factor waits on each value in
-// turn); then each lane updates its own row.  buf: 32 elements of 16-byte
-// aligned shared memory for this warp.
+// [G_PP | I] as chol_block_factor, with lane t holding ROW t of the block,
+// two pivots per round.  Lanes j and j+1 write their rows to shared memory;
+// every lane reads both back (16-byte loads, all issued before the first
+// use), forms row j+1 after pivot j itself (the same operations lane j+1
+// would do, so every lane has the same bits), and applies both pivots to
+// its own row: one shared-memory round trip per two pivots.  buf: 64
+// elements of 16-byte aligned shared memory.
 template <typename T>
 __device__ __forceinline__ void chol_block_rows(T* W, int ld, int p0, int nb, T tol, T* s_invd,
                                                 T* s_rs, T* s_sq, int* s_def, T* buf) {
@@ -337,45 +338,69 @@ __device__ __forceinline__ void chol_block_rows(T* W, int ld, int p0, int nb, T 
 #pragma unroll
   for (int c = 0; c < 32; ++c) w[c] = (t < nb && c < nb) ? W[p0 + t + (p0 + c) * ld] : T(0);
 #pragma unroll
-  for (int j = 0; j < 32; ++j) {
+  for (int j = 0; j < 32; j += 2) {
     if (j < nb) {
-      if (t == j) {
+      const bool pair = j + 1 < nb;
+      if (t == j || t == j + 1) {
+        T* dst = buf + (t == j ? 0 : 32);
 #pragma unroll
         for (int c = 0; c < 32; c += 4) {
           const T v[4] = {w[c], w[c + 1], w[c + 2], w[c + 3]};
-          st4(buf + c, v);
+          st4(dst + c, v);
         }
       }
       __syncwarp();
-      asm volatile("" ::: "memory");   // every lane reloads the new pivot row
-      T row[32];
-      const T gt = buf[t];   // G[t][j]: the pivot row's value at column t
+      asm volatile("" ::: "memory");   // every lane reloads the new pivot rows
+      const T ga = buf[t], gb = buf[32 + t];
+      T ra[32], rb[32];
 #pragma unroll
       for (int c = 0; c < 32; c += 4) {
-        T v[4];
+        T v[4], u[4];
         ld4(buf + c, v);
-        row[c] = v[0];
-        row[c + 1] = v[1];
-        row[c + 2] = v[2];
-        row[c + 3] = v[3];
+        ld4(buf + 32 + c, u);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          ra[c + e] = v[e];
+          rb[c + e] = u[e];
+        }
       }
-      const T d = row[j];
-      T invd = T(0), rs = T(0), sq = T(0);
-      const bool keep = d > tol;
-      if (keep) pivot_scales(d, invd, rs, sq);
+      // pivot j
+      const T d0 = buf[j];
+      T invd0 = T(0), rs0 = T(0), sq0 = T(0);
+      const bool keep0 = d0 > tol;
+      if (keep0) pivot_scales(d0, invd0, rs0, sq0);
+      // row j+1 after pivot j, then pivot j+1
+      const T a1 = buf[j + 1];
+      const T mlt = a1 * invd0;
+#pragma unroll
+      for (int c = 0; c < 32; ++c) rb[c] = (c == j) ? -mlt : fma(-mlt, ra[c], rb[c]);
+      const T d1 = fma(-mlt, a1, buf[32 + j + 1]);
+      T invd1 = T(0), rs1 = T(0), sq1 = T(0);
+      const bool keep1 = pair && d1 > tol;
+      if (keep1) pivot_scales(d1, invd1, rs1, sq1);
       if (t == j) {
-        s_invd[p0 + j] = invd;
-        s_rs[p0 + j] = rs;
-        s_sq[p0 + j] = sq;
-        if (!keep) atomicAdd(s_def, 1);
+        s_invd[p0 + j] = invd0;
+        s_rs[p0 + j] = rs0;
+        s_sq[p0 + j] = sq0;
+        if (!keep0) atomicAdd(s_def, 1);
       }
-      if (t > j && t < nb) {
-        const T f = gt * invd;
+      if (t == j + 1 && pair) {
+        s_invd[p0 + j + 1] = invd1;
+        s_rs[p0 + j + 1] = rs1;
+        s_sq[p0 + j + 1] = sq1;
+        if (!keep1) atomicAdd(s_def, 1);
+#pragma unroll
+        for (int c = 0; c < 32; ++c) w[c] = rb[c];
+      }
+      if (t > j + 1 && t < nb) {
+        const T f0 = ga * invd0;
+        const T f1 = fma(-mlt, ga, gb) * invd1;   // G[t][j+1] after pivot j, / D_{j+1}
 #pragma unroll
         for (int c = 0; c < 32; ++c) {
-          if (c < j) w[c] = fma(-f, row[c], w[c]);          // L^-1 part of row t
-          else if (c == j) w[c] = -f;                       // I part starts at column j
-          else w[c] = (c >= t) ? fma(-f, row[c], w[c]) : w[c];   // Schur complement
+          if (c < j) w[c] = fma(-f1, rb[c], fma(-f0, ra[c], w[c]));   // L^-1 part
+          else if (c == j) w[c] = fma(f1, mlt, -f0);
+          else if (c == j + 1) w[c] = -f1;
+          else w[c] = (c >= t) ? fma(-f1, rb[c], fma(-f0, ra[c], w[c])) : w[c];
         }
       }
       __syncwarp();
@@ -392,7 +417,7 @@ __device__ __forceinline__ void chol_inv_panels(const T* __restrict__ G, int64_t
                                                 T* __restrict__ R, T* __restrict__ Rinv,
                                                 T* __restrict__ W, DeviceStatus* status) {
   __shared__ T s_invd[RSVD_L_MAX + 32], s_rs[RSVD_L_MAX + 32], s_sq[RSVD_L_MAX + 32];
-  __shared__ __align__(16) T s_buf[32];
+  __shared__ __align__(16) T s_buf[64];
   __shared__ int s_def;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lp = chol_pad(l), ld = chol_tld(l), ldt = ld;

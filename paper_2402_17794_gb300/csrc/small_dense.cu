@@ -134,9 +134,14 @@ cudaError_t launch_chol_inv(const T* G, int64_t ldg, int l, T* R, T* Rinv, T* wo
   const size_t pan = chol_panel_elems(l) * sizeof(T);
   // FP32: the panel variant (its one-warp pivot blocks run at the FP32 rate;
   // in FP64 the blocked variant's narrower panels are faster)
-  if (sizeof(T) == 4 && chol_panels_fit<T>(l) &&
-      pan <= dynamic_smem_cap((const void*)chol_inv_panels_kernel<T>)) {
-    chol_inv_panels_kernel<T><<<1, CHOL_THREADS, pan, st>>>(G, ldg, l, R, Rinv, status);
+  bool done = false;
+  if constexpr (sizeof(T) == 4) {
+    if (chol_panels_fit<T>(l) && pan <= dynamic_smem_cap((const void*)chol_inv_panels_kernel<T>)) {
+      chol_inv_panels_kernel<T><<<1, CHOL_THREADS, pan, st>>>(G, ldg, l, R, Rinv, status);
+      done = true;
+    }
+  }
+  if (done) {
   } else if (chol_in_regs<T>(l)) {
     const float* g = (const float*)G;
     float *r = (float*)R, *ri = (float*)Rinv;
