@@ -241,6 +241,18 @@ template int orth<double>(rsvd_plan_t, const double*, int64_t, int, int64_t, dou
 template int orth<float>(rsvd_plan_t, const float*, int64_t, int, int64_t, float*, int64_t, float*,
                          bool);
 
+// One CholeskyQR pass: Q = Y R^-1 with R the Cholesky factor of Y^T Y.  Q
+// spans range(Y) exactly; its columns are orthonormal to about u kappa(Y)^2.
+template <typename T>
+int orth1(rsvd_plan_t P, const T* Y, int64_t rows, int l, int64_t ldy, T* Q, int64_t ldq) {
+  Work<T> W = work_of<T>(P);
+  int rc;
+  if ((rc = gram<T>(P, Y, ldy, rows, l, W.G))) return rc;
+  RSVD_CK(launch_chol_inv<T>(W.G, l, l, W.R1, W.R1i, W.cholw, dstatus(P), P->stream));
+  return gemm<T>(P, Y, ldy, false, W.R1i, l, Q, ldq, rows, l, l, true);
+}
+template int orth1<float>(rsvd_plan_t, const float*, int64_t, int, int64_t, float*, int64_t);
+
 // Shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa, Yamamoto, Yanagisawa,
 // SIAM J. Sci. Comput. 2020): one Cholesky QR of Y with the Gram shifted by
 // s = 11 (rows l + l (l+1)) u ||Y||_F^2, which keeps the factorisation defined
@@ -341,16 +353,24 @@ int solve_mixed(rsvd_plan_t P, const void* A, int64_t m, int64_t n, int64_t lda,
   Work<float> W = work_of<float>(P);
   int rc;
   // 1. Omega (FP32, rounded to BF16 for the pass);  2. Y = A Omega;  3. Q = orth(Y)
+  // Inside the power steps only range(Q) matters to the next product, and the
+  // product rounds Q to BF16 (relative 2^-9) before using it, so one
+  // CholeskyQR pass (orthonormal to u kappa^2) is enough there; the Q that B
+  // and U are formed from takes two passes.
   RSVD_CK(launch_gaussian(n, l, seed, 0u, kOutF32Fast, W.om, n, P->stream));
   if ((rc = mixed_pass(P, true, A, m, n, lda, W.om, l, 1, W.y, m))) return rc;
-  if ((rc = orth<float>(P, W.y, m, l, m, W.qm, m, nullptr, false))) return rc;
+  if ((rc = orth1<float>(P, W.y, m, l, m, W.qm, m))) return rc;
   // 4-5. q power steps on a BF16 operand, then one refinement step on bf16x2
   for (int j = 0; j <= q; ++j) {
     const int slices = (j == q) ? 2 : 1;
     if ((rc = mixed_pass(P, false, A, m, n, lda, W.qm, l, slices, W.z, n))) return rc;
-    if ((rc = orth<float>(P, W.z, n, l, n, W.om, n, nullptr, false))) return rc;
+    if ((rc = orth1<float>(P, W.z, n, l, n, W.om, n))) return rc;
     if ((rc = mixed_pass(P, true, A, m, n, lda, W.om, l, slices, W.y, m))) return rc;
-    if ((rc = orth<float>(P, W.y, m, l, m, W.qm, m, nullptr, false))) return rc;
+    if (j < q) {
+      if ((rc = orth1<float>(P, W.y, m, l, m, W.qm, m))) return rc;
+    } else if ((rc = orth<float>(P, W.y, m, l, m, W.qm, m, nullptr, false))) {
+      return rc;
+    }
   }
   // 6. B^T = A^T Q with Q split in three BF16 slices;  7-8. small SVD and lift
   if ((rc = mixed_pass(P, false, A, m, n, lda, W.qm, l, 3, W.z, n))) return rc;
