@@ -543,6 +543,12 @@ def run_ours(args):
     w = WORKLOADS[args.workload]
     m, n, k, p, q, seed = w["m"], w["n"], w["k"], w["p"], w["q"], w["seed"]
     l = k + p
+    # the library's own launch count at each section boundary, so that a
+    # profiler's launch list of this run can be split by section
+    marks = [("start", R.rsvd_kernel_launches())]
+
+    def mark(name):
+        marks.append((name, R.rsvd_kernel_launches()))
     passes = 2 * q + 2
     a_bytes = m * n * 8
     dA = _make_input(w, rank)
@@ -659,22 +665,31 @@ def run_ours(args):
     if st != 0:
         raise RuntimeError(f"e2e solve failed: {R.rsvd_status_string(st)}")
 
+    mark("plain")
     # --- Algorithm 6 (single pass) on the same matrix ---
     singlepass = run_singlepass(args, world, dA, w, plan, 6)
+    mark("singlepass")
     algorithm3 = run_singlepass(args, world, dA, w, plan, 3)
+    mark("algorithm3")
     adaptive = run_adaptive(args, world, dA, w)
+    mark("adaptive")
     srft = run_srft(args, world, dA, w, t_an)
+    mark("srft")
 
     # --- the mixed-precision workload beside it ---
     mixed = mixed_fp8 = None
     if not args.no_mixed:
         del A_h, dA2
         mixed = run_mixed(args, world, rank, uuid)
+        mark("mixed")
         torch.cuda.empty_cache()
         mixed_fp8 = run_mixed(args, world, rank, uuid, "mixed-fp8")
+        mark("mixed_fp8")
 
     batched = None if args.no_batched else run_batched(args, stream)
+    mark("batched")
     serving = None if args.no_serving else run_serving(args)
+    mark("serving")
 
     # --- CPU oracle on this host (rank 0, N = 1 only) ---
     cpu = None
@@ -708,6 +723,7 @@ def run_ours(args):
         "serving": serving,
         "gpu_launches": int(launches),
         "gpu_launches_per_step": launches / args.steps,
+        "launches_by_section": {b[0]: b[1] - a[1] for a, b in zip(marks, marks[1:])},
         "jacobi_sweeps": sweeps,
         "clocks": clocks,
         "peaks_source": peak_kind,
