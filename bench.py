@@ -948,8 +948,9 @@ def run_reference(args):
 
 def run_profile_case(args):
     """A reduced case of the same kernels for ncu captures (no timing):
-    A 8192 x 4096 FP64 (268 MB, larger than L2), l = 80; two passes of each
-    kind and one full solve."""
+    A 8192 x 4096 FP64 (268 MB, larger than L2), l = 80: two passes of each
+    kind, one full solve and two SRFT sketches; A 16384 x 16384 BF16 and
+    FP8, l = 160: two passes of each kind and one mixed solve."""
     import numpy as np
     import torch
 
@@ -974,7 +975,14 @@ def run_profile_case(args):
     st = plan.status()
     if st != 0:
         raise RuntimeError(R.rsvd_status_string(st))
-    del dA, plan
+    # the SRFT sketch through the FFT (n = 4096, a multiple of 64), l = 80
+    splan = R.Plan(m, n, 2 * l)
+    for _ in range(2):
+        splan.srft_sketch(dA, m, n, l, 5)
+    st = splan.status()
+    if st != 0:
+        raise RuntimeError(R.rsvd_status_string(st))
+    del dA, plan, splan
     # tcgen05 passes: A 16384 x 16384 BF16 (512 MB), l = 160
     m = n = 16384
     l = 160
@@ -985,6 +993,8 @@ def run_profile_case(args):
     for _ in range(2):
         R.rsvd_apply_a(plan.handle, dA, m, n, m, Xn, n, l, Y, m)
         R.rsvd_apply_at(plan.handle, dA, m, n, m, Xn, m, l, Y, n)
+    # one mixed solve (k = 128, p = 32, q = 1): the FP32 l x l kernels at l = 160
+    plan.solve(dA, m, n, 128, 32, 1, 3)
     st = plan.status()
     if st != 0:
         raise RuntimeError(R.rsvd_status_string(st))
