@@ -55,14 +55,99 @@ __global__ void apass_fixup_kernel(const float* __restrict__ part, int grid, int
   }
 }
 
+// The split tiles and their partial slots, listed on the host (kernel
+// parameter): the list kernel's blocks all do real work, and none searches
+// the stream-K schedule on the device.
+constexpr int kFixMaxTiles = 192;
+constexpr int kFixMaxSrc = 512;
+struct FixList {
+  int n;                          // split tiles
+  int tile[kFixMaxTiles];
+  int off[kFixMaxTiles + 1];      // sources of tile i: src[off[i] .. off[i+1])
+  int src[kFixMaxSrc];            // partial slot (CTA * 2 + 0 first / 1 last tile)
+};
+
+__global__ void apass_fixup_list_kernel(const float* __restrict__ part, int bmt, int l,
+                                        int64_t rows_out, float* __restrict__ out, int64_t ldo,
+                                        int accumulate, const __grid_constant__ FixList fl) {
+  const int i = blockIdx.x;
+  const int64_t t = fl.tile[i];
+  const int s0 = fl.off[i], s1 = fl.off[i + 1];
+  const int64_t per_tile = (int64_t)bmt * l;
+  const int c0 = blockIdx.y * kFixCols;
+  for (int r = threadIdx.x; r < bmt; r += blockDim.x) {
+    const int64_t row = t * bmt + r;
+    if (row >= rows_out) continue;
+#pragma unroll
+    for (int cc = 0; cc < kFixCols; ++cc) {
+      const int c = c0 + cc;
+      if (c >= l) break;
+      float s = 0.f;
+      for (int j = s0; j < s1; ++j) s += part[(size_t)fl.src[j] * per_tile + (size_t)c * bmt + r];
+      float* d = out + row + (int64_t)c * ldo;
+      *d = accumulate ? *d + s : s;
+    }
+  }
+}
+
+// Host mirror of the pass kernel's stream-K ranges: CTA c of `grid` takes
+// iterations [total c / grid, total (c+1) / grid).
+int64_t host_begin(int64_t total, int c, int grid) {
+  return (int64_t)((__int128)total * c / grid);
+}
+
+int host_cta_of(int64_t g, int64_t total, int grid) {
+  int c = (int)((__int128)g * grid / total);
+  while (c + 1 < grid && host_begin(total, c + 1, grid) <= g) ++c;
+  while (c > 0 && host_begin(total, c, grid) > g) --c;
+  return c;
+}
+
+// Fills fl with the split tiles in the same order and with the same slots as
+// the device-side search; false when it does not fit.
+bool build_fix_list(int grid, int64_t total, int kt, int64_t tiles, FixList& fl) {
+  fl.n = 0;
+  int ns = 0;
+  for (int c = 0; c < grid; ++c) {
+    // only tiles that hold a CTA boundary can be split
+    const int64_t b = host_begin(total, c, grid);
+    if (b % kt == 0) continue;
+    const int64_t t = b / kt;
+    if (fl.n > 0 && fl.tile[fl.n - 1] == t) continue;
+    const int cf = host_cta_of(t * kt, total, grid), cl = host_cta_of((t + 1) * kt - 1, total, grid);
+    if (cf == cl) continue;
+    if (fl.n >= kFixMaxTiles) return false;
+    fl.tile[fl.n] = (int)t;
+    fl.off[fl.n] = ns;
+    for (int cc = cf; cc <= cl; ++cc) {
+      const int64_t bc = host_begin(total, cc, grid);
+      if (bc >= host_begin(total, cc + 1, grid)) continue;
+      if (ns >= kFixMaxSrc) return false;
+      fl.src[ns++] = cc * 2 + ((bc / kt == t) ? 0 : 1);
+    }
+    ++fl.n;
+  }
+  fl.off[fl.n] = ns;
+  (void)tiles;
+  return true;
+}
+
 }  // namespace
 
 int launch_apass_fixup(const float* part, int grid, int64_t total, int kt, int bmt, int l,
                        int64_t rows_out, int64_t tiles, float* out, int64_t ldo, int accumulate,
                        cudaStream_t st) {
-  const dim3 fgrid((unsigned)tiles, (unsigned)((l + kFixCols - 1) / kFixCols));
-  apass_fixup_kernel<<<fgrid, 256, 0, st>>>(part, grid, total, kt, bmt, l, rows_out, out, ldo,
-                                            accumulate);
+  static thread_local FixList fl;
+  if (build_fix_list(grid, total, kt, tiles, fl)) {
+    if (fl.n == 0) return RSVD_OK;   // every tile written whole by one CTA
+    const dim3 fgrid((unsigned)fl.n, (unsigned)((l + kFixCols - 1) / kFixCols));
+    apass_fixup_list_kernel<<<fgrid, 256, 0, st>>>(part, bmt, l, rows_out, out, ldo, accumulate,
+                                                   fl);
+  } else {
+    const dim3 fgrid((unsigned)tiles, (unsigned)((l + kFixCols - 1) / kFixCols));
+    apass_fixup_kernel<<<fgrid, 256, 0, st>>>(part, grid, total, kt, bmt, l, rows_out, out, ldo,
+                                              accumulate);
+  }
   note_launch();
   return cudaGetLastError() == cudaSuccess ? RSVD_OK : RSVD_ERR_CUDA;
 }

@@ -1,7 +1,8 @@
 // Gram products G = Y^T Y of CholeskyQR2 (the orth(.) of Algorithm 4,
 // Section 3.3) on the CUDA cores, FP64 or FP32.
 //
-// Y is tall and skinny (up to 65536 rows, l <= 272 columns) and G is l x l
+// Y is tall and skinny (up to 65536 rows, l <= 272 columns in FP32, 160 in
+// FP64) and G is l x l
 // and symmetric, so only the upper triangle is formed:
 //
 //  * every CTA takes a contiguous range of rows and forms its rows' whole
@@ -89,7 +90,7 @@ __device__ __forceinline__ void ld_frag(const double* p, double (&v)[B]) {
 // the largest l that the block edge serves, rounded up to warps).
 template <typename T, int B>
 constexpr int gram_max_threads() {
-  return (sizeof(T) == 4 && B == 8) ? 608 : 544;
+  return (sizeof(T) == 4 && B == 8) ? 608 : (sizeof(T) == 8 ? 832 : 544);
 }
 
 template <typename T, int B>
@@ -210,7 +211,7 @@ cudaError_t launch_b(const T* Y, int64_t ldy, int64_t rows, int l, T* G, int64_t
 template <typename T>
 int block_edge(int l) {
   if (sizeof(T) == 4) return l <= 64 ? 4 : (l <= 272 ? 8 : 0);
-  return l <= 128 ? 4 : 0;
+  return l <= 160 ? 4 : 0;   // 40 x 41 / 2 = 820 blocks of 4 x 4 at l = 160
 }
 
 }  // namespace
