@@ -813,7 +813,9 @@ constexpr int JACOBI_REGS_SMALL = 6;
 // it holds -- one barrier per round.  FP64: the rotation costs tens of FP64
 // operations at 2 per clock per SM, so one thread per pair forms it between
 // two barriers and the group then applies it.
-template <typename T, int RMAX = JacobiRegs<T>::value>
+// GF > 0: the thread group per column pair is GF at compile time (the caller
+// guarantees jacobi_group(l) == GF), so a thread's row offsets are constants.
+template <typename T, int RMAX = JacobiRegs<T>::value, int GF = 0>
 __device__ __forceinline__ void jacobi_body(const T* __restrict__ M, int l, int64_t ldm,
                                             T* __restrict__ sig, T* __restrict__ Um, int64_t ldu,
                                             T* __restrict__ Vm, int64_t ldv,
@@ -830,7 +832,7 @@ __device__ __forceinline__ void jacobi_body(const T* __restrict__ M, int l, int6
   __shared__ T s_cs[kFused ? 1 : (RSVD_L_MAX + 1) / 2][2];
   const int tid = threadIdx.x, nt = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, nwarps = nt >> 5;
-  const int G = jacobi_group(l);
+  const int G = GF > 0 ? GF : jacobi_group(l);
   const int items = P * G;
   const int R = (l + G - 1) / G;          // rows per thread
   const bool in_regs = R <= RMAX;
@@ -843,6 +845,16 @@ __device__ __forceinline__ void jacobi_body(const T* __restrict__ M, int l, int6
     Wm[i + (int64_t)j * ldw] = v;
     fro = fma(v, v, fro);
     if (want_v) Wv[i + (int64_t)j * ldw] = (i == j) ? T(1) : T(0);
+  }
+  if constexpr (GF > 0) {
+    // rows l .. G R - 1 of every column are zero, so the fixed-group path
+    // reads and rotates them without a bounds test (ldw >= G R)
+    const int pad = G * R - l;
+    for (int t = tid; t < pad * twoP; t += nt) {
+      const int i = l + t % pad, j = t / pad;
+      Wm[i + (int64_t)j * ldw] = T(0);
+      if (want_v) Wv[i + (int64_t)j * ldw] = T(0);
+    }
   }
   fro = warp_sum(fro);
   if (lane == 0) s_fro[warp] = fro;
@@ -880,8 +892,9 @@ __device__ __forceinline__ void jacobi_body(const T* __restrict__ M, int l, int6
 #pragma unroll
           for (int k = 0; k < RMAX; ++k) {
             const int i = sub + G * k;
-            x[k] = (k < R && i < l) ? cp[i] : T(0);
-            y[k] = (k < R && i < l) ? cq[i] : T(0);
+            const bool ok = GF > 0 ? k < R : (k < R && i < l);
+            x[k] = ok ? cp[i] : T(0);
+            y[k] = ok ? cq[i] : T(0);
             a = fma(x[k], x[k], a);
             b = fma(y[k], y[k], b);
             g = fma(x[k], y[k], g);
@@ -945,7 +958,7 @@ __device__ __forceinline__ void jacobi_body(const T* __restrict__ M, int l, int6
 #pragma unroll
           for (int k = 0; k < RMAX; ++k) {
             const int i = sub + G * k;
-            if (k < R && i < l) {
+            if (GF > 0 ? k < R : (k < R && i < l)) {
               cp[i] = c * x[k] - sn * y[k];
               cq[i] = sn * x[k] + c * y[k];
             }

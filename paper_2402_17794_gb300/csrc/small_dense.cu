@@ -93,6 +93,17 @@ jacobi_svd_kernel(const T* __restrict__ M, int l, int64_t ldm, T* __restrict__ s
                  status);
 }
 
+// FP32, 80 < l <= 160: eight threads per column pair fixed at compile time
+__global__ void __launch_bounds__(JACOBI_THREADS)
+jacobi_svd_g8_kernel(const float* __restrict__ M, int l, int64_t ldm, float* __restrict__ sig,
+                     float* __restrict__ Um, int64_t ldu, float* __restrict__ Vm, int64_t ldv,
+                     float* __restrict__ UsInv, DeviceStatus* status) {
+  extern __shared__ __align__(16) unsigned char jg8_raw[];
+  jacobi_body<float, JacobiRegs<float>::value, 8>(M, l, ldm, sig, Um, ldu, Vm, ldv, UsInv,
+                                                  reinterpret_cast<float*>(jg8_raw),
+                                                  jacobi_ld<float>(l, true), status);
+}
+
 template <typename T>
 __global__ void __cluster_dims__(JACOBI_CLUSTER, 1, 1) __launch_bounds__(JACOBI_CL_THREADS)
 jacobi_cluster_kernel(const T* __restrict__ M, int l, int64_t ldm, T* __restrict__ sig,
@@ -198,6 +209,15 @@ cudaError_t launch_jacobi_svd(const T* M, int l, int64_t ldm, T* sig, T* Um, int
   }
   const int twoP = (l + 1) & ~1;
   const size_t need = (size_t)(Vm ? 2 : 1) * jacobi_ld<T>(l, true) * twoP * sizeof(T);
+  if constexpr (sizeof(T) == 4) {
+    if (jacobi_group(l) == 8 && (l + 7) / 8 <= JacobiRegs<float>::value &&
+        need <= dynamic_smem_cap((const void*)jacobi_svd_g8_kernel)) {
+      jacobi_svd_g8_kernel<<<1, JACOBI_THREADS, need, st>>>(M, l, ldm, sig, Um, ldu, Vm, ldv,
+                                                            UsInv, status);
+      note_launch();
+      return cudaGetLastError();
+    }
+  }
   const bool smem = need <= dynamic_smem_cap((const void*)jacobi_svd_kernel<T>);
   jacobi_svd_kernel<T><<<1, JACOBI_THREADS, smem ? need : 0, st>>>(
       M, l, ldm, sig, Um, ldu, Vm, ldv, UsInv, work, smem ? 1 : 0, status);
