@@ -406,6 +406,37 @@ def _oracle_rate(A_host, w, budget_s: float):
     return n_done, el
 
 
+def _oracle_rows(A_host, w):
+    """The CPU oracle of each further row on the same matrix, timed once each
+    (as it stands, on this host): Algorithm 6, Algorithm 3, the adaptive
+    range finder + SVD and FastRandRF with the SRFT."""
+    import numpy as np
+
+    import oracle
+    from oracle import adaptive as oad
+    from oracle import singlepass as osp
+    from oracle import srft as osr
+    A = np.asfortranarray(A_host)
+    k, p, q, seed = w["k"], w["p"], w["q"], w["seed"]
+    runs = {
+        "singlepass": lambda: osp.singlepass_rsvd(A, k, p, seed),
+        "algorithm3": lambda: oracle.rsvd(A, k, p, q, seed, algorithm=3),
+        "adaptive": lambda: oad.adaptive_rsvd(A, ADAPTIVE["eps"], ADAPTIVE["r"], seed,
+                                              l_max=ADAPTIVE["l_cap"]),
+        "srft": lambda: osr.fast_range_finder(A, k + p, seed),
+    }
+    out = {}
+    for name, fn in runs.items():
+        t0 = time.perf_counter()
+        fn()
+        el = time.perf_counter() - t0
+        out[name] = {"value": round(1.0 / el, 4),
+                     "unit": "ranges/s" if name == "srft" else "solves/s",
+                     "cores": _cores(), "kind": "oracle",
+                     "sample": f"one full oracle run of the same workload ({el:.1f} s)"}
+    return out
+
+
 def _cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -700,6 +731,10 @@ def run_ours(args):
                "kind": "oracle",
                "sample": f"{done} full oracle solve(s) of the same workload in {el:.1f} s "
                          f"(numpy FP64, LAPACK QR/SVD)"}
+        for name, base in _oracle_rows(A_np, w).items():
+            section = {"singlepass": singlepass, "algorithm3": algorithm3,
+                       "adaptive": adaptive, "srft": srft}[name]
+            section["cpu_baseline"] = base
 
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": world,
