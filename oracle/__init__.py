@@ -3,7 +3,9 @@
 A plain, slow, FP64 restatement of the thesis' randomized SVD (Algorithm 4,
 Section 3.3; Algorithm 2 when q = 0; Algorithm 3 and Algorithm 1 for the
 analysis tests), with the analysis formulas it is checked against
-(Eq. 3.1, Theorems 2, 3, 5 and 6, Eq. 3.5, Eq. 4.3).
+(Eq. 3.1, Theorems 2, 3, 5 and 6, Eq. 3.5, Eq. 4.3); Algorithm 6
+(``singlepass``); the toolbox's adaptive range finder (``adaptive``) and its
+SRFT test matrix with FastRandRF (``srft``).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
 ``--impl reference`` legs of ``bench.py`` may import anything here.  The
