@@ -104,3 +104,25 @@ def test_algorithm_argument_errors():
     assert R.rsvd_solve_algorithm(plan.handle, 3, A, 100, 80, 100, 8, 4, -1, 0, U, 100, S, VT, 8) == -9
     mplan = R.Plan(100, 80, 16, a_dtype=R.BF16, mode=R.MIXED)
     assert R.rsvd_solve_algorithm(mplan.handle, 3, A, 100, 80, 104, 8, 4, 1, 0, U, 100, S, VT, 8) == 7
+
+
+def test_algorithm6_config_full_size_fp64():
+    """The benchmark's Algorithm 6 solve: A 16384 x 8192 FP64, Haar factors,
+    sigma_i = i^-1.5, k = 64, p = 16, seed 2: sigma within 1e-10 relative and
+    the residual within 1.0001x of the oracle's single-pass solve."""
+    from oracle import singlepass as sp
+    m, n, k, p, seed = 16384, 8192, 64, 16, 2
+    dA = syn.lowrank_matrix_torch(m, n, syn.spectrum("poly", n, alpha=1.5), seed=0)
+    A = np.asfortranarray(dA.cpu().numpy().T)
+    plan = R.Plan(m, n, k + p)
+    U, S, VT = plan.solve_algorithm(6, dA, m, n, k, p, 0, seed)
+    st = plan.status()
+    assert st == 0, R.rsvd_status_string(st)
+    ref = sp.singlepass_rsvd(A, k, p, seed)
+    s = S.cpu().numpy()
+    rel = np.abs(s - ref.S) / ref.S
+    assert rel.max() <= 1e-10, rel.max()
+    u, vt = R.to_numpy_f(U), R.to_numpy_f(VT)
+    r_gpu = analysis.lowrank_residual(A, u, s, vt)
+    r_orc = analysis.lowrank_residual(A, ref.U, ref.S, ref.Vt)
+    assert r_gpu <= 1.0001 * r_orc + 1e-15 * ref.S[0], (r_gpu, r_orc)
