@@ -14,7 +14,9 @@ The thesis defines the test matrix (n x l, complex)
 
 and FastRandRF (Algorithm 4.5 of Halko, Martinsson and Tropp 2011, which it
 names as its source): Y = A Omega, Q = orth(Y), an m x l orthonormal
-(complex) basis approximating range(A).
+(complex) basis approximating range(A).  ``srft_rsvd`` adds Stage B of the
+prototype (Section 2.2) on that basis: the rank-k SVD B = Q^H A = U~ S V^H,
+U = Q U~.
 
 Readings (the thesis is silent on these):
   * the random numbers come from the Philox4x32-10 generator of
@@ -112,3 +114,32 @@ def gram_schmidt_phases(Q: np.ndarray, Y: np.ndarray) -> np.ndarray:
     d = np.einsum("ij,ij->j", Q.conj(), Y)
     ph = np.where(np.abs(d) > 0, d / np.where(np.abs(d) > 0, np.abs(d), 1.0), 1.0)
     return Q * ph[None, :]
+
+
+@dataclass
+class SrftSvd:
+    U: np.ndarray        # m x k complex, orthonormal columns
+    S: np.ndarray        # k, descending
+    Vt: np.ndarray       # k x n complex (V^H)
+    range: SrftRange
+
+
+def srft_rsvd(A: np.ndarray, k: int, p: int, seed: int) -> SrftSvd:
+    """The rank-k SVD on FastRandRF's range (Stage B of the prototype,
+    Section 2.2, on the complex basis): B = Q^H A, B = U~ S V^H, U = Q U~,
+    keep the leading k triplets (Section 3.1's truncation).  Each (u_i, v_i)
+    is rotated by the unit factor that makes u_i's largest-magnitude entry
+    real and positive (the complex form of the real sign convention)."""
+    A = np.asarray(A)
+    l = k + p
+    rf = fast_range_finder(A, l, seed)
+    B = rf.Q.conj().T @ A
+    Ut, S, Vh = np.linalg.svd(B, full_matrices=False)
+    U = rf.Q @ Ut[:, :k]
+    Vh = Vh[:k]
+    idx = np.argmax(np.abs(U), axis=0)
+    ph = U[idx, np.arange(k)]
+    ph = np.where(np.abs(ph) > 0, ph / np.abs(ph), 1.0)
+    U = U / ph[None, :]
+    Vh = Vh / ph[:, None].conj()
+    return SrftSvd(U=U, S=S[:k], Vt=Vh, range=rf)

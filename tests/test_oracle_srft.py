@@ -109,3 +109,31 @@ def test_planted_mistake_missing_d():
     assert np.linalg.norm(A - good.Q @ (good.Q.conj().T @ A), 2) <= 1e-12 * np.linalg.norm(A, 2)
     bad_Y = A @ (np.sqrt(n / l) * srft.dft_columns(n, r))  # D left out
     assert np.linalg.norm(bad_Y) <= 1e-12 * np.linalg.norm(A)
+
+
+def test_srft_rsvd_stage_b():
+    """Stage B on the SRFT range: exact for a matrix of rank <= k, Eckart-Young
+    and interlacing otherwise, orthonormal factors, the phase convention, and
+    U S V^H reproducing Q Q^H A truncated to rank k."""
+    m, n, k, p = 240, 192, 12, 8
+    sig = np.geomspace(2.0, 1e-2, 10)
+    A = syn.lowrank_matrix(m, n, sig, seed=3)                  # rank 10 <= k
+    out = srft.srft_rsvd(A, k, p, seed=2)
+    assert np.abs(out.S[:10] - sig).max() <= 1e-12 * sig[0]
+    assert np.abs(out.S[10:]).max() <= 1e-12 * sig[0]
+    assert np.linalg.norm(A - out.U @ np.diag(out.S) @ out.Vt, 2) <= 1e-12 * sig[0]
+    full = syn.spectrum("exp", n, r=5.0)
+    A = syn.lowrank_matrix(m, n, full, seed=4)
+    out = srft.srft_rsvd(A, k, p, seed=5)
+    err = np.linalg.norm(A - out.U @ np.diag(out.S) @ out.Vt, 2)
+    assert err >= full[k] * (1 - 1e-12)                        # Eckart-Young
+    assert np.all(out.S <= full[:k] * (1 + 1e-12))             # interlacing
+    assert np.abs(out.U.conj().T @ out.U - np.eye(k)).max() <= 1e-12
+    assert np.abs(out.Vt @ out.Vt.conj().T - np.eye(k)).max() <= 1e-12
+    idx = np.argmax(np.abs(out.U), axis=0)
+    lead = out.U[idx, np.arange(k)]
+    assert np.abs(lead.imag).max() <= 1e-14 and np.all(lead.real > 0)
+    # truncating Q Q^H A to rank k gives the same matrix
+    P = out.range.Q @ (out.range.Q.conj().T @ A)
+    u, s, vh = np.linalg.svd(P, full_matrices=False)
+    assert np.abs((u[:, :k] * s[:k]) @ vh[:k] - out.U @ np.diag(out.S) @ out.Vt).max() <= 1e-12
