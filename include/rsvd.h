@@ -305,6 +305,25 @@ int rsvd_range_srft(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64
                     uint64_t seed, void* Q, int64_t ldq);
 
 /*
+ * rsvd_solve_srft: FastRandRF with l = k + p (as rsvd_range_srft), then
+ * Stage B of the prototype (Section 2.2) on the complex basis, truncated to
+ * rank k (Section 3.1): B = Q^H A (computed as B^H = A^T Q), B = U~ S V^H,
+ * U = Q U~.  Complex outputs are planar:
+ *   U    m x 2k real (ldu >= m): [Re U | Im U];
+ *   S    k FP64 values, descending;
+ *   VT   k x 2n real (ldvt >= k): [Re V^H | Im V^H].
+ * Each (u_i, v_i) is multiplied by the unit factor that makes the entry of
+ * u_i with the largest modulus real and positive (lowest row on ties).
+ * Plain plans with l_max >= 2(k+p); 2(k+p) <= RSVD_L_MAX.
+ * Argument errors: -1 plan; -2 A NULL; -3 m; -4 n; -5 lda; -6 k; -7 p (or
+ * k+p > min(m, n)); -9 U NULL; -10 ldu; -11 S NULL; -12 VT NULL; -13 ldvt.
+ * RSVD_ERR_WORKSPACE / RSVD_ERR_UNSUPPORTED as rsvd_range_srft.
+ */
+int rsvd_solve_srft(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t lda, int k,
+                    int p, uint64_t seed, void* U, int64_t ldu, double* S, void* VT,
+                    int64_t ldvt);
+
+/*
  * rsvd_srft_sketch: the sketch alone, Y = A Omega with the SRFT Omega of
  * rsvd_range_srft (same seed, same D and R), written planar to Y (real
  * m x 2l, ldy >= m).  Arguments and errors as rsvd_range_srft (Y for Q).

@@ -50,6 +50,8 @@ SIGNATURES = {
                                     c_void_p, c_int64, ctypes.POINTER(c_int)]),
     "rsvd_range_srft": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_int64, c_int, c_uint64,
                                 c_void_p, c_int64]),
+    "rsvd_solve_srft": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_int64, c_int, c_int,
+                                c_uint64, c_void_p, c_int64, c_void_p, c_void_p, c_int64]),
     "rsvd_srft_sketch": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_int64, c_int, c_uint64,
                                  c_void_p, c_int64]),
     "rsvd_gaussian": (c_int, [c_void_p, c_int64, c_int, c_uint64, c_uint32, c_int, c_void_p,

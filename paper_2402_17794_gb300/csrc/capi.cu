@@ -426,6 +426,28 @@ int rsvd_range_srft(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64
   return range_srft(plan, (const double*)A, m, n, lda, l, seed, (double*)Q, ldq);
 }
 
+int rsvd_solve_srft(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t lda, int k,
+                    int p, uint64_t seed, void* U, int64_t ldu, double* S, void* VT,
+                    int64_t ldvt) {
+  if (!plan) return -1;
+  if (!A) return -2;
+  if (m < 1) return -3;
+  if (n < 1 || n > INT32_MAX) return -4;
+  if (lda < m) return -5;
+  if (k < 1) return -6;
+  if (p < 0 || k + p > (m < n ? m : n) || 2 * (k + p) > RSVD_L_MAX) return -7;
+  if (!U) return -9;
+  if (ldu < m) return -10;
+  if (!S) return -11;
+  if (!VT) return -12;
+  if (ldvt < k) return -13;
+  if (!ready(plan) || m > plan->m_max || n > plan->n_max || 2 * (k + p) > plan->l_max)
+    return RSVD_ERR_WORKSPACE;
+  if (plan->mode != RSVD_MODE_PLAIN || plan->batched) return RSVD_ERR_UNSUPPORTED;
+  return solve_srft(plan, (const double*)A, m, n, lda, k, p, seed, (double*)U, ldu, S,
+                    (double*)VT, ldvt);
+}
+
 int rsvd_srft_sketch(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t lda, int l,
                      uint64_t seed, void* Y, int64_t ldy) {
   const int rc = srft_args(plan, A, m, n, lda, l, Y, ldy);

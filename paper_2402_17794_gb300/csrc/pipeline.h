@@ -122,6 +122,10 @@ int range_srft(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t lda
                uint64_t seed, double* Q, int64_t ldq);
 int sketch_srft(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t lda, int l,
                 uint64_t seed, double* Y, int64_t ldy);
+// FastRandRF, then the rank-k SVD on the complex basis (Stage B): U (m x 2k
+// planar, ldu), S (k), VT (k x 2n planar [Re V^H | Im V^H], ldvt).
+int solve_srft(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t lda, int k, int p,
+               uint64_t seed, double* U, int64_t ldu, double* S, double* VT, int64_t ldvt);
 
 // Step entry: one tcgen05 pass with a BF16 operand X (ldx) of `l` columns.
 int mixed_apply(rsvd_plan_t P, const void* A, int64_t m, int64_t n, int64_t lda, const void* X,

@@ -135,6 +135,93 @@ __global__ void complex_coef_kernel(const double* __restrict__ Ri, int l, double
   }
 }
 
+// M_R (2l x 2l, ld 2l) = the block realification [[M_re, -M_im], [M_im, M_re]]
+// of M = R^H, R = Q_B^H Z (l x l complex) read from the real product
+// G2 = [Re Q_B | Im Q_B]^T [Re Z | Im Z] (2l x 2l, ld 2l):
+// R_re = G2_11 + G2_22, R_im = G2_12 - G2_21.
+__global__ void realify_rh_kernel(const double* __restrict__ G2, int l, double* __restrict__ MR) {
+  const int L = 2 * l;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < L * L; t += gridDim.x * blockDim.x) {
+    const int a = t % L, b = t / L;
+    const int i = a % l, j = b % l;
+    // M[i][j] = conj(R[j][i])
+    const double mre = G2[j + i * L] + G2[(l + j) + (l + i) * L];
+    const double mim = -(G2[j + (l + i) * L] - G2[(l + j) + i * L]);
+    const bool top = a < l, left = b < l;
+    MR[t] = (top == left) ? mre : (top ? -mim : mim);
+  }
+}
+
+// C (2l x 2k, ld 2l) = [[X_re, X_im], [-X_im, X_re]] for the complex l x k
+// matrix whose column i is column 2i of the realified singular vectors X
+// (2l x 2l, ld 2l): X[:, 2i] = [Re x_i ; Im x_i].
+__global__ void pick_pairs_kernel(const double* __restrict__ X, int l, int k,
+                                  double* __restrict__ C) {
+  const int L = 2 * l;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < l * k; t += gridDim.x * blockDim.x) {
+    const int r = t % l, i = t / l;
+    const double xr = X[r + (2 * i) * L], xi = X[(l + r) + (2 * i) * L];
+    C[r + i * L] = xr;
+    C[r + (k + i) * L] = xi;
+    C[(l + r) + i * L] = -xi;
+    C[(l + r) + (k + i) * L] = xr;
+  }
+}
+
+// One block per triplet i: the phase that makes u_i's largest-magnitude entry
+// (lowest row on ties) real and positive is removed from u_i and v_i; then
+// V^H's row i is written planar ([Re V^H | Im V^H], ld ldvt) and S_i = sig_{2i}.
+// U: m x 2k planar (ld ldu), V: n x 2k planar (ld n).
+__global__ void finalize_complex_kernel(double* __restrict__ U, int64_t m, int64_t ldu, int k,
+                                        const double* __restrict__ V, int64_t n,
+                                        const double* __restrict__ sig, double* __restrict__ S,
+                                        double* __restrict__ VT, int64_t ldvt) {
+  const int i = blockIdx.x;
+  double* ure = U + (int64_t)i * ldu;
+  double* uim = U + (int64_t)(k + i) * ldu;
+  __shared__ double sv[256];
+  __shared__ int64_t si[256];
+  double best = -1.0;
+  int64_t bidx = 0;
+  for (int64_t r = threadIdx.x; r < m; r += blockDim.x) {
+    const double v = hypot(ure[r], uim[r]);
+    if (v > best) {
+      best = v;
+      bidx = r;
+    }
+  }
+  sv[threadIdx.x] = best;
+  si[threadIdx.x] = bidx;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+      const double o = sv[threadIdx.x + h];
+      const int64_t oi = si[threadIdx.x + h];
+      if (o > sv[threadIdx.x] || (o == sv[threadIdx.x] && oi < si[threadIdx.x])) {
+        sv[threadIdx.x] = o;
+        si[threadIdx.x] = oi;
+      }
+    }
+    __syncthreads();
+  }
+  const double a = hypot(ure[si[0]], uim[si[0]]);
+  const double pr = a > 0.0 ? ure[si[0]] / a : 1.0, pi = a > 0.0 ? uim[si[0]] / a : 0.0;
+  __syncthreads();   // every thread has read the pivot entry before it changes
+  for (int64_t r = threadIdx.x; r < m; r += blockDim.x) {   // u <- u conj(ph)
+    const double xr = ure[r], xi = uim[r];
+    ure[r] = xr * pr + xi * pi;
+    uim[r] = xi * pr - xr * pi;
+  }
+  const double* vre = V + (int64_t)i * n;
+  const double* vim = V + (int64_t)(k + i) * n;
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {   // (V^H)_ij = ph conj(v_j)
+    const double vr = vre[j], vi = vim[j];
+    VT[i + j * ldvt] = pr * vr + pi * vi;
+    VT[i + (n + j) * ldvt] = pi * vr - pr * vi;
+  }
+  if (threadIdx.x == 0) S[i] = sig[2 * i];
+}
+
 }  // namespace
 
 int srft_setup(rsvd_plan_t P, int64_t n, int l, uint64_t seed, double* d_re, double* d_im,
@@ -204,6 +291,41 @@ int range_srft(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t lda
   if ((rc = srft_setup(P, n, l, seed, d_re, d_im, r))) return rc;
   if ((rc = srft_sketch(P, A, m, n, lda, l, d_re, d_im, r, W.y, m))) return rc;
   return orth_complex(P, W.y, m, l, m, Q, ldq);
+}
+
+int solve_srft(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t lda, int k, int p,
+               uint64_t seed, double* U, int64_t ldu, double* S, double* VT, int64_t ldvt) {
+  Work<double> W = work_of<double>(P);
+  const int l = k + p, L = 2 * l;
+  cudaStream_t st = P->stream;
+  int rc;
+  // FastRandRF: Q (m x l complex, planar) in W.qm
+  if ((rc = range_srft(P, A, m, n, lda, l, seed, W.qm, m))) return rc;
+  // B^H = A^T Q (A real): one real product with the 2l planar columns
+  if ((rc = gemm<double>(P, A, lda, true, W.qm, m, W.z, n, n, m, L))) return rc;
+  // B^H = Q_B R_B (complex CholeskyQR2), R_B = Q_B^H B^H
+  if ((rc = orth_complex(P, W.z, n, l, n, W.qb, n))) return rc;
+  if ((rc = gemm<double>(P, W.qb, n, true, W.z, n, W.G, L, L, n, L))) return rc;
+  // R_B^H = U~ S W^H through the realified 2l x 2l matrix: each singular
+  // value appears twice, and column 2i of either factor is [Re x_i ; Im x_i]
+  realify_rh_kernel<<<(L * L + 255) / 256, 256, 0, st>>>(W.G, l, W.Mt);
+  note_launch();
+  RSVD_CK(cudaGetLastError());
+  RSVD_CK(launch_jacobi_svd<double>(W.Mt, L, L, W.sig, W.Um, L, W.Vm, L, nullptr, W.jw, dstatus(P),
+                                    st));
+  pick_pairs_kernel<<<(l * k + 255) / 256, 256, 0, st>>>(W.Um, l, k, W.R1);
+  note_launch();
+  RSVD_CK(cudaGetLastError());
+  pick_pairs_kernel<<<(l * k + 255) / 256, 256, 0, st>>>(W.Vm, l, k, W.R2);
+  note_launch();
+  RSVD_CK(cudaGetLastError());
+  // U = Q U~ (into U, planar), V = Q_B W (into W.tmp, planar)
+  if ((rc = gemm<double>(P, W.qm, m, false, W.R1, L, U, ldu, m, L, 2 * k))) return rc;
+  if ((rc = gemm<double>(P, W.qb, n, false, W.R2, L, W.tmp, n, n, L, 2 * k))) return rc;
+  finalize_complex_kernel<<<k, 256, 0, st>>>(U, m, ldu, k, W.tmp, n, W.sig, S, VT, ldvt);
+  note_launch();
+  RSVD_CK(cudaGetLastError());
+  return RSVD_OK;
 }
 
 int sketch_srft(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t lda, int l,

@@ -157,6 +157,11 @@ def rsvd_range_srft(plan, A, m, n, lda, l, seed, Q, ldq) -> int:
     return _lib.load().rsvd_range_srft(plan, _ptr(A), m, n, lda, l, seed, _ptr(Q), ldq)
 
 
+def rsvd_solve_srft(plan, A, m, n, lda, k, p, seed, U, ldu, S, VT, ldvt) -> int:
+    return _lib.load().rsvd_solve_srft(plan, _ptr(A), m, n, lda, k, p, seed, _ptr(U), ldu,
+                                       _ptr(S), _ptr(VT), ldvt)
+
+
 def rsvd_srft_sketch(plan, A, m, n, lda, l, seed, Y, ldy) -> int:
     return _lib.load().rsvd_srft_sketch(plan, _ptr(A), m, n, lda, l, seed, _ptr(Y), ldy)
 
@@ -349,6 +354,19 @@ class Plan:
         Q = torch.empty(2 * l, m, dtype=torch.float64, device=A.device)
         _check(rsvd_range_srft(self.handle, A, m, n, lda, l, seed, Q, m), "rsvd_range_srft")
         return Q
+
+    def solve_srft(self, A, m, n, k, p, seed, lda=None):
+        """FastRandRF + the rank-k SVD on its complex basis (plain plan with
+        l_max >= 2(k+p)): U as a planar tensor (2k, m) (rows 0..k-1 Re U),
+        S (k,), VT as a planar tensor (2n, k) (rows 0..n-1 Re V^H).
+        Enqueued only."""
+        lda = lda or A.shape[1]
+        U = torch.empty(2 * k, m, dtype=torch.float64, device=A.device)
+        S = torch.empty(k, dtype=torch.float64, device=A.device)
+        VT = torch.empty(2 * n, k, dtype=torch.float64, device=A.device)
+        _check(rsvd_solve_srft(self.handle, A, m, n, lda, k, p, seed, U, m, S, VT, k),
+               "rsvd_solve_srft")
+        return U, S, VT
 
     def srft_sketch(self, A, m, n, l, seed, lda=None):
         """Y = A Omega with the SRFT Omega, planar (2l, m).  Enqueued only."""

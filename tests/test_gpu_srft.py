@@ -108,3 +108,29 @@ def test_srft_config_full_size_fp64():
     assert np.abs(y - Yo).max() <= 1e-12 * np.abs(Yo).max()
     assert np.abs(q.conj().T @ q - np.eye(l)).max() <= 1e-12
     assert np.abs(q - Qo).max() <= 1e-9, np.abs(q - Qo).max()
+
+
+@pytest.mark.parametrize("m,n,k,p,lda_pad", [(700, 512, 16, 8, 0), (513, 640, 30, 10, 3),
+                                            (1000, 97, 12, 6, 0)])
+def test_solve_srft_matches_oracle(m, n, k, p, lda_pad):
+    """FastRandRF + Stage B on the complex basis against the oracle's
+    srft_rsvd: sigma within 1e-10 relative, U and V^H within 1e-8 after the
+    shared phase convention, U S V^H within 1e-10 sigma_1."""
+    A = syn.lowrank_matrix(m, n, syn.spectrum("exp", min(m, n), r=8.0), seed=m + 2 * n)
+    ref = srft.srft_rsvd(A, k, p, seed=k)
+    dA, lda = _device(A, lda_pad)
+    plan = R.Plan(m, n, 2 * (k + p))
+    U, S, VT = plan.solve_srft(dA, m, n, k, p, seed=k, lda=lda)
+    assert plan.status() == 0
+    s = S.cpu().numpy()
+    assert (np.abs(s - ref.S) / ref.S).max() <= 1e-10
+    u = _complex(U, k)
+    vt_planar = R.to_numpy_f(VT)          # k x 2n
+    vt = vt_planar[:, :n] + 1j * vt_planar[:, n:]
+    assert np.abs(u.conj().T @ u - np.eye(k)).max() <= 1e-12
+    assert np.abs(vt @ vt.conj().T - np.eye(k)).max() <= 1e-12
+    assert np.abs(u - ref.U).max() <= 1e-8, np.abs(u - ref.U).max()
+    assert np.abs(vt - ref.Vt).max() <= 1e-8, np.abs(vt - ref.Vt).max()
+    rec = (u * s) @ vt
+    rec_o = (ref.U * ref.S) @ ref.Vt
+    assert np.abs(rec - rec_o).max() <= 1e-10 * ref.S[0]
