@@ -18,8 +18,9 @@ Pinning (what ties the oracle to the thesis rather than to itself) lives in
 spectrum, Eckart-Young (Eq. 3.1), orthonormality, interlacing, the expected
 error bounds of Theorems 2, 3 and 6 averaged over seeds, the canonical-angle
 bound of Theorem 5, distribution tests of the Gaussian generator, and planted
-mistakes that each pin must catch.  Parity unpinned: the exact Philox bit
-stream (no published test vectors are used; it is pinned statistically).
+mistakes that each pin must catch.  The Philox bit stream is pinned to the
+published Philox4x32-10 known-answer vectors (Salmon et al., SC'11), stored
+in ``tests/golden/philox4x32_10_kat.txt``.
 """
 
 from .philox import philox4x32_10, gaussian_matrix  # noqa: F401

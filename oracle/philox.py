@@ -23,6 +23,9 @@ t = j*n + i as counter words (lo32(t), hi32(t), stream, 0) and the key
 (lo32(seed), hi32(seed)).  Words 0,1 give u1 and words 2,3 give u2, each as
 (x + 1/2) 2^-52 where x is the 52-bit integer (w_a >> 6) 2^26 + (w_b >> 6);
 that value is exact in FP64 and lies strictly inside (0, 1).
+
+Pinned by the published known-answer vectors of Philox4x32-10 (the all-zero,
+all-ones and pi-digit counter/key cases of Random123's known-answer file).
 """
 from __future__ import annotations
 

@@ -14,6 +14,7 @@ Each check ties ``oracle/`` to something other than itself:
 * planted mistakes: each mutant of the oracle must fail at least one check.
 """
 import math
+import pathlib
 
 import numpy as np
 import pytest
@@ -22,7 +23,7 @@ from scipy import stats
 import oracle
 from oracle import analysis
 from oracle import randsvd as orsvd
-from oracle.philox import gaussian_matrix, philox_words
+from oracle.philox import gaussian_matrix, philox4x32_10, philox_words
 from paper_2402_17794_gb300 import synthetic as syn
 
 
@@ -158,6 +159,62 @@ def test_philox_words_uniform_and_distinct_streams():
     # seeds above 2^32 use the high key word
     d = gaussian_matrix(64, 8, seed=1 + (1 << 32))
     assert np.abs(a - d).max() > 0.1
+
+
+def _read_kat():
+    rows = []
+    path = pathlib.Path(__file__).parent / "golden" / "philox4x32_10_kat.txt"
+    for line in path.read_text().splitlines():
+        if line.strip() and not line.startswith("#"):
+            rows.append([int(x, 16) for x in line.split()])
+    return rows
+
+
+def check_philox_kat(fn=philox4x32_10):
+    """The published Philox4x32-10 known-answer vectors (Salmon et al., SC'11;
+    Random123's known-answer file): counter (c0..c3) and key (k0, k1) map to
+    the four printed output words."""
+    rows = _read_kat()
+    assert len(rows) == 3
+    for r in rows:
+        c = [np.array([x], dtype=np.uint64) for x in r[:4]]
+        out = [int(w[0]) for w in fn(*c, r[4], r[5])]
+        assert out == r[6:], (r, [hex(x) for x in out])
+
+
+def test_philox_known_answer_vectors():
+    check_philox_kat()
+
+
+def _philox_mutant(swap_multipliers=False, permute=False, rounds=10):
+    """Philox4x32 with one plausible mistake planted (a test-side copy of the
+    round structure, not the oracle's code)."""
+    mask = (1 << 32) - 1
+    m0, m1 = 0xD2511F53, 0xCD9E8D57
+    if swap_multipliers:
+        m0, m1 = m1, m0
+
+    def fn(c0, c1, c2, c3, k0, k1):
+        c = [int(x[0]) for x in (c0, c1, c2, c3)]
+        k = [int(k0), int(k1)]
+        for rnd in range(rounds):
+            if rnd:
+                k = [(k[0] + 0x9E3779B9) & mask, (k[1] + 0xBB67AE85) & mask]
+            p0, p1 = m0 * c[0], m1 * c[2]
+            c = [(p1 >> 32) ^ c[1] ^ k[0], p1 & mask, (p0 >> 32) ^ c[3] ^ k[1], p0 & mask]
+        if permute:
+            c = [c[1], c[0], c[3], c[2]]
+        return [np.array([x], dtype=np.uint64) for x in c]
+    return fn
+
+
+@pytest.mark.parametrize("mutant", [
+    dict(swap_multipliers=True), dict(permute=True), dict(rounds=9)])
+def test_philox_kat_catches_planted_mistakes(mutant):
+    # the unmutated test-side copy passes, so the pin, not the copy, decides
+    check_philox_kat(_philox_mutant())
+    with pytest.raises(AssertionError):
+        check_philox_kat(_philox_mutant(**mutant))
 
 
 def test_omega_prefix_property():
