@@ -16,12 +16,12 @@ Readings (the thesis' listing is garbled or silent on these):
     Y_r = A* Omega_r, the only product the dimensions allow for m != n.
   * step 4 does not weight the two equations; "the least-squares solution of
     the joint system" is read as minimising the sum of both squared
-    Frobenius residuals with equal weights.  Its normal equations are the
-    Sylvester equation  (M* M) C + C (N N*) = M* P + R N*  with
-    M = Omega_r* Q_c, P = Y_r* Q_r, N = Q_r* Omega_c, R = Q_c* Y_c, solved
-    here through the eigendecompositions of the two SPD coefficient
-    matrices (LAPACK).  The tests pin it to the stacked (Kronecker) least
-    squares on small k.
+    Frobenius residuals with equal weights, with M = Omega_r* Q_c,
+    P = Y_r* Q_r, N = Q_r* Omega_c, R = Q_c* Y_c.  The oracle writes that
+    definition out: both equations vectorised (column-major vec, so
+    vec(M C) = (I kron M) vec C and vec(C N) = (N^T kron I) vec C), stacked
+    into one (2 l k) x k^2 system and handed to LAPACK's least-squares
+    solver.  No normal equations are formed.
   * Omega_r comes from Philox stream 1 of the same seed (the thesis draws
     the two matrices independently and names no generator).
 """
@@ -53,16 +53,13 @@ def dominant_left(Y: np.ndarray, k: int) -> np.ndarray:
 
 def joint_lstsq(M, P, N, R) -> np.ndarray:
     """Step 4: C minimising ||M C - P||_F^2 + ||C N - R||_F^2 (M: l x k,
-    P: l x k, N: k x l, R: k x l) through the normal equations
-    (M* M) C + C (N N*) = M* P + R N*, a Sylvester equation with SPD
-    coefficients, diagonalised by their eigendecompositions."""
-    A1 = M.T @ M
-    B1 = N @ N.T
-    F = M.T @ P + R @ N.T
-    la, Va = np.linalg.eigh(A1)
-    lb, Vb = np.linalg.eigh(B1)
-    G = (Va.T @ F @ Vb) / (la[:, None] + lb[None, :])
-    return Va @ G @ Vb.T
+    P: l x k, N: k x l, R: k x l), as the stacked least-squares problem
+    [I kron M ; N^T kron I] vec C = [vec P ; vec R] (column-major vec)."""
+    k = M.shape[1]
+    K = np.vstack([np.kron(np.eye(k), M), np.kron(N.T, np.eye(k))])
+    rhs = np.concatenate([P.flatten("F"), R.flatten("F")])
+    c = np.linalg.lstsq(K, rhs, rcond=None)[0]
+    return c.reshape(k, k, order="F")
 
 
 def singlepass_rsvd(A: np.ndarray, k: int, p: int, seed: int,

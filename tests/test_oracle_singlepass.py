@@ -25,17 +25,48 @@ def test_exact_rank_k_recovery(m, n, k, p):
     assert np.linalg.norm(A - r.U @ np.diag(r.S) @ r.Vt, 2) <= 1e-12 * sig[0]
 
 
-def test_joint_lstsq_equals_stacked_kronecker_least_squares():
+def _sylvester_normal_equations(M, P, N, R):
+    """Test-side cross-check of step 4 by a different route: the normal
+    equations of the joint problem are the Sylvester equation
+    (M* M) C + C (N N*) = M* P + R N*, whose SPD coefficients are
+    diagonalised by their eigendecompositions."""
+    la, Va = np.linalg.eigh(M.T @ M)
+    lb, Vb = np.linalg.eigh(N @ N.T)
+    G = (Va.T @ (M.T @ P + R @ N.T) @ Vb) / (la[:, None] + lb[None, :])
+    return Va @ G @ Vb.T
+
+
+def test_joint_lstsq_minimises_both_residuals():
+    """The stacked solution is a stationary point of the joint objective (its
+    gradient M*(MC-P) + (CN-R)N* vanishes), it agrees with the Sylvester
+    normal equations, and no perturbation lowers the objective."""
     rng = np.random.default_rng(0)
     for l, k in [(9, 4), (12, 12), (20, 7)]:
         M, P = rng.standard_normal((l, k)), rng.standard_normal((l, k))
         N, R = rng.standard_normal((k, l)), rng.standard_normal((k, l))
         C = sp.joint_lstsq(M, P, N, R)
-        # column-major vec: vec(M C) = (I kron M) vec C, vec(C N) = (N^T kron I) vec C
-        K = np.vstack([np.kron(np.eye(k), M), np.kron(N.T, np.eye(k))])
-        rhs = np.concatenate([P.flatten("F"), R.flatten("F")])
-        ref = np.linalg.lstsq(K, rhs, rcond=None)[0].reshape(k, k, order="F")
-        assert np.abs(C - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
+        grad = M.T @ (M @ C - P) + (C @ N - R) @ N.T
+        assert np.abs(grad).max() <= 1e-11 * max(1.0, np.abs(C).max())
+        ref = _sylvester_normal_equations(M, P, N, R)
+        assert np.abs(C - ref).max() <= 1e-11 * max(1.0, np.abs(ref).max())
+
+        def obj(X):
+            return np.linalg.norm(M @ X - P) ** 2 + np.linalg.norm(X @ N - R) ** 2
+        f0 = obj(C)
+        for _ in range(5):
+            assert obj(C + 1e-3 * rng.standard_normal(C.shape)) > f0
+
+
+def test_joint_lstsq_planted_mistake_one_equation_only():
+    """Planted mistake: solving only the first equation (M C = P) is not the
+    joint least squares; the stationarity pin catches it."""
+    rng = np.random.default_rng(2)
+    l, k = 12, 5
+    M, P = rng.standard_normal((l, k)), rng.standard_normal((l, k))
+    N, R = rng.standard_normal((k, l)), rng.standard_normal((k, l))
+    bad = np.linalg.lstsq(M, P, rcond=None)[0]
+    grad = M.T @ (M @ bad - P) + (bad @ N - R) @ N.T
+    assert np.abs(grad).max() > 1e-3
 
 
 def test_joint_lstsq_recovers_a_consistent_solution():
