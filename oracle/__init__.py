@@ -3,8 +3,8 @@
 A plain, slow, FP64 restatement of the thesis' randomized SVD (Algorithm 4,
 Section 3.3; Algorithm 2 when q = 0; Algorithm 3 and Algorithm 1 for the
 analysis tests), with the analysis formulas it is checked against
-(Eq. 3.1, Theorems 2, 3, 5 and 6, Eq. 3.5, Eq. 4.3); Algorithm 6
-(``singlepass``); the toolbox's adaptive range finder (``adaptive``) and its
+(Eq. 3.1, Theorems 2, 3, 5 and 6, Eq. 3.5, Eq. 4.3); Algorithm 5
+(``hermitian``); Algorithm 6 (``singlepass``); the toolbox's adaptive range finder (``adaptive``) and its
 SRFT test matrix with FastRandRF (``srft``).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
@@ -27,4 +27,4 @@ from .philox import philox4x32_10, gaussian_matrix  # noqa: F401
 from .randsvd import (  # noqa: F401
     RsvdResult, orth, range_finder, rsvd, sign_normalise,
 )
-from . import adaptive, analysis, srft  # noqa: F401
+from . import adaptive, analysis, hermitian, singlepass, srft  # noqa: F401

@@ -86,6 +86,25 @@ def lowrank_matrix(m: int, n: int, sigma: np.ndarray, seed: int,
     return np.asfortranarray(a)
 
 
+def symmetric_matrix(n: int, lam: np.ndarray, seed: int) -> np.ndarray:
+    """A = U diag(lam) U^T, FP64, column-major: a real symmetric (Hermitian)
+    n x n matrix with the prescribed eigenvalues ``lam`` (any signs) and Haar
+    eigenvectors, so its eigenvalues are known exactly by construction."""
+    r = len(lam)
+    if r > n:
+        raise ValueError("more eigenvalues than n")
+    u = haar_columns(n, r, _rng(seed, _STREAM_U))
+    a = (u * np.asarray(lam, dtype=np.float64)) @ u.T
+    return np.asfortranarray(0.5 * (a + a.T))
+
+
+def signed_spectrum(sigma: np.ndarray, seed: int) -> np.ndarray:
+    """``sigma`` with seeded random signs: an indefinite spectrum with the
+    prescribed magnitudes (the order by magnitude is kept)."""
+    sg = np.where(_rng(seed, _STREAM_SPARSE + 1).uniform(size=len(sigma)) < 0.5, -1.0, 1.0)
+    return np.asarray(sigma, dtype=np.float64) * sg
+
+
 def lowrank_factors(m: int, n: int, sigma: np.ndarray, seed: int):
     """The exact factors (U, sigma, V) of :func:`lowrank_matrix` (no noise)."""
     r = len(sigma)
@@ -184,6 +203,26 @@ def lowrank_matrix_torch(m: int, n: int, sigma: np.ndarray, seed: int, *,
     out = torch.zeros(n, lda, dtype=dtype, device=device)
     out[:, :m] = at.to(dtype)
     return out
+
+
+def symmetric_matrix_torch(n: int, lam: np.ndarray, seed: int, *, device="cuda"):
+    """Build A = U diag(lam) U^T (FP64, n x n, Haar U) on ``device`` with
+    torch; A is symmetric, so its row-major and column-major storage agree.
+    The Gaussians of U are drawn on the CPU from a seeded torch Generator."""
+    import torch
+
+    r = len(lam)
+    g = torch.Generator(device="cpu")
+    g.manual_seed((int(seed) * 1000003 + _STREAM_U) & 0x7FFFFFFFFFFFFFFF)
+    x = torch.randn(n, r, generator=g, dtype=torch.float32).to(device=device, dtype=torch.float64)
+    q, rr = torch.linalg.qr(x, mode="reduced")
+    d = torch.sign(torch.diagonal(rr))
+    d[d == 0] = 1
+    u = q * d
+    lt = torch.as_tensor(np.asarray(lam), dtype=torch.float64, device=device)
+    a = (u * lt) @ u.T
+    a = 0.5 * (a + a.T)
+    return a.contiguous()
 
 
 # ---------------------------------------------------------------------------
