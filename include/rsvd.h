@@ -134,6 +134,23 @@ int rsvd_plan_diagnostics(rsvd_plan_t plan, int* jacobi_sweeps, int* dropped_col
 int rsvd_plan_set_stream(rsvd_plan_t plan, void* cuda_stream);
 
 /*
+ * rsvd_plan_set_wait_limit: the bound, in SM clock cycles (clock64), of every
+ * wait inside the tensor-core passes of a mixed plan (a pipeline stage's
+ * data, a free stage, the accumulator).  0 (the default) means about one
+ * second (2e9 cycles).  A wait that runs past its bound does not hang the
+ * GPU: the pass stops issuing, waits (up to one second) for its own copies and
+ * products in flight, frees its tensor memory, and rsvd_plan_status() then
+ * returns RSVD_ERR_TIMEOUT; the outputs of that call are undefined.  A limit
+ * below about 1e6 cycles polls without blocking and reads the clock on every
+ * poll, so a limit of a few cycles makes the first incomplete wait expire:
+ * that is how the tests exercise this failure path without a GPU fault.
+ * Takes effect for calls enqueued afterwards.  Errors: -1 plan; -2 cycles < 0.
+ * The thesis has no counterpart: this is the failure-detection bound of the
+ * GPU pipeline.
+ */
+int rsvd_plan_set_wait_limit(rsvd_plan_t plan, int64_t cycles);
+
+/*
  * rsvd_set_tile_scales (RSVD_FP8E4M3 plans): the scales of A.  Element (i, j)
  * of A is the E4M3 value of code A[i + j*lda] times scales[I + J*lds] with
  * I = i / 128, J = j / 128; `scales` is a DEVICE array of rows x cols FP32
@@ -230,6 +247,29 @@ int rsvd_solve_algorithm(rsvd_plan_t plan, int algorithm, const void* A, int64_t
 int rsvd_solve_singlepass(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t lda,
                           int k, int p, uint64_t seed, void* U, int64_t ldu, double* S,
                           void* VT, int64_t ldvt);
+
+/*
+ * rsvd_solve_hermitian: rank-k randomized eigendecomposition A ~ U diag(D) U^T
+ * of a real symmetric (Hermitian) n x n matrix by Algorithm 5 ("Single-Pass
+ * Randomized SVD for a Hermitian Matrix", Section 3.4.1; Eqs. 3.6-3.13).  A
+ * is read by exactly one product, Y = A Omega (Omega n x (k+p) from Philox
+ * stream 0 of `seed`, as in rsvd_solve), and never again.  Q is the k
+ * dominant left singular vectors of Y; C (k x k) is the least-squares
+ * solution of C (Q^T Omega) = Q^T Y (Eq. 3.13; an overdetermined system of
+ * k+p equations per row of C); its symmetric part (C + C^T)/2 is decomposed
+ * as U^ diag(D) U^^T and U = Q U^.  Only the upper and lower triangles' sum
+ * of A enters through Y, so A must be symmetric: the library does not check.
+ * Outputs (device, caller-owned): U n x k column-major (ldu), each column's
+ * largest-magnitude entry positive; D[k] the eigenvalues, FP64, ordered by
+ * decreasing magnitude (A may be indefinite).  Eigenvalues of equal
+ * magnitude and opposite sign make the eigenvectors of that pair arbitrary
+ * within their 2-D space.  Plain (FP64) plans with m_max, n_max >= n.
+ * Argument errors: -1 plan; -2 A NULL; -3 n; -4 lda < n; -5 k; -6 p (or
+ * k+p > n); -8 U NULL; -9 ldu; -10 D NULL.  RSVD_ERR_WORKSPACE as rsvd_solve;
+ * RSVD_ERR_UNSUPPORTED for mixed or batch plans.
+ */
+int rsvd_solve_hermitian(rsvd_plan_t plan, const void* A, int64_t n, int64_t lda, int k, int p,
+                         uint64_t seed, void* U, int64_t ldu, double* D);
 
 /*
  * rsvd_range_adaptive: the adaptive randomized range finder ("Adaptive_randRF"

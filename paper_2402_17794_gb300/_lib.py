@@ -30,6 +30,7 @@ SIGNATURES = {
     "rsvd_set_workspace": (c_int, [c_void_p, c_void_p, c_size_t]),
     "rsvd_plan_status": (c_int, [c_void_p]),
     "rsvd_plan_set_stream": (c_int, [c_void_p, c_void_p]),
+    "rsvd_plan_set_wait_limit": (c_int, [c_void_p, c_int64]),
     "rsvd_set_tile_scales": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_int64]),
     "rsvd_plan_diagnostics": (c_int, [c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
     "rsvd_plan_destroy": (c_int, [c_void_p]),
@@ -42,6 +43,8 @@ SIGNATURES = {
                                      c_int64]),
     "rsvd_solve_singlepass": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_int64, c_int, c_int,
                                       c_uint64, c_void_p, c_int64, c_void_p, c_void_p, c_int64]),
+    "rsvd_solve_hermitian": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_int, c_int,
+                                     c_uint64, c_void_p, c_int64, c_void_p]),
     "rsvd_range_adaptive": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_int64, ctypes.c_double,
                                     c_int, c_int, c_uint64, c_void_p, c_int64,
                                     ctypes.POINTER(c_int)]),

@@ -184,6 +184,13 @@ int rsvd_plan_set_stream(rsvd_plan_t plan, void* cuda_stream) {
   return RSVD_OK;
 }
 
+int rsvd_plan_set_wait_limit(rsvd_plan_t plan, int64_t cycles) {
+  if (!plan) return -1;
+  if (cycles < 0) return -2;
+  plan->wait_cycles = (long long)cycles;
+  return RSVD_OK;
+}
+
 int rsvd_set_tile_scales(rsvd_plan_t plan, const float* scales, int64_t rows, int64_t cols,
                          int64_t lds) {
   if (!plan) return -1;
@@ -346,6 +353,24 @@ int rsvd_solve_singlepass(rsvd_plan_t plan, const void* A, int64_t m, int64_t n,
   if (plan->mode != RSVD_MODE_PLAIN || plan->batched) return RSVD_ERR_UNSUPPORTED;
   return solve_singlepass(plan, (const double*)A, m, n, lda, k, p, seed, (double*)U, ldu, S,
                           (double*)VT, ldvt);
+}
+
+int rsvd_solve_hermitian(rsvd_plan_t plan, const void* A, int64_t n, int64_t lda, int k, int p,
+                         uint64_t seed, void* U, int64_t ldu, double* D) {
+  if (!plan) return -1;
+  if (!A) return -2;
+  if (n < 1) return -3;
+  if (lda < n) return -4;
+  if (k < 1) return -5;
+  if (p < 0) return -6;
+  if (k + p > n) return -6;
+  if (!U) return -8;
+  if (ldu < n) return -9;
+  if (!D) return -10;
+  if (!ready(plan) || n > plan->m_max || n > plan->n_max || k + p > plan->l_max)
+    return RSVD_ERR_WORKSPACE;
+  if (plan->mode != RSVD_MODE_PLAIN || plan->batched) return RSVD_ERR_UNSUPPORTED;
+  return solve_hermitian(plan, (const double*)A, n, lda, k, p, seed, (double*)U, ldu, D);
 }
 
 namespace {

@@ -76,6 +76,7 @@ struct rsvd_plan_s {
   rsvd::BatchLayout* batch_lay;   // owned
   void* h_ctx;                    // pinned staging for the context table
   cudaEvent_t ctx_event;          // marks the table copy of the last batched solve
+  long long wait_cycles;          // rsvd_plan_set_wait_limit (0: the default bound)
 };
 
 namespace rsvd {
@@ -152,5 +153,11 @@ cudaError_t launch_jacobi_svd(const T* M, int l, int64_t ldm, T* sig, T* Um, int
 template <typename T>
 cudaError_t launch_finalize(T* U, int64_t m, int64_t ldu, int k, const T* Vk, int64_t n, T* VT,
                             int64_t ldvt, const T* sig, double* S, T* sign_work, cudaStream_t st);
+
+// Flips columns of U (m x k, ldu) so each column's largest-|.| entry is
+// positive (lowest index on ties).
+template <typename T>
+cudaError_t launch_sign_columns(T* U, int64_t m, int64_t ldu, int k, T* sign_work,
+                                cudaStream_t st);
 
 }  // namespace rsvd

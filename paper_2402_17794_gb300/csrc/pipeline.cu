@@ -85,6 +85,7 @@ int mixed_pass(rsvd_plan_t P, bool ax, const void* A, int64_t m, int64_t n, int6
   c.fp8 = P->dtype == RSVD_FP8E4M3;
   c.scales = P->scales;
   c.lds = P->lds;
+  c.wait_cycles = P->wait_cycles;
   rc = launch_apass_bf16(c, P->num_sms, &dstatus(P)->flags, P->stream);
   if (rc != RSVD_ERR_UNSUPPORTED || slices == 1) return rc;
   // the slices do not fit two shared-memory stages at this l: run the leading
@@ -400,6 +401,7 @@ int mixed_apply(rsvd_plan_t P, const void* A, int64_t m, int64_t n, int64_t lda,
   c.fp8 = P->dtype == RSVD_FP8E4M3;
   c.scales = P->scales;
   c.lds = P->lds;
+  c.wait_cycles = P->wait_cycles;
   return launch_apass_bf16(c, P->num_sms, &dstatus(P)->flags, P->stream);
 }
 

@@ -87,6 +87,11 @@ int solve_singlepass(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64
                      int p, uint64_t seed, double* U, int64_t ldu, double* S, double* VT,
                      int64_t ldvt);
 
+// Algorithm 5 (single-pass randomized EVD of a symmetric matrix), FP64:
+// U (n x k, ldu) and the eigenvalues D (k, by decreasing magnitude).
+int solve_hermitian(rsvd_plan_t P, const double* A, int64_t n, int64_t lda, int k, int p,
+                    uint64_t seed, double* U, int64_t ldu, double* D);
+
 // Adaptive randomized range finder (Halko, Martinsson, Tropp 2011, Algorithm
 // 4.2), FP64, blocked: Q (ldq) gets rank <= l_cap orthonormal columns.
 // Synchronous.  RSVD_OK when the tolerance test passed, RSVD_ERR_NOT_REACHED

@@ -87,6 +87,31 @@ __global__ void sylvester_scale_kernel(T* __restrict__ G, int k, const T* __rest
   G[t] = G[t] / (la[i] + lb[j]);
 }
 
+// S = (C + C^T) / 2 (k x k, ld k): the Hermitian part of the solved C.
+template <typename T>
+__global__ void symmetrise_kernel(const T* __restrict__ C, int k, T* __restrict__ S) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= k * k) return;
+  const int i = t % k, j = t / k;
+  S[t] = T(0.5) * (C[i + j * k] + C[j + i * k]);
+}
+
+// For a symmetric S = Uh diag(sig) Vh^T (one-sided Jacobi), column j of Uh is
+// an eigenvector with eigenvalue sig_j when Uh_j = Vh_j and -sig_j when
+// Uh_j = -Vh_j: D_j = sig_j * sign(Uh_j . Vh_j).  One warp per column.
+template <typename T>
+__global__ void eig_sign_kernel(const T* __restrict__ Uh, const T* __restrict__ Vh, int k,
+                                const T* __restrict__ sig, double* __restrict__ D) {
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (j >= k) return;
+  T d = T(0);
+  for (int i = lane; i < k; i += 32) d += Uh[i + (int64_t)j * k] * Vh[i + (int64_t)j * k];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+  if (lane == 0) D[j] = (double)(d < T(0) ? -sig[j] : sig[j]);
+}
+
 template <typename T>
 cudaError_t small_gemm(const T* A, int64_t lda, bool ta, const T* B, int64_t ldb, bool tb, T* C,
                        int64_t ldc, int M, int N, int K, bool accumulate, cudaStream_t st) {
@@ -157,6 +182,71 @@ int solve_singlepass(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64
   if ((rc = gemm<T>(P, W.y, m, false, X1, l, U, ldu, m, l, k))) return rc;
   if ((rc = gemm<T>(P, W.z, n, false, X2, l, W.qb, n, n, l, k))) return rc;
   RSVD_CK(launch_finalize<T>(U, m, ldu, k, W.qb, n, VT, ldvt, sig, S, W.sign, st));
+  return RSVD_OK;
+}
+
+}  // namespace rsvd
+
+namespace rsvd {
+
+// Algorithm 5 (Section 3.4.1), FP64, A symmetric n x n, l = k + p:
+//   1-2. Omega (n x l, Philox stream 0); Y = A Omega       (the only pass over A)
+//   3.   Y = Q1 R (CholeskyQR2), R = Ur diag(s) W^T: Q = Q1 Ur_k, the k
+//        dominant left singular vectors of Y (never formed)
+//   4.   C (k x k) least squares of C N = H with N = Q^T Omega = Ur_k^T (Q1^T
+//        Omega) and H = Q^T Y = Ur_k^T R (k x l each): the normal equations
+//        C (N N^T) = H N^T, with N N^T = Vb diag(lb) Vb^T (one-sided Jacobi
+//        of the SPD matrix), C = (H N^T) Vb diag(1/lb) Vb^T
+//   5.   S = (C + C^T)/2 = Uh diag(sig) Vh^T, eigenvalues D_j = +-sig_j
+//   6.   U = Q1 (Ur_k Uh), each column's largest-|.| entry made positive
+int solve_hermitian(rsvd_plan_t P, const double* A, int64_t n, int64_t lda, int k, int p,
+                    uint64_t seed, double* U, int64_t ldu, double* D) {
+  using T = double;
+  const int l = k + p;
+  Work<T> W = work_of<T>(P);
+  cudaStream_t st = P->stream;
+  DeviceStatus* status = dstatus(P);
+  char* base = P->ws + P->lay.sp;
+  const size_t ss = P->lay.small_stride;
+  auto slot = [&](int i) { return (T*)(base + (size_t)i * ss); };
+  T *R = slot(0), *Ur = slot(1), *E = slot(2), *Nt = slot(3), *Ht = slot(4), *F = slot(5);
+  T *B1 = slot(6), *Vb = slot(7), *G = slot(8), *C = slot(9), *Cs = slot(10), *Uh = slot(11);
+  T *Vh = slot(12), *X1 = slot(13);
+  T* vec = slot(kSinglePassSlots);
+  T *sr = vec, *la = vec + l, *lb = vec + 2 * l, *sig = vec + 3 * l;
+  int rc;
+
+  // 1-2
+  RSVD_CK(launch_gaussian(n, l, seed, 0u, RSVD_F64, W.om, n, st));
+  if ((rc = gemm<T>(P, A, lda, false, W.om, n, W.y, n, n, n, l))) return rc;
+  // 3
+  if ((rc = orth<T>(P, W.y, n, l, n, W.y, n, R, false))) return rc;
+  RSVD_CK(launch_jacobi_svd<T>(R, l, l, sr, Ur, l, nullptr, l, nullptr, W.jw, status, st));
+  // 4: E = Omega^T Q1 (l x l); N^T = E Ur_k (l x k); H^T = R^T Ur_k (l x k)
+  if ((rc = gemm<T>(P, W.om, n, true, W.y, n, E, l, l, n, l))) return rc;
+  RSVD_CK(small_gemm<T>(E, l, false, Ur, l, false, Nt, l, l, k, l, false, st));
+  RSVD_CK(small_gemm<T>(R, l, true, Ur, l, false, Ht, l, l, k, l, false, st));
+  RSVD_CK(small_gemm<T>(Ht, l, true, Nt, l, false, F, k, k, k, l, false, st));    // H N^T
+  RSVD_CK(small_gemm<T>(Nt, l, true, Nt, l, false, B1, k, k, k, l, false, st));   // N N^T
+  RSVD_CK(launch_jacobi_svd<T>(B1, k, k, lb, Vb, k, nullptr, k, nullptr, W.jw, status, st));
+  RSVD_CK(small_gemm<T>(F, k, false, Vb, k, false, G, k, k, k, k, false, st));    // F Vb
+  RSVD_CK(cudaMemsetAsync(la, 0, sizeof(T) * (size_t)k, st));
+  sylvester_scale_kernel<T><<<(k * k + 255) / 256, 256, 0, st>>>(G, k, la, lb);   // / lb_j
+  note_launch();
+  RSVD_CK(cudaGetLastError());
+  RSVD_CK(small_gemm<T>(G, k, false, Vb, k, true, C, k, k, k, k, false, st));     // C
+  // 5
+  symmetrise_kernel<T><<<(k * k + 255) / 256, 256, 0, st>>>(C, k, Cs);
+  note_launch();
+  RSVD_CK(cudaGetLastError());
+  RSVD_CK(launch_jacobi_svd<T>(Cs, k, k, sig, Uh, k, Vh, k, nullptr, W.jw, status, st));
+  eig_sign_kernel<T><<<(k + 7) / 8, 256, 0, st>>>(Uh, Vh, k, sig, D);
+  note_launch();
+  RSVD_CK(cudaGetLastError());
+  // 6
+  RSVD_CK(small_gemm<T>(Ur, l, false, Uh, k, false, X1, l, l, k, k, false, st));
+  if ((rc = gemm<T>(P, W.y, n, false, X1, l, U, ldu, n, l, k))) return rc;
+  RSVD_CK(launch_sign_columns<T>(U, n, ldu, k, W.sign, st));
   return RSVD_OK;
 }
 

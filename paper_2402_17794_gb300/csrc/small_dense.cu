@@ -240,6 +240,14 @@ cudaError_t launch_finalize(T* U, int64_t m, int64_t ldu, int k, const T* Vk, in
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_sign_columns(T* U, int64_t m, int64_t ldu, int k, T* sign_work,
+                                cudaStream_t st) {
+  sign_kernel<T><<<k, 1024, 0, st>>>(U, m, ldu, sign_work);
+  note_launch();
+  return cudaGetLastError();
+}
+
 #define RSVD_INSTANTIATE_SMALL(T)                                                              \
   template cudaError_t launch_chol_inv<T>(const T*, int64_t, int, T*, T*, T*, DeviceStatus*,   \
                                           cudaStream_t);                                       \
@@ -248,7 +256,8 @@ cudaError_t launch_finalize(T* U, int64_t m, int64_t ldu, int k, const T* Vk, in
   template cudaError_t launch_jacobi_svd<T>(const T*, int, int64_t, T*, T*, int64_t, T*,       \
                                             int64_t, T*, T*, DeviceStatus*, cudaStream_t);     \
   template cudaError_t launch_finalize<T>(T*, int64_t, int64_t, int, const T*, int64_t, T*,    \
-                                          int64_t, const T*, double*, T*, cudaStream_t);
+                                          int64_t, const T*, double*, T*, cudaStream_t);       \
+  template cudaError_t launch_sign_columns<T>(T*, int64_t, int64_t, int, T*, cudaStream_t);
 RSVD_INSTANTIATE_SMALL(double)
 RSVD_INSTANTIATE_SMALL(float)
 

@@ -26,6 +26,7 @@ struct ApassCall {
   bool fp8 = false;
   const float* scales = nullptr;
   int64_t lds = 0;
+  long long wait_cycles = 0;  // bound of each pipeline wait in clock64 cycles; 0: ~1 s
 };
 
 // Floats of partial-slot workspace a pass with `l` output columns needs.

@@ -23,9 +23,10 @@
 //    the TMEM accumulator and one lane issues tcgen05.mma (M=128, N<=256 per
 //    instruction, K=16, FP32 accumulate in TMEM) and tcgen05.commit; warps
 //    2-5 drain the accumulator with tcgen05.ld and store FP32 results.
-//  * Every mbarrier wait is bounded (about one second of clock64); on expiry
-//    the CTA records RSVD_ERR_TIMEOUT, stops issuing, drains what it issued
-//    and frees its TMEM before returning.
+//  * Every mbarrier wait is bounded (about one second of clock64 by default,
+//    the plan's wait limit if set); on expiry the CTA records
+//    RSVD_ERR_TIMEOUT, stops issuing, drains what it issued (those waits keep
+//    the one-second bound) and frees its TMEM before returning.
 //  * FP8 A (E4M3, one power-of-two scale per 128 x 128 tile): TMA brings the
 //    raw 8-bit tile into a staging buffer of the stage; eight more warps turn
 //    it into the same swizzled BF16 operand the TMA would have written, with
@@ -51,7 +52,8 @@ constexpr int A_STAGE_BYTES = BM * BK * 2;
 constexpr int THREADS = 192;          // 6 warps
 constexpr int THREADS_F8 = 448;       // + 8 converter warps for FP8 A
 constexpr int CONV_WARPS = 8;
-constexpr long long kWaitCycles = 2000000000LL;   // ~1 s at 2 GHz
+constexpr long long kWaitCycles = 2000000000LL;   // ~1 s at 2 GHz: default bound of a wait
+constexpr long long kShortWait = 1LL << 20;       // limits below this poll without blocking
 
 // ---------------------------------------------------------------------------
 // PTX wrappers
@@ -87,15 +89,41 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait; returns false (and raises the CTA's abort flag) on expiry or
-// when another role already aborted.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait (limit in clock64 cycles); returns false (and raises the CTA's
+// abort flag) on expiry or when another role already aborted.  Limits below
+// kShortWait poll with the non-blocking test_wait and read the clock on every
+// poll, so even a limit of a few cycles expires on the first wait that is
+// not already complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort,
+                                          long long limit) {
   long long t0 = clock64();
+  if (limit < kShortWait) {
+    for (;;) {
+      if (mbar_test_wait(bar, parity)) return true;
+      if (*abort) return false;
+      if (clock64() - t0 > limit) {
+        *abort = 1;
+        return false;
+      }
+    }
+  }
   for (uint32_t it = 0;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((it & 255) == 255) {
       if (*abort) return false;
-      if (clock64() - t0 > kWaitCycles) {
+      if (clock64() - t0 > limit) {
         *abort = 1;
         return false;
       }
@@ -266,6 +294,7 @@ struct ApassArgs {
   const float* scales;  // FP8 A: tile scales, tile (I, J) at scales[I + J * lds]
   int64_t lds;
   int sc_rows, sc_cols; // tiles of A along m and n
+  long long wait_cycles;  // bound of every pipeline wait (the drain waits keep kWaitCycles)
 };
 
 __device__ __forceinline__ int64_t range_begin(int64_t total, int c, int g) {
@@ -331,7 +360,7 @@ apass_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       int kb = (int)(g0 - t * args.kt);
       int64_t issued = 0;
       for (int64_t g = g0; g < g1; ++g) {
-        if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) break;
+        if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, args.wait_cycles)) break;
         uint8_t* a_s = tiles + (size_t)s * stage_bytes;
         uint8_t* x_s = a_s + A_BYTES;
         mbar_expect_tx(&full[s], (uint32_t)(STG_BYTES + (F8 ? x_stage_bytes : stage_bytes)));
@@ -390,11 +419,11 @@ apass_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         const bool seg_last = (g == g1 - 1) || kb == args.kt - 1;
         if (seg_first && seg > 0) {
           // the epilogue must have drained the previous segment
-          if (!mbar_wait(acc_empty, (uint32_t)((seg - 1) & 1), abort_flag)) { ok = false; break; }
+          if (!mbar_wait(acc_empty, (uint32_t)((seg - 1) & 1), abort_flag, args.wait_cycles)) { ok = false; break; }
           tc_fence_after();
         }
-        if (!mbar_wait(&full[s], ph, abort_flag)) { ok = false; break; }
-        if (F8 && !mbar_wait(&conv[s], ph, abort_flag)) { ok = false; break; }
+        if (!mbar_wait(&full[s], ph, abort_flag, args.wait_cycles)) { ok = false; break; }
+        if (F8 && !mbar_wait(&conv[s], ph, abort_flag, args.wait_cycles)) { ok = false; break; }
         tc_fence_after();
         const uint32_t a_base = tiles_base + (uint32_t)s * (uint32_t)stage_bytes;
         const uint32_t x_base = a_base + A_BYTES;
@@ -465,7 +494,7 @@ apass_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       int64_t t = g0 / args.kt;
       int kb = (int)(g0 - t * args.kt);
       for (int64_t g = g0; g < g1; ++g) {
-        if (!mbar_wait(&full[s], ph, abort_flag)) break;
+        if (!mbar_wait(&full[s], ph, abort_flag, args.wait_cycles)) break;
         uint8_t* a_s = tiles + (size_t)s * stage_bytes;
         const uint8_t* stg = a_s + A_BYTES + x_stage_bytes;
         // scales of the stage's MT tiles: AX walks 128-row tiles I of A at
@@ -514,7 +543,7 @@ apass_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       const int kb0 = (int)(g - t * args.kt);
       const int64_t gend = (g1 < (t + 1) * args.kt) ? g1 : (t + 1) * args.kt;
       const bool full_tile = (kb0 == 0) && (gend - t * args.kt == args.kt);
-      if (!mbar_wait(acc_full, (uint32_t)(seg & 1), abort_flag)) break;
+      if (!mbar_wait(acc_full, (uint32_t)(seg & 1), abort_flag, args.wait_cycles)) break;
       tc_fence_after();
       float* dst;
       int64_t ld;
@@ -675,6 +704,7 @@ int launch_apass_bf16(const ApassCall& c, int num_sms, int* status, cudaStream_t
   a.lds = c.lds;
   a.sc_rows = (int)((c.m + 127) / 128);
   a.sc_cols = (int)((c.n + 127) / 128);
+  a.wait_cycles = c.wait_cycles > 0 ? c.wait_cycles : kWaitCycles;
   if (c.part_floats < (size_t)grid * 2 * bmt * c.l) return RSVD_ERR_WORKSPACE;
   if ((int64_t)kt * grid / total + 2 > 32) return RSVD_ERR_UNSUPPORTED;
 #define RSVD_LAUNCH_APASS(AXV, MTV, F8V)                                                     \

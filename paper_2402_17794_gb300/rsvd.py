@@ -109,6 +109,10 @@ def rsvd_plan_set_stream(plan, stream=None) -> None:
     _check(_lib.load().rsvd_plan_set_stream(plan, _stream_handle(stream)), "rsvd_plan_set_stream")
 
 
+def rsvd_plan_set_wait_limit(plan, cycles) -> int:
+    return _lib.load().rsvd_plan_set_wait_limit(plan, int(cycles))
+
+
 def rsvd_set_tile_scales(plan, scales, rows, cols, lds) -> int:
     return _lib.load().rsvd_set_tile_scales(plan, _ptr(scales), rows, cols, lds)
 
@@ -169,6 +173,11 @@ def rsvd_srft_sketch(plan, A, m, n, lda, l, seed, Y, ldy) -> int:
 def rsvd_solve_singlepass(plan, A, m, n, lda, k, p, seed, U, ldu, S, VT, ldvt) -> int:
     return _lib.load().rsvd_solve_singlepass(plan, _ptr(A), m, n, lda, k, p, seed, _ptr(U), ldu,
                                              _ptr(S), _ptr(VT), ldvt)
+
+
+def rsvd_solve_hermitian(plan, A, n, lda, k, p, seed, U, ldu, D) -> int:
+    return _lib.load().rsvd_solve_hermitian(plan, _ptr(A), n, lda, k, p, seed, _ptr(U), ldu,
+                                            _ptr(D))
 
 
 def rsvd_gaussian(plan, n, l, seed, stream_id, out_dtype, out, ldo) -> int:
@@ -322,6 +331,17 @@ class Plan:
         _check(rsvd_solve_singlepass(self.handle, A, m, n, lda, k, p, seed, U, m, S, VT, k),
                "rsvd_solve_singlepass")
         return U, S, VT
+
+    def solve_hermitian(self, A, n, k, p, seed, lda=None):
+        """Algorithm 5 on a plain plan (A symmetric n x n): (U, D) with U
+        (k, n) holding the column-major n x k eigenvectors and D the k
+        eigenvalues by decreasing magnitude; enqueued only."""
+        lda = lda or A.shape[1]
+        U = torch.empty(k, n, dtype=torch.float64, device=A.device)
+        D = torch.empty(k, dtype=torch.float64, device=A.device)
+        _check(rsvd_solve_hermitian(self.handle, A, n, lda, k, p, seed, U, n, D),
+               "rsvd_solve_hermitian")
+        return U, D
 
     def range_adaptive(self, A, m, n, eps, r, l_cap, seed, lda=None):
         """Adaptive range finder on a plain plan: (Q (rank, m) column-major,

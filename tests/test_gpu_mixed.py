@@ -149,3 +149,35 @@ def test_mixed_solve_full_size_bf16():
     r_gpu = analysis.lowrank_residual(A16, u, s, vt)
     r_orc = analysis.lowrank_residual(A16, ref.U, ref.S, ref.Vt)
     assert r_gpu <= RESID_RATIO * r_orc, (r_gpu, r_orc)
+
+
+@pytest.mark.parametrize("ax", [True, False])
+def test_bounded_wait_expires_and_plan_recovers(ax):
+    """Failure detection without a GPU fault: a wait limit of a few cycles
+    makes the first incomplete pipeline wait of a tensor-core pass expire.
+    The pass drains what it issued, frees its tensor memory and reports
+    RSVD_ERR_TIMEOUT through rsvd_plan_status(); with the default limit
+    restored, a full solve on the same plan meets the oracle."""
+    m, n, l = 4096, 2048, 48
+    rng = np.random.default_rng(17)
+    dA, _ = _bf16_matrix(rng.standard_normal((m, n)))
+    rows = n if ax else m
+    dX = torch.from_numpy(rng.standard_normal((l, rows))).to(torch.bfloat16).cuda()
+    out_rows = m if ax else n
+    Y = torch.zeros(l, out_rows, dtype=torch.float32, device="cuda")
+    plan = R.Plan(m, n, l, a_dtype=R.BF16, mode=R.MIXED)
+    assert R.rsvd_plan_set_wait_limit(plan.handle, -1) == -2
+    assert R.rsvd_plan_set_wait_limit(plan.handle, 8) == 0
+    f = R.rsvd_apply_a if ax else R.rsvd_apply_at
+    assert f(plan.handle, dA, m, n, m, dX, rows, l, Y, out_rows) == 0
+    assert plan.status() == 3          # RSVD_ERR_TIMEOUT
+    assert plan.status() == 0          # reading the status clears it
+    assert R.rsvd_plan_set_wait_limit(plan.handle, 0) == 0
+    A = syn.lowrank_matrix(m, n, syn.spectrum("exp", 400, r=30.0), seed=21)
+    dA2, A16 = _bf16_matrix(A)
+    k, p, q, seed = 32, 16, 1, 4
+    ref = oracle.rsvd(A16, k, p, q + 1, seed)
+    U, S, VT = plan.solve(dA2, m, n, k, p, q, seed)
+    _ok(plan)
+    rel = np.abs(S.cpu().numpy() - ref.S) / ref.S
+    assert rel.max() <= SIG_RTOL, rel.max()
