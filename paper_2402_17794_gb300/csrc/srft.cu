@@ -152,25 +152,110 @@ __global__ void realify_rh_kernel(const double* __restrict__ G2, int l, double* 
   }
 }
 
-// C (2l x 2k, ld 2l) = [[X_re, X_im], [-X_im, X_re]] for the complex l x k
-// matrix whose column i is column 2i of the realified singular vectors X
-// (2l x 2l, ld 2l): X[:, 2i] = [Re x_i ; Im x_i].
-__global__ void pick_pairs_kernel(const double* __restrict__ X, int l, int k,
-                                  double* __restrict__ C) {
+// The complex singular triplets of M (l x l) from the real SVD of its block
+// realification M_R = Xu diag(sig) Xv^T (2l x 2l, ld 2l).  Every singular
+// value of M appears twice in M_R, and the two real columns of a pair span
+// {z, i z} for a complex singular vector z (column [Re z ; Im z]).  When
+// singular values repeat, a real column may instead be any unit vector of
+// the combined subspace, so the complex vectors are picked by structure, not
+// by position: the real columns are taken in order (sig descending), each
+// read as a complex vector x = Xu[:l, c] + i Xu[l:, c] and orthogonalised
+// (complex classical Gram-Schmidt, two passes) against the vectors already
+// accepted; x is accepted when more than half its unit norm remains (the
+// second column of a pair, i z up to rounding, leaves none).  The matching
+// right vector y = Xv[:l, c] + i Xv[l:, c] takes the same complex
+// coefficients: M y_c = sig_c x_c, and within one value of sig the same
+// combination maps the y's to the x's; across distinct values the
+// coefficients are rounding-sized.  Outputs: Cu, Cv (2l x 2k, ld 2l) =
+// [[X_re, X_im], [-X_im, X_re]] of the accepted vectors, sig_out[k].
+// One block; dynamic shared memory (4 l + 2 k + 32) doubles.
+__global__ void select_pairs_kernel(const double* __restrict__ Xu, const double* __restrict__ Xv,
+                                    const double* __restrict__ sig, int l, int k,
+                                    double* __restrict__ Cu, double* __restrict__ Cv,
+                                    double* __restrict__ sig_out) {
   const int L = 2 * l;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < l * k; t += gridDim.x * blockDim.x) {
-    const int r = t % l, i = t / l;
-    const double xr = X[r + (2 * i) * L], xi = X[(l + r) + (2 * i) * L];
-    C[r + i * L] = xr;
-    C[r + (k + i) * L] = xi;
-    C[(l + r) + i * L] = -xi;
-    C[(l + r) + (k + i) * L] = xr;
+  extern __shared__ double sh[];
+  double *xr = sh, *xi = xr + l, *yr = xi + l, *yi = yr + l, *ar = yi + l, *ai = ar + k;
+  double* red = ai + k;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  int count = 0;
+  for (int c = 0; c < L && count < k; ++c) {
+    for (int r = tid; r < l; r += blockDim.x) {
+      xr[r] = Xu[r + (int64_t)c * L];
+      xi[r] = Xu[l + r + (int64_t)c * L];
+      yr[r] = Xv[r + (int64_t)c * L];
+      yi[r] = Xv[l + r + (int64_t)c * L];
+    }
+    __syncthreads();
+    for (int pass = 0; pass < 2 && count > 0; ++pass) {
+      for (int j = warp; j < count; j += nw) {   // alpha_j = z_j^H x
+        double sr = 0.0, si = 0.0;
+        for (int r = lane; r < l; r += 32) {
+          const double zr = Cu[r + (int64_t)j * L], zi = Cu[r + (int64_t)(k + j) * L];
+          sr += zr * xr[r] + zi * xi[r];
+          si += zr * xi[r] - zi * xr[r];
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+          sr += __shfl_xor_sync(0xffffffffu, sr, o);
+          si += __shfl_xor_sync(0xffffffffu, si, o);
+        }
+        if (lane == 0) {
+          ar[j] = sr;
+          ai[j] = si;
+        }
+      }
+      __syncthreads();
+      for (int r = tid; r < l; r += blockDim.x) {   // x -= sum alpha_j z_j, y -= sum alpha_j w_j
+        double pxr = xr[r], pxi = xi[r], pyr = yr[r], pyi = yi[r];
+        for (int j = 0; j < count; ++j) {
+          const double a_r = ar[j], a_i = ai[j];
+          const double zr = Cu[r + (int64_t)j * L], zi = Cu[r + (int64_t)(k + j) * L];
+          const double wr = Cv[r + (int64_t)j * L], wi = Cv[r + (int64_t)(k + j) * L];
+          pxr -= a_r * zr - a_i * zi;
+          pxi -= a_r * zi + a_i * zr;
+          pyr -= a_r * wr - a_i * wi;
+          pyi -= a_r * wi + a_i * wr;
+        }
+        xr[r] = pxr;
+        xi[r] = pxi;
+        yr[r] = pyr;
+        yi[r] = pyi;
+      }
+      __syncthreads();
+    }
+    double s2 = 0.0;
+    for (int r = tid; r < l; r += blockDim.x) s2 += xr[r] * xr[r] + xi[r] * xi[r];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    if (lane == 0) red[warp] = s2;
+    __syncthreads();
+    double tot = 0.0;
+    for (int w = 0; w < nw; ++w) tot += red[w];
+    if (tot > 0.25) {   // residual norm above 1/2: a new complex direction
+      const double inv = 1.0 / sqrt(tot);
+      for (int r = tid; r < l; r += blockDim.x) {
+        const double a = xr[r] * inv, b = xi[r] * inv, e = yr[r] * inv, f = yi[r] * inv;
+        Cu[r + (int64_t)count * L] = a;
+        Cu[r + (int64_t)(k + count) * L] = b;
+        Cu[(l + r) + (int64_t)count * L] = -b;
+        Cu[(l + r) + (int64_t)(k + count) * L] = a;
+        Cv[r + (int64_t)count * L] = e;
+        Cv[r + (int64_t)(k + count) * L] = f;
+        Cv[(l + r) + (int64_t)count * L] = -f;
+        Cv[(l + r) + (int64_t)(k + count) * L] = e;
+      }
+      if (tid == 0) sig_out[count] = sig[c];
+      ++count;
+    }
+    __syncthreads();
   }
 }
 
 // One block per triplet i: the phase that makes u_i's largest-magnitude entry
 // (lowest row on ties) real and positive is removed from u_i and v_i; then
-// V^H's row i is written planar ([Re V^H | Im V^H], ld ldvt) and S_i = sig_{2i}.
+// V^H's row i is written planar ([Re V^H | Im V^H], ld ldvt) and S_i = sig_i
+// (the singular values of the selected pairs).
 // U: m x 2k planar (ld ldu), V: n x 2k planar (ld n).
 __global__ void finalize_complex_kernel(double* __restrict__ U, int64_t m, int64_t ldu, int k,
                                         const double* __restrict__ V, int64_t n,
@@ -219,7 +304,7 @@ __global__ void finalize_complex_kernel(double* __restrict__ U, int64_t m, int64
     VT[i + j * ldvt] = pr * vr + pi * vi;
     VT[i + (n + j) * ldvt] = pi * vr - pr * vi;
   }
-  if (threadIdx.x == 0) S[i] = sig[2 * i];
+  if (threadIdx.x == 0) S[i] = sig[i];
 }
 
 }  // namespace
@@ -307,22 +392,20 @@ int solve_srft(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t lda
   if ((rc = orth_complex(P, W.z, n, l, n, W.qb, n))) return rc;
   if ((rc = gemm<double>(P, W.qb, n, true, W.z, n, W.G, L, L, n, L))) return rc;
   // R_B^H = U~ S W^H through the realified 2l x 2l matrix: each singular
-  // value appears twice, and column 2i of either factor is [Re x_i ; Im x_i]
+  // value appears twice; the complex triplets are selected by structure
   realify_rh_kernel<<<(L * L + 255) / 256, 256, 0, st>>>(W.G, l, W.Mt);
   note_launch();
   RSVD_CK(cudaGetLastError());
   RSVD_CK(launch_jacobi_svd<double>(W.Mt, L, L, W.sig, W.Um, L, W.Vm, L, nullptr, W.jw, dstatus(P),
                                     st));
-  pick_pairs_kernel<<<(l * k + 255) / 256, 256, 0, st>>>(W.Um, l, k, W.R1);
-  note_launch();
-  RSVD_CK(cudaGetLastError());
-  pick_pairs_kernel<<<(l * k + 255) / 256, 256, 0, st>>>(W.Vm, l, k, W.R2);
+  const size_t sel_smem = (size_t)(4 * l + 2 * k + 32) * sizeof(double);
+  select_pairs_kernel<<<1, 256, sel_smem, st>>>(W.Um, W.Vm, W.sig, l, k, W.R1, W.R2, W.sign);
   note_launch();
   RSVD_CK(cudaGetLastError());
   // U = Q U~ (into U, planar), V = Q_B W (into W.tmp, planar)
   if ((rc = gemm<double>(P, W.qm, m, false, W.R1, L, U, ldu, m, L, 2 * k))) return rc;
   if ((rc = gemm<double>(P, W.qb, n, false, W.R2, L, W.tmp, n, n, L, 2 * k))) return rc;
-  finalize_complex_kernel<<<k, 256, 0, st>>>(U, m, ldu, k, W.tmp, n, W.sig, S, VT, ldvt);
+  finalize_complex_kernel<<<k, 256, 0, st>>>(U, m, ldu, k, W.tmp, n, W.sign, S, VT, ldvt);
   note_launch();
   RSVD_CK(cudaGetLastError());
   return RSVD_OK;

@@ -134,3 +134,32 @@ def test_solve_srft_matches_oracle(m, n, k, p, lda_pad):
     rec = (u * s) @ vt
     rec_o = (ref.U * ref.S) @ ref.Vt
     assert np.abs(rec - rec_o).max() <= 1e-10 * ref.S[0]
+
+
+@pytest.mark.parametrize("k,p", [(12, 8), (6, 10)])
+def test_solve_srft_repeated_singular_values(k, p):
+    """Stage B when singular values repeat (exactly, up to rounding): A of
+    rank 12 with sigma = (3, 2, 2, 1, 1, 1, 0.5, 0.5, 0.25, 0.1, 0.1, 0.1),
+    captured exactly by the range.  The complex triplets must stay complex
+    orthonormal (U^H U = I, V V^H = I), sigma must match the oracle to 1e-10,
+    and U S V^H must reproduce the oracle's rank-k approximation (unique: k
+    ends on a gap)."""
+    sig = np.array([3.0, 2.0, 2.0, 1.0, 1.0, 1.0, 0.5, 0.5, 0.25, 0.1, 0.1, 0.1])
+    m, n = 600, 512
+    A = syn.lowrank_matrix(m, n, sig, seed=31)
+    ref = srft.srft_rsvd(A, k, p, seed=5)
+    dA, lda = _device(A)
+    plan = R.Plan(m, n, 2 * (k + p))
+    U, S, VT = plan.solve_srft(dA, m, n, k, p, seed=5, lda=lda)
+    assert plan.status() == 0
+    s = S.cpu().numpy()
+    assert (np.abs(s - ref.S) / ref.S).max() <= 1e-10
+    assert np.abs(s - sig[:k]).max() <= 1e-12 * sig[0]
+    u = _complex(U, k)
+    vt_planar = R.to_numpy_f(VT)
+    vt = vt_planar[:, :n] + 1j * vt_planar[:, n:]
+    assert np.abs(u.conj().T @ u - np.eye(k)).max() <= 1e-12
+    assert np.abs(vt @ vt.conj().T - np.eye(k)).max() <= 1e-12
+    rec = (u * s) @ vt
+    rec_o = (ref.U * ref.S) @ ref.Vt
+    assert np.abs(rec - rec_o).max() <= 1e-10 * sig[0]
