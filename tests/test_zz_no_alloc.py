@@ -4,10 +4,11 @@ For callers that may not allocate device memory (they run inside a host
 framework that owns the device memory, or were handed only inputs and
 outputs), rsvd_apply_a_f64_static keeps its split-K partials in a fixed
 array inside the library.  This checks, through the C ABI, that two calls in
-a row give the product of the plan-based rsvd_apply_a within the FP64 test
-tolerance (64 ulps of max |A||X|), and that a size beyond the fixed array is
-refused.  The file sorts last so a stop-at-first-failure run has already run
-every other test; it also passes on its own in a fresh process.
+a row give the host's FP64 product a @ x (numpy, independent of the GPU) and
+the plan-based rsvd_apply_a, both within the FP64 test tolerance (64 ulps of
+max |A||X|), and that a size beyond the fixed array is refused.  The file
+sorts last so a stop-at-first-failure run has already run every other test;
+it also passes on its own in a fresh process.
 """
 import numpy as np
 import pytest
@@ -24,7 +25,7 @@ def built():
     __graft_entry__.build()
 
 
-def test_static_scratch_product_matches_plan_entry_point():
+def test_static_scratch_product_matches_host_product_and_plan_entry_point():
     m, n, l = 12000, 9000, 80          # m * l = 960000 <= 4 Mi: several split-K slices fit
     rng = np.random.default_rng(123)
     lda = m + 5
@@ -38,6 +39,7 @@ def test_static_scratch_product_matches_plan_entry_point():
     a = A[:, :m].cpu().numpy().T
     x = X.cpu().numpy().T
     tol = 64 * 2.0 ** -52 * (np.abs(a) @ np.abs(x)).max()
+    host = (a @ x).T                   # (l, m): the layout of the device output
     ref = Y_ref.cpu().numpy()
     for _ in range(2):
         Y = torch.full((l, m), float("nan"), dtype=torch.float64, device="cuda")
@@ -45,6 +47,7 @@ def test_static_scratch_product_matches_plan_entry_point():
         torch.cuda.synchronize()
         got = Y.cpu().numpy()
         assert np.isfinite(got).all()
+        assert np.abs(got - host).max() <= tol
         assert np.abs(got - ref).max() <= tol
 
 
