@@ -4,9 +4,15 @@ Requests (m x n matrix already on the device, k, p, q, sigma tolerance) arrive
 over time.  The server keeps a set of *lanes*; each lane is one CUDA stream
 with one batch plan (rsvd_batch_plan_create) for a class of requests:
 
-* precision: FP32 lanes serve requests whose tolerance FP32 meets (>= 1e-4
-  relative on sigma), FP64 lanes the rest (the matrix is promoted to FP64 on
-  the device);
+* precision: a request's tolerance is relative on every sigma_i, i <= k.
+  Requests with tol >= 1e-4 start on FP32 lanes, the rest on FP64 lanes
+  (the matrix is promoted to FP64 on the device).  FP32 rounding moves each
+  computed sigma by about u_32 sigma_1 (u_32 = 2^-24), i.e. by u_32
+  sigma_1 / sigma_i relative, so whether FP32 meets a tolerance depends on
+  the spectrum, which is known only once solved: an FP32 result is accepted
+  when FP32_ERR_COEF u_32 sigma_1 / sigma_k <= tol (computed sigmas), and
+  otherwise the request is promoted and solved again on an FP64 lane (its
+  latency covers both solves);
 * size: "small" lanes (k + p <= 80) and "big" lanes (k + p up to 288), so a
   few large problems never hold back the latency of the many small ones.
 
@@ -29,6 +35,8 @@ from dataclasses import dataclass, field
 from typing import Dict, List, Optional
 
 FP32_TOL_LIMIT = 1e-4     # tolerances below this go to FP64 lanes
+FP32_UNIT = 2.0 ** -24
+FP32_ERR_COEF = 256.0     # FP32 sigma error bound: FP32_ERR_COEF * u_32 * sigma_1
 SMALL_L_MAX = 80
 BIG_L_MAX = 288
 
@@ -51,6 +59,8 @@ class Request:
     done: Optional[float] = None
     status: Optional[int] = None
     result: object = None
+    precision: Optional[str] = None   # "f32" / "f64" once routed (promotion sets "f64")
+    promoted: bool = False
 
     @property
     def l(self) -> int:
@@ -62,9 +72,20 @@ class Request:
 
 
 def request_class(r: Request) -> str:
-    prec = "f32" if r.tol >= FP32_TOL_LIMIT else "f64"
+    prec = r.precision or ("f32" if r.tol >= FP32_TOL_LIMIT else "f64")
     size = "small" if r.l <= SMALL_L_MAX else "big"
     return f"{prec}-{size}"
+
+
+def fp32_meets(sigma, tol: float) -> bool:
+    """Whether an FP32 result's singular values (descending, length k) meet
+    the relative tolerance on every sigma_i: the FP32 error bound
+    FP32_ERR_COEF u_32 sigma_1, relative to the smallest sigma_k, must not
+    exceed tol.  Non-finite or non-positive sigma_k fails."""
+    s = [float(x) for x in sigma]
+    if not s or not all(math.isfinite(x) for x in s) or s[-1] <= 0.0:
+        return False
+    return FP32_ERR_COEF * FP32_UNIT * s[0] / s[-1] <= tol
 
 
 def footprint_bytes(r: Request) -> int:
@@ -119,8 +140,10 @@ class Server:
         self.finished: List[Request] = []
         self.clock = clock
         self.admission_stalls = 0
+        self.promotions = 0
 
     def submit(self, r: Request, now: float = 0.0):
+        r.precision = r.precision or ("f32" if r.tol >= FP32_TOL_LIMIT else "f64")
         cls = request_class(r)
         if cls not in self.queues:
             raise ValueError(f"no lane serves request class {cls}")
@@ -132,6 +155,26 @@ class Server:
             self.finished.append(r)
             return
         self.queues[cls].append(r)
+
+    def _promote(self, r: Request, now: float):
+        """FP32 did not meet r's tolerance: queue it again on the FP64 class,
+        ahead of requests that arrived after it (FIFO by arrival)."""
+        r.precision = "f64"
+        r.promoted = True
+        r.result = None
+        self.promotions += 1
+        cls = request_class(r)
+        spec = next((l.spec for l in self.lanes if l.spec.name == cls), None)
+        if (spec is None or footprint_bytes(r) > self.budget or r.l > spec.l_max or
+                r.m > spec.rows_total or r.n > spec.cols_total):
+            r.status, r.done = 4, now
+            self.finished.append(r)
+            return
+        q = self.queues[cls]
+        i = 0
+        while i < len(q) and q[i].arrival <= r.arrival:
+            i += 1
+        q.insert(i, r)
 
     def _fill(self, lane: Lane, now: float) -> List[Request]:
         q = self.queues[lane.spec.name]
@@ -162,12 +205,17 @@ class Server:
         for lane in self.lanes:
             if lane.busy and self.backend.poll(lane):
                 t = now if self.clock is None else self.clock()
-                for r, st in zip(lane.batch, self.backend.statuses(lane)):
+                f32 = lane.spec.name.startswith("f32")
+                sig = self.backend.sigmas(lane) if f32 else [None] * len(lane.batch)
+                for r, st, s in zip(lane.batch, self.backend.statuses(lane), sig):
+                    self.in_use -= footprint_bytes(r)
+                    if f32 and st == 0 and not fp32_meets(s, r.tol):
+                        self._promote(r, t)
+                        continue
                     r.done = t
                     r.status = st
-                    self.in_use -= footprint_bytes(r)
                     self.finished.append(r)
-                completed += len(lane.batch)
+                    completed += 1
                 lane.busy = False
                 lane.batch = []
         for lane in self.lanes:
@@ -216,6 +264,7 @@ def run(server: Server, requests: List[Request], now_fn, max_wall: float = 600.0
             "max_ms": max(lat) * 1e3 if lat else float("nan"),
             "batches": sum(l.batches for l in server.lanes),
             "admission_stalls": server.admission_stalls,
+            "promotions": server.promotions,
             "failed": sum(1 for r in server.finished if r.status != 0)}
 
 
@@ -262,3 +311,8 @@ class TorchBackend:
 
     def statuses(self, lane: Lane) -> List[int]:
         return self.state[lane.key]["plan"].status()
+
+    def sigmas(self, lane: Lane):
+        """Host copies of each finished request's singular values (the lane's
+        event has completed, so the copies do not wait on work in flight)."""
+        return [r.result[1].cpu().tolist() for r in lane.batch]

@@ -1,6 +1,9 @@
 """Continuous batching on the GPU: every served result equals the same
 request solved alone (bitwise: the grouped kernels share no work between
-problems), and results meet the oracle at the lane's precision."""
+problems), and every result meets its own request's tolerance, relative on
+each sigma_i (i <= k), against the FP64 oracle on the stored matrix.
+Requests whose FP32 result cannot meet the tolerance (a steep spectrum with
+a large k) are promoted to FP64 lanes by the server."""
 import time
 
 import numpy as np
@@ -21,7 +24,7 @@ def built():
     __graft_entry__.build()
 
 
-def test_served_results_equal_solo_results():
+def test_served_results_equal_solo_results_and_meet_their_tolerance():
     rng = np.random.default_rng(0)
     bases = []
     for i in range(6):
@@ -32,20 +35,30 @@ def test_served_results_equal_solo_results():
     big = syn.lowrank_matrix(2000, 1500, syn.spectrum("poly", 1500, alpha=1.0), seed=9)
     big = big.astype(np.float32).astype(np.float64)
     bases.append((big, R.from_numpy_f(big, dtype=torch.float32)))
+    # a steep spectrum (sigma_i = exp(-i/5)): sigma_60 / sigma_1 ~ 7e-6 is below
+    # what FP32 resolves to 1e-3, so its 1e-3 requests must be promoted
+    steep = syn.lowrank_matrix(1200, 900, syn.spectrum("exp", 200, r=5.0), seed=77)
+    steep = steep.astype(np.float32).astype(np.float64)
+    bases.append((steep, R.from_numpy_f(steep, dtype=torch.float32)))
     torch.cuda.synchronize()
-    reqs = []
+    reqs, host = [], {}
     t = 0.0
-    for i in range(40):
+    for i in range(44):
         t += float(rng.exponential(0.004))
         if i % 13 == 5:
-            A, dA = bases[-1]
+            b = 6
             k, p, q = 100, 20, 2
+        elif i % 11 == 3:
+            b = 7
+            k, p, q = 60, 10, 1
         else:
-            A, dA = bases[i % 6]
+            b = i % 6
             k, p, q = int(rng.integers(10, 40)), 10, 1
+        A, dA = bases[b]
         tol = 1e-6 if i % 4 == 0 else 1e-3
         m, n = A.shape
         reqs.append(serve.Request(i, m, n, k, p, q, tol, 1000 + i, t, A=dA))
+        host[i] = A
     specs = [serve.LaneSpec("f32-small", 8, 8 * 1500, 8 * 1000, 80),
              serve.LaneSpec("f64-small", 8, 8 * 1500, 8 * 1000, 80),
              serve.LaneSpec("f32-big", 2, 2 * 2000, 2 * 1500, 288),
@@ -53,8 +66,10 @@ def test_served_results_equal_solo_results():
     srv = serve.Server(specs, serve.TorchBackend(), 8 * 10**9, lanes_per_class=2)
     stats = serve.run(srv, reqs, time.perf_counter, max_wall=120.0)
     torch.cuda.synchronize()
-    assert stats["completed"] == 40 and stats["failed"] == 0
-    assert stats["batches"] < 40             # requests were batched together
+    assert stats["completed"] == 44 and stats["failed"] == 0
+    assert stats["batches"] < 44             # requests were batched together
+    steep_1e3 = [r for r in srv.finished if host[r.rid] is steep and r.tol == 1e-3]
+    assert steep_1e3 and all(r.promoted for r in steep_1e3)
     for r in srv.finished:
         cls = serve.request_class(r)
         dt = R.F32 if cls.startswith("f32") else R.F64
@@ -64,12 +79,17 @@ def test_served_results_equal_solo_results():
         assert solo.status() == [0]
         for x, y in zip((U, S, VT), r.result):
             assert torch.equal(x, y), r.rid
-    # accuracy at the lane precision, against the oracle on the stored matrix
-    for r in srv.finished[:12]:
-        A = bases[-1][0] if r.k == 100 else bases[r.rid % 6][0]
-        ref = oracle.rsvd(A, r.k, r.p, r.q, r.seed)
+    # every result meets its own request's tolerance on every sigma_i
+    worst = 0.0
+    for r in srv.finished:
+        ref = oracle.rsvd(host[r.rid], r.k, r.p, r.q, r.seed)
         s = r.result[1].cpu().numpy()
-        if serve.request_class(r).startswith("f64"):
-            assert (np.abs(s - ref.S) / ref.S).max() <= 1e-10
-        else:
-            assert np.abs(s - ref.S).max() <= 1e-5 * ref.S[0]
+        rel = (np.abs(s - ref.S) / ref.S).max()
+        assert rel <= r.tol, (r.rid, serve.request_class(r), rel, r.tol)
+        if serve.request_class(r).startswith("f32"):
+            worst = max(worst, float(np.abs(s - ref.S).max() / ref.S[0]))
+        elif host[r.rid] is not steep:
+            # sigma_k / sigma_1 >= ~1e-3 here: the plain FP64 bar applies
+            assert rel <= 1e-10, (r.rid, rel)
+    # the acceptance rule's bound on FP32 sigma errors holds with room to spare
+    assert worst <= serve.FP32_ERR_COEF * serve.FP32_UNIT, worst

@@ -31,6 +31,12 @@ class FakeBackend:
     def statuses(self, lane):
         return self.state[lane.key][1]
 
+    def sigmas(self, lane):
+        """Simulated FP32 singular values: sigma_i = exp(-i / r.decay) (each
+        request may carry a ``decay``; default a flat-ish spectrum)."""
+        import math
+        return [[math.exp(-i / getattr(r, "decay", 1e3)) for i in range(r.k)] for r in lane.batch]
+
 
 class Clock:
     def __init__(self):
@@ -151,3 +157,54 @@ def test_requests_that_can_never_fit_are_refused_not_blocking():
     assert stats["completed"] == 2
     st = {r.rid: r.status for r in srv.finished}
     assert st[0] == 4 and st[1] == 0
+
+
+def test_fp32_acceptance_rule():
+    u = serve.FP32_UNIT * serve.FP32_ERR_COEF
+    flat = [1.0, 0.9, 0.5]
+    assert serve.fp32_meets(flat, 1e-3)
+    # sigma_1 / sigma_k just inside / outside tol / (coef u)
+    ratio = 1e-3 / u
+    assert serve.fp32_meets([1.0, 1.0 / (0.99 * ratio)], 1e-3)
+    assert not serve.fp32_meets([1.0, 1.0 / (1.01 * ratio)], 1e-3)
+    assert not serve.fp32_meets([1.0, 0.0], 1e-3)
+    assert not serve.fp32_meets([1.0, float("nan")], 1e-3)
+
+
+def test_steep_spectrum_requests_are_promoted_to_fp64():
+    """A 1e-3 request whose FP32 result cannot resolve sigma_k to 1e-3 is
+    solved again on an FP64 lane; the others finish on FP32 lanes."""
+    clock = Clock()
+    be = FakeBackend(clock)
+    srv = serve.Server(SPECS, be, 10**11, lanes_per_class=1, clock=lambda: clock.t)
+    reqs = []
+    for i in range(20):
+        r = serve.Request(i, 1000, 800, 60, 10, 1, 1e-3, i, i * 1e-4)
+        r.decay = 5.0 if i % 3 == 0 else 200.0     # e^(59/5) ~ 1.3e5 vs e^(59/200) ~ 1.3
+        reqs.append(r)
+    stats = serve.run(srv, reqs, clock)
+    assert stats["completed"] == 20 and stats["failed"] == 0
+    assert stats["promotions"] == 7
+    for r in srv.finished:
+        steep = r.rid % 3 == 0
+        assert r.promoted == steep
+        assert serve.request_class(r) == ("f64-small" if steep else "f32-small")
+        assert r.lane.startswith("f64" if steep else "f32")
+    # promoted requests ran twice: once on an FP32 lane, then on an FP64 lane
+    ran = {}
+    for key, rids, _ in be.launches:
+        for rid in rids:
+            ran.setdefault(rid, []).append(key.split("-")[0])
+    for rid, lanes in ran.items():
+        assert lanes == (["f32", "f64"] if rid % 3 == 0 else ["f32"]), (rid, lanes)
+    assert srv.in_use == 0
+
+
+def test_tight_tolerance_goes_straight_to_fp64():
+    clock = Clock()
+    be = FakeBackend(clock)
+    srv = serve.Server(SPECS, be, 10**11, lanes_per_class=1, clock=lambda: clock.t)
+    r = serve.Request(0, 500, 400, 20, 10, 1, 1e-6, 0, 0.0)
+    stats = serve.run(srv, [r], clock)
+    assert stats["completed"] == 1 and stats["promotions"] == 0
+    assert r.lane.startswith("f64") and not r.promoted
