@@ -69,8 +69,27 @@ typedef enum {
 
 typedef enum {
   RSVD_MODE_PLAIN = 0, /* FP64 arithmetic throughout (A must be RSVD_F64)   */
-  RSVD_MODE_MIXED = 1  /* BF16 operands on tcgen05 tensor cores, FP32
+  RSVD_MODE_MIXED = 1, /* BF16 operands on tcgen05 tensor cores, FP32
                           accumulation, FP32 for the other steps            */
+  RSVD_MODE_F64_TENSOR = 2
+                       /* FP64 A, FP64 results, every step as in plain mode
+                          except the passes over A: those run on the tcgen05
+                          tensor cores as exact products of BF16 digit
+                          slices.  Each row of A gets a power-of-two scale
+                          and six balanced base-256 digits (A = scale * sum
+                          of digits * 2^(-7-8s) + a remainder below 2^-48 of
+                          the scale); the operand is split the same way per
+                          column; the 21 digit products of weight >= 2^-40
+                          are accumulated exactly (integer sums in FP32
+                          drained to 64-bit integers every 256 terms) or, for
+                          the two smallest weights, in FP32.  A pass with
+                          contraction length K is then within about
+                          2^-45 K max|a_i.| max|x_.c| of the exact product
+                          (worst case; near 2^-45 sqrt(K) of that scale in
+                          practice).  Every call that reads A first builds
+                          its digit slices (12 bytes per element of A, in the
+                          workspace).  Entry points and outputs as in plain
+                          mode; A must be RSVD_F64.                        */
 } rsvd_mode_t;
 
 /* Status codes (positive). */
@@ -100,7 +119,9 @@ typedef enum {
  * Allocates a small pinned host status buffer and nothing on the device.
  * Errors: -1 plan NULL; -2/-3 sizes < 1; -4 l_max < 1 or > RSVD_L_MAX (256 in
  * mixed mode); -5 unknown dtype; -6 unknown mode or mode/dtype mismatch;
- * RSVD_ERR_CUDA if the host allocation fails.
+ * RSVD_ERR_CUDA if the host allocation fails.  RSVD_MODE_F64_TENSOR plans
+ * need 12 m_max n_max bytes more workspace than plain ones (A's digit
+ * slices).
  */
 int rsvd_plan_create(rsvd_plan_t* plan, int64_t m_max, int64_t n_max, int l_max,
                      int a_dtype, int mode, void* cuda_stream);
@@ -149,6 +170,22 @@ int rsvd_plan_set_stream(rsvd_plan_t plan, void* cuda_stream);
  * GPU pipeline.
  */
 int rsvd_plan_set_wait_limit(rsvd_plan_t plan, int64_t cycles);
+
+/*
+ * rsvd_plan_prepare_a / rsvd_plan_release_a: RSVD_MODE_F64_TENSOR plans build
+ * the digit slices of A at the start of every call that reads A.
+ * rsvd_plan_prepare_a builds them now (enqueued on the plan's stream) and
+ * keeps them: later calls that name the same (A, m, n, lda) skip that step,
+ * until rsvd_plan_release_a or a call on another matrix (whose slices then
+ * replace them).  The caller must not change A's contents while it is
+ * prepared: the kept slices would no longer match it.  On plans of other
+ * modes both calls return RSVD_OK and do nothing.  Errors: -1 plan; -2 A
+ * NULL; -3 m; -4 n; -5 lda < m; RSVD_ERR_WORKSPACE if the plan has no
+ * workspace or m, n exceed it.  The thesis has no counterpart: this is a
+ * cache of the tensor passes' operand format.
+ */
+int rsvd_plan_prepare_a(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t lda);
+int rsvd_plan_release_a(rsvd_plan_t plan);
 
 /*
  * rsvd_set_tile_scales (RSVD_FP8E4M3 plans): the scales of A.  Element (i, j)

@@ -31,6 +31,8 @@ SIGNATURES = {
     "rsvd_plan_status": (c_int, [c_void_p]),
     "rsvd_plan_set_stream": (c_int, [c_void_p, c_void_p]),
     "rsvd_plan_set_wait_limit": (c_int, [c_void_p, c_int64]),
+    "rsvd_plan_prepare_a": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_int64]),
+    "rsvd_plan_release_a": (c_int, [c_void_p]),
     "rsvd_set_tile_scales": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_int64]),
     "rsvd_plan_diagnostics": (c_int, [c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
     "rsvd_plan_destroy": (c_int, [c_void_p]),

@@ -55,18 +55,6 @@ __global__ void apass_fixup_kernel(const float* __restrict__ part, int grid, int
   }
 }
 
-// The split tiles and their partial slots, listed on the host (kernel
-// parameter): the list kernel's blocks all do real work, and none searches
-// the stream-K schedule on the device.
-constexpr int kFixMaxTiles = 192;
-constexpr int kFixMaxSrc = 512;
-struct FixList {
-  int n;                          // split tiles
-  int tile[kFixMaxTiles];
-  int off[kFixMaxTiles + 1];      // sources of tile i: src[off[i] .. off[i+1])
-  int src[kFixMaxSrc];            // partial slot (CTA * 2 + 0 first / 1 last tile)
-};
-
 __global__ void apass_fixup_list_kernel(const float* __restrict__ part, int bmt, int l,
                                         int64_t rows_out, float* __restrict__ out, int64_t ldo,
                                         int accumulate, const __grid_constant__ FixList fl) {
@@ -89,6 +77,8 @@ __global__ void apass_fixup_list_kernel(const float* __restrict__ part, int bmt,
     }
   }
 }
+
+}  // namespace
 
 // Host mirror of the pass kernel's stream-K ranges: CTA c of `grid` takes
 // iterations [total c / grid, total (c+1) / grid).
@@ -131,8 +121,6 @@ bool build_fix_list(int grid, int64_t total, int kt, int64_t tiles, FixList& fl)
   (void)tiles;
   return true;
 }
-
-}  // namespace
 
 int launch_apass_fixup(const float* part, int grid, int64_t total, int kt, int bmt, int l,
                        int64_t rows_out, int64_t tiles, float* out, int64_t ldo, int accumulate,

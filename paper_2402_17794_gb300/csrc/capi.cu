@@ -38,6 +38,29 @@ bool power_of_two(float x) {
   return (b >> 31) == 0 && e != 0 && e != 0xFF && mant == 0;
 }
 
+// RSVD_MODE_F64_TENSOR plans: A's digit slices are built at the start of a
+// call that reads A, and its passes run on the tensor cores until the call
+// returns.  Plain plans: nothing.
+// A matrix prepared by rsvd_plan_prepare_a is reused as long as the call
+// names the same (A, m, n, lda).
+struct TcScope {
+  rsvd_plan_t P;
+  int rc = RSVD_OK;
+  bool keep = false;
+  TcScope(rsvd_plan_t p, const void* A, int64_t m, int64_t n, int64_t lda) : P(p) {
+    if (!P->f64tc) return;
+    if (P->tc_pinned && P->tc_A == A && P->tc_m == m && P->tc_n == n && P->tc_lda == lda) {
+      keep = true;
+      return;
+    }
+    P->tc_pinned = 0;   // another matrix: its slices replace the prepared ones
+    rc = f64tc_begin(P, (const double*)A, m, n, lda);
+  }
+  ~TcScope() {
+    if (P->f64tc && !keep) f64tc_end(P);
+  }
+};
+
 }  // namespace
 
 extern "C" {
@@ -50,7 +73,10 @@ int rsvd_plan_create(rsvd_plan_t* plan, int64_t m_max, int64_t n_max, int l_max,
   if (n_max < 1) return -3;
   if (l_max < 1 || l_max > RSVD_L_MAX) return -4;
   if (a_dtype != RSVD_F64 && a_dtype != RSVD_BF16 && a_dtype != RSVD_FP8E4M3) return -5;
-  if (mode != RSVD_MODE_PLAIN && mode != RSVD_MODE_MIXED) return -6;
+  if (mode != RSVD_MODE_PLAIN && mode != RSVD_MODE_MIXED && mode != RSVD_MODE_F64_TENSOR)
+    return -6;
+  const bool f64tc = mode == RSVD_MODE_F64_TENSOR;
+  if (f64tc) mode = RSVD_MODE_PLAIN;   // plain in everything but the passes over A
   if ((mode == RSVD_MODE_PLAIN) != (a_dtype == RSVD_F64)) return -6;
   if (mode == RSVD_MODE_MIXED && l_max > 256) return -4;
   rsvd_plan_s* P = new (std::nothrow) rsvd_plan_s();
@@ -76,7 +102,8 @@ int rsvd_plan_create(rsvd_plan_t* plan, int64_t m_max, int64_t n_max, int l_max,
     delete P;
     return RSVD_ERR_CUDA;
   }
-  P->lay = make_layout(m_max, n_max, l_max, mode, P->num_sms);
+  P->f64tc = f64tc ? 1 : 0;
+  P->lay = make_layout(m_max, n_max, l_max, mode, P->num_sms, f64tc);
   std::memset(P->h_status, 0, sizeof(int) * 8);
   *plan = P;
   return RSVD_OK;
@@ -191,6 +218,27 @@ int rsvd_plan_set_wait_limit(rsvd_plan_t plan, int64_t cycles) {
   return RSVD_OK;
 }
 
+int rsvd_plan_prepare_a(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t lda) {
+  if (!plan) return -1;
+  if (!A) return -2;
+  if (m < 1) return -3;
+  if (n < 1) return -4;
+  if (lda < m) return -5;
+  if (!ready(plan) || m > plan->m_max || n > plan->n_max) return RSVD_ERR_WORKSPACE;
+  if (!plan->f64tc) return RSVD_OK;
+  plan->tc_pinned = 0;
+  const int rc = f64tc_begin(plan, (const double*)A, m, n, lda);
+  if (rc == RSVD_OK) plan->tc_pinned = 1;
+  return rc;
+}
+
+int rsvd_plan_release_a(rsvd_plan_t plan) {
+  if (!plan) return -1;
+  plan->tc_pinned = 0;
+  if (plan->f64tc) f64tc_end(plan);
+  return RSVD_OK;
+}
+
 int rsvd_set_tile_scales(rsvd_plan_t plan, const float* scales, int64_t rows, int64_t cols,
                          int64_t lds) {
   if (!plan) return -1;
@@ -292,9 +340,12 @@ int rsvd_solve(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t ld
   if (plan->mode == RSVD_MODE_MIXED && (lda % 8 || ((uintptr_t)A % 16)))
     return RSVD_ERR_UNSUPPORTED;
   if (plan->dtype == RSVD_FP8E4M3 && !fp8_ready(plan, m, n, lda)) return RSVD_ERR_UNSUPPORTED;
-  if (plan->mode == RSVD_MODE_PLAIN)
+  if (plan->mode == RSVD_MODE_PLAIN) {
+    TcScope tc(plan, A, m, n, lda);
+    if (tc.rc) return tc.rc;
     return solve_plain(plan, (const double*)A, m, n, lda, k, p, q, seed, (double*)U, ldu, S,
                        (double*)VT, ldvt);
+  }
   return solve_mixed(plan, A, m, n, lda, k, p, q, seed, (float*)U, ldu, S, (float*)VT, ldvt);
 }
 
@@ -324,6 +375,8 @@ int rsvd_solve_algorithm(rsvd_plan_t plan, int algorithm, const void* A, int64_t
   if (algorithm == 2 || algorithm == 4)
     return rsvd_solve(plan, A, m, n, lda, k, p, q, seed, U, ldu, S, VT, ldvt);
   if (plan->mode != RSVD_MODE_PLAIN) return RSVD_ERR_UNSUPPORTED;
+  TcScope tc(plan, A, m, n, lda);
+  if (tc.rc) return tc.rc;
   if (algorithm == 3)
     return solve_plain_alg3(plan, (const double*)A, m, n, lda, k, p, q, seed, (double*)U, ldu, S,
                             (double*)VT, ldvt);
@@ -351,6 +404,8 @@ int rsvd_solve_singlepass(rsvd_plan_t plan, const void* A, int64_t m, int64_t n,
   if (!ready(plan) || m > plan->m_max || n > plan->n_max || l > plan->l_max)
     return RSVD_ERR_WORKSPACE;
   if (plan->mode != RSVD_MODE_PLAIN || plan->batched) return RSVD_ERR_UNSUPPORTED;
+  TcScope tc(plan, A, m, n, lda);
+  if (tc.rc) return tc.rc;
   return solve_singlepass(plan, (const double*)A, m, n, lda, k, p, seed, (double*)U, ldu, S,
                           (double*)VT, ldvt);
 }
@@ -370,6 +425,8 @@ int rsvd_solve_hermitian(rsvd_plan_t plan, const void* A, int64_t n, int64_t lda
   if (!ready(plan) || n > plan->m_max || n > plan->n_max || k + p > plan->l_max)
     return RSVD_ERR_WORKSPACE;
   if (plan->mode != RSVD_MODE_PLAIN || plan->batched) return RSVD_ERR_UNSUPPORTED;
+  TcScope tc(plan, A, n, n, lda);
+  if (tc.rc) return tc.rc;
   return solve_hermitian(plan, (const double*)A, n, lda, k, p, seed, (double*)U, ldu, D);
 }
 
@@ -405,6 +462,8 @@ int rsvd_range_adaptive(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, i
   if (rc) return rc;
   if (!Q) return -10;
   if (ldq < m) return -11;
+  TcScope tc(plan, A, m, n, lda);
+  if (tc.rc) return tc.rc;
   return range_adaptive(plan, (const double*)A, m, n, lda, eps, r, l_cap, seed, (double*)Q, ldq,
                         rank);
 }
@@ -420,6 +479,8 @@ int rsvd_solve_adaptive(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, i
   if (!S) return -12;
   if (!VT) return -13;
   if (ldvt < l_cap) return -14;
+  TcScope tc(plan, A, m, n, lda);
+  if (tc.rc) return tc.rc;
   return solve_adaptive(plan, (const double*)A, m, n, lda, eps, r, l_cap, seed, (double*)U, ldu,
                         S, (double*)VT, ldvt, rank);
 }
@@ -448,6 +509,8 @@ int rsvd_range_srft(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64
                     uint64_t seed, void* Q, int64_t ldq) {
   const int rc = srft_args(plan, A, m, n, lda, l, Q, ldq);
   if (rc) return rc;
+  TcScope tc(plan, A, m, n, lda);
+  if (tc.rc) return tc.rc;
   return range_srft(plan, (const double*)A, m, n, lda, l, seed, (double*)Q, ldq);
 }
 
@@ -469,6 +532,8 @@ int rsvd_solve_srft(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64
   if (!ready(plan) || m > plan->m_max || n > plan->n_max || 2 * (k + p) > plan->l_max)
     return RSVD_ERR_WORKSPACE;
   if (plan->mode != RSVD_MODE_PLAIN || plan->batched) return RSVD_ERR_UNSUPPORTED;
+  TcScope tc(plan, A, m, n, lda);
+  if (tc.rc) return tc.rc;
   return solve_srft(plan, (const double*)A, m, n, lda, k, p, seed, (double*)U, ldu, S,
                     (double*)VT, ldvt);
 }
@@ -507,9 +572,12 @@ int rsvd_apply_a(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t 
   if (!ready(plan) || m > plan->m_max || n > plan->n_max || l > plan->l_max)
     return RSVD_ERR_WORKSPACE;
   if (plan->dtype == RSVD_FP8E4M3 && !fp8_ready(plan, m, n, lda)) return RSVD_ERR_UNSUPPORTED;
-  if (plan->mode == RSVD_MODE_PLAIN)
+  if (plan->mode == RSVD_MODE_PLAIN) {
+    TcScope tc(plan, A, m, n, lda);
+    if (tc.rc) return tc.rc;
     return gemm<double>(plan, (const double*)A, lda, false, (const double*)X, ldx, (double*)Y, ldy,
                         m, n, l);
+  }
   return mixed_apply(plan, A, m, n, lda, X, ldx, l, (float*)Y, ldy, false);
 }
 
@@ -528,9 +596,12 @@ int rsvd_apply_at(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t
   if (!ready(plan) || m > plan->m_max || n > plan->n_max || l > plan->l_max)
     return RSVD_ERR_WORKSPACE;
   if (plan->dtype == RSVD_FP8E4M3 && !fp8_ready(plan, m, n, lda)) return RSVD_ERR_UNSUPPORTED;
-  if (plan->mode == RSVD_MODE_PLAIN)
+  if (plan->mode == RSVD_MODE_PLAIN) {
+    TcScope tc(plan, A, m, n, lda);
+    if (tc.rc) return tc.rc;
     return gemm<double>(plan, (const double*)A, lda, true, (const double*)X, ldx, (double*)Z, ldz,
                         n, m, l);
+  }
   return mixed_apply(plan, A, m, n, lda, X, ldx, l, (float*)Z, ldz, true);
 }
 

@@ -48,6 +48,11 @@ struct Layout {
   // mixed-mode extras: BF16 operand slices (om16), tcgen05 partial slots (y32)
   size_t om16, y32;
   size_t small_stride;  // bytes of one l x l FP64 matrix (padded)
+  size_t refine;        // FP64 / FP32 l x l scratch of the small SVD (step 7)
+  // RSVD_MODE_F64_TENSOR: A's digit slices, row exponents, the operand's
+  // slices and exponents, raw outputs and partial slots of the passes
+  size_t tc_slices, tc_rmax, tc_xs, tc_fexp, tc_rawt, tc_rawr, tc_partt, tc_partr;
+  int64_t tc_ncol, tc_ldsl, tc_ldxs;
 };
 
 }  // namespace rsvd
@@ -77,6 +82,10 @@ struct rsvd_plan_s {
   void* h_ctx;                    // pinned staging for the context table
   cudaEvent_t ctx_event;          // marks the table copy of the last batched solve
   long long wait_cycles;          // rsvd_plan_set_wait_limit (0: the default bound)
+  int f64tc;                      // RSVD_MODE_F64_TENSOR (mode holds RSVD_MODE_PLAIN)
+  const void* tc_A;               // the A whose slices are current (during a call)
+  int64_t tc_m, tc_n, tc_lda;
+  int tc_pinned;                  // rsvd_plan_prepare_a: slices kept across calls
 };
 
 namespace rsvd {
@@ -153,6 +162,22 @@ cudaError_t launch_jacobi_svd(const T* M, int l, int64_t ldm, T* sig, T* Um, int
 template <typename T>
 cudaError_t launch_finalize(T* U, int64_t m, int64_t ldu, int k, const T* Vk, int64_t n, T* VT,
                             int64_t ldvt, const T* sig, double* S, T* sign_work, cudaStream_t st);
+
+// FP64 refinement of an approximate SVD M = U diag(s) V^T (all l x l, ld l),
+// `steps` steps in place (see svd_refine.cu); work: 8 l^2 doubles.
+cudaError_t launch_svd_refine(const double* M, int l, double* U, double* V, double* s, int steps,
+                              double cluster_tol, double* work, cudaStream_t st);
+// Us = U diag(1/s) (0 where s_i <= 0); V = M^T Us; C = A B (all l x l, ld l, FP64).
+cudaError_t launch_scale_cols(const double* U, const double* s, int l, double* Us,
+                              cudaStream_t st);
+cudaError_t launch_right_vectors(const double* M, const double* Us, int l, double* V,
+                                 cudaStream_t st);
+cudaError_t launch_small_product(const double* A, const double* B, int l, double* C,
+                                 cudaStream_t st);
+// V <- V (3 I - V^T V) / 2, `steps` times (work: 2 l^2 doubles).
+cudaError_t launch_orthonormalize(double* V, int l, int steps, double* work, cudaStream_t st);
+template <typename Tin, typename Tout>
+cudaError_t launch_convert(const Tin* in, int64_t count, Tout* out, cudaStream_t st);
 
 // Flips columns of U (m x k, ldu) so each column's largest-|.| entry is
 // positive (lowest index on ties).

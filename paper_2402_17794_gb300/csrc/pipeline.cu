@@ -1,6 +1,8 @@
 // Host-side orchestration of Algorithm 4 (Section 3.3) for both paths.
 //
-// Plain path (FP64 A):   every step in FP64; passes over A on the CUDA cores.
+// Plain path (FP64 A):   every step in FP64; passes over A on the CUDA cores,
+//                        or (RSVD_MODE_F64_TENSOR plans) on the tensor cores
+//                        as exact products of BF16 digit slices.
 // Mixed path (BF16 A):   passes over A on the tcgen05 tensor cores with BF16
 //                        operands and FP32 accumulation; everything else in
 //                        FP32.  The q power steps use a single BF16 copy of
@@ -106,7 +108,7 @@ int mixed_pass(rsvd_plan_t P, bool ax, const void* A, int64_t m, int64_t n, int6
 // Workspace
 // ---------------------------------------------------------------------------
 
-Layout make_layout(int64_t m, int64_t n, int l, int mode, int num_sms) {
+Layout make_layout(int64_t m, int64_t n, int l, int mode, int num_sms, bool f64tc) {
   Layout L{};
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -132,10 +134,25 @@ Layout make_layout(int64_t m, int64_t n, int l, int mode, int num_sms) {
                  align_up(((size_t)l * l + 33 * (size_t)(l + 64)) * e));
   L.sp = take(L.small_stride * kSinglePassSlots + align_up(kSinglePassVecs * (size_t)l * e));
   L.ad = take((size_t)m * l * e);
+  L.refine = take(((size_t)16 * l * l + 4 * (size_t)l) * sizeof(double));
   if (mode == RSVD_MODE_MIXED) {
     const int l16 = (l + 15) / 16 * 16;
     L.om16 = take((size_t)round8(mn) * 3 * l16 * sizeof(__nv_bfloat16));
     L.y32 = take(apass_partial_floats(num_sms, l) * sizeof(float));
+  }
+  if (f64tc) {
+    const int64_t lw = (int64_t)kF64tcMaxL;
+    L.tc_ncol = (n + 127) / 128 * 128;
+    L.tc_ldsl = round8(m);
+    L.tc_ldxs = round8(mn);
+    L.tc_slices = take((size_t)6 * L.tc_ncol * L.tc_ldsl * 2);
+    L.tc_rmax = take(sizeof(int) * (size_t)m);
+    L.tc_xs = take((size_t)6 * lw * L.tc_ldxs * 2);
+    L.tc_fexp = take(sizeof(int) * (size_t)lw);
+    L.tc_rawt = take((size_t)mn * lw * 8);
+    L.tc_rawr = take((size_t)mn * lw * 4);
+    L.tc_partt = take((size_t)num_sms * 2 * 128 * lw * 8);
+    L.tc_partr = take((size_t)num_sms * 2 * 128 * lw * 4);
   }
   L.total = off;
   return L;
@@ -195,9 +212,60 @@ bool plan_ready(rsvd_plan_t P) { return P && P->ws && P->ws_bytes >= P->lay.tota
 // Shared steps
 // ---------------------------------------------------------------------------
 
+int f64tc_begin(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t lda) {
+  const Layout& L = P->lay;
+  int rc = f64tc_prepare_a(A, m, n, lda, P->ws + L.tc_slices, L.tc_ldsl, L.tc_ncol,
+                           (int*)(P->ws + L.tc_rmax), &dstatus(P)->flags, P->num_sms, P->stream);
+  if (rc) return rc;
+  P->tc_A = A;
+  P->tc_m = m;
+  P->tc_n = n;
+  P->tc_lda = lda;
+  return RSVD_OK;
+}
+
+namespace {
+
+// C (ldc) = A X (ax) or A^T X for the prepared A, X (ldx) with N columns, on
+// the tensor cores.
+int f64tc_pass(rsvd_plan_t P, bool ax, const double* X, int64_t ldx, double* C, int64_t ldc,
+               int N) {
+  const Layout& L = P->lay;
+  F64tcCall c;
+  c.ax = ax;
+  c.slices = P->ws + L.tc_slices;
+  c.m = P->tc_m;
+  c.n = P->tc_n;
+  c.ldsl = L.tc_ldsl;
+  c.ncol = L.tc_ncol;
+  c.rmax = (const int*)(P->ws + L.tc_rmax);
+  c.X = X;
+  c.ldx = ldx;
+  c.l = N;
+  c.out = C;
+  c.ldo = ldc;
+  c.xslices = P->ws + L.tc_xs;
+  c.ldxs = L.tc_ldxs;
+  c.fexp = (int*)(P->ws + L.tc_fexp);
+  c.raw_t = (int64_t*)(P->ws + L.tc_rawt);
+  c.raw_r = (float*)(P->ws + L.tc_rawr);
+  c.part_t = (int64_t*)(P->ws + L.tc_partt);
+  c.part_r = (float*)(P->ws + L.tc_partr);
+  c.wait_cycles = P->wait_cycles;
+  return launch_apass_f64tc(c, P->num_sms, &dstatus(P)->flags, P->stream);
+}
+
+}  // namespace
+
 template <typename T>
 int gemm(rsvd_plan_t P, const T* A, int64_t lda, bool trans, const T* X, int64_t ldx, T* C,
          int64_t ldc, int64_t M, int64_t K, int N, bool x_upper) {
+  if constexpr (sizeof(T) == 8) {
+    // a pass over the prepared A of an RSVD_MODE_F64_TENSOR plan
+    if (P->tc_A && (const void*)A == P->tc_A && lda == P->tc_lda && !x_upper &&
+        (trans ? (M == P->tc_n && K == P->tc_m) : (M == P->tc_m && K == P->tc_n)))
+      return f64tc_pass(P, !trans, X, ldx, C, ldc, N);
+  }
   GemmArgs<T> g{A, lda, trans, X, ldx, C, ldc, M, K, N, x_upper};
   Work<T> W = work_of<T>(P);
   RSVD_CK(launch_gemm<T>(g, W.part, W.part_elems, P->num_sms, P->stream));
@@ -253,6 +321,7 @@ int orth1(rsvd_plan_t P, const T* Y, int64_t rows, int l, int64_t ldy, T* Q, int
   return gemm<T>(P, Y, ldy, false, W.R1i, l, Q, ldq, rows, l, l, true);
 }
 template int orth1<float>(rsvd_plan_t, const float*, int64_t, int, int64_t, float*, int64_t);
+template int orth1<double>(rsvd_plan_t, const double*, int64_t, int, int64_t, double*, int64_t);
 
 // Shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa, Yamamoto, Yanagisawa,
 // SIAM J. Sci. Comput. 2020): one Cholesky QR of Y with the Gram shifted by
@@ -276,16 +345,74 @@ int orth_shifted(rsvd_plan_t P, const T* Y, int64_t rows, int l, int64_t ldy, T*
 template int orth_shifted<double>(rsvd_plan_t, const double*, int64_t, int, int64_t, double*,
                                   int64_t);
 
+// Step 7: the SVD of the l x l factor Mt = R_B^T: W.sig, W.Um (its left
+// singular vectors, B's) and Us = Um diag(1 / sig) (ld l), computed to FP64
+// accuracy on both paths.
+//  * FP64 (plain): a one-sided Jacobi in FP32 with its rotations V32
+//    accumulated, V32 made orthogonal in FP64 (Newton-Schulz), then the FP64
+//    one-sided Jacobi of Mt V (same left singular vectors and values; its
+//    columns are already orthogonal to about 1e-6, so it converges in a few
+//    sweeps instead of seven).
+//  * FP32 (mixed): the FP32 one-sided Jacobi, then two FP64 refinement steps
+//    of (U, sig, V = Mt^T U diag(1/sig)) against the FP64 copy of Mt; sig64
+//    receives the FP64 singular values for the output.
+template <typename T>
+int small_svd_fp64(rsvd_plan_t P, const Work<T>& W, int l, T* us_inv, double* sig64) {
+  const size_t ll = (size_t)l * l;
+  double* d = (double*)(P->ws + P->lay.refine);
+  double *M64 = d, *U64 = d + ll, *V64 = d + 2 * ll, *Us64 = d + 3 * ll, *work = d + 4 * ll;
+  double* s64 = d + 12 * ll;
+  float* f = (float*)(d + 12 * ll + l);
+  float *M32 = f, *U32 = f + ll, *V32 = f + 2 * ll, *s32 = f + 3 * ll;
+  cudaStream_t st = P->stream;
+  DeviceStatus* status = dstatus(P);
+  if constexpr (sizeof(T) == 8) {
+    RSVD_CK((launch_convert<double, float>(W.Mt, (int64_t)ll, M32, st)));
+    RSVD_CK(launch_jacobi_svd<float>(M32, l, l, s32, U32, l, V32, l, nullptr, (float*)W.jw,
+                                     status, st));
+    RSVD_CK((launch_convert<float, double>(V32, (int64_t)ll, V64, st)));
+    // V32 is orthogonal to about 1e-6, which would move sigma(Mt V) by as
+    // much: two Newton-Schulz steps make it orthogonal to FP64 rounding
+    RSVD_CK(launch_orthonormalize(V64, l, 2, work, st));
+    RSVD_CK(launch_small_product(W.Mt, V64, l, M64, st));          // Mt V
+    RSVD_CK(launch_jacobi_svd<double>(M64, l, l, W.sig, W.Um, l, nullptr, l, us_inv, W.jw,
+                                      status, st));
+    (void)U64;
+    (void)Us64;
+    (void)s64;
+    (void)sig64;
+  } else {
+    RSVD_CK(launch_jacobi_svd<float>(W.Mt, l, l, W.sig, W.Um, l, nullptr, l, nullptr, W.jw,
+                                     status, st));
+    RSVD_CK((launch_convert<float, double>(W.Mt, (int64_t)ll, M64, st)));
+    RSVD_CK((launch_convert<float, double>(W.Um, (int64_t)ll, U64, st)));
+    RSVD_CK((launch_convert<float, double>(W.sig, (int64_t)l, s64, st)));
+    RSVD_CK(launch_scale_cols(U64, s64, l, Us64, st));
+    RSVD_CK(launch_right_vectors(M64, Us64, l, V64, st));
+    RSVD_CK(launch_svd_refine(M64, l, U64, V64, s64, 2, 1e-6, work, st));
+    RSVD_CK(launch_scale_cols(U64, s64, l, Us64, st));
+    RSVD_CK((launch_convert<double, float>(U64, (int64_t)ll, W.Um, st)));
+    RSVD_CK((launch_convert<double, float>(Us64, (int64_t)ll, us_inv, st)));
+    RSVD_CK((launch_convert<double, float>(s64, (int64_t)l, W.sig, st)));
+    if (sig64) RSVD_CK((launch_convert<double, double>(s64, (int64_t)l, sig64, st)));
+    (void)M32;
+    (void)U32;
+    (void)V32;
+    (void)s32;
+  }
+  return RSVD_OK;
+}
+
 template <typename T>
 int finish(rsvd_plan_t P, const Work<T>& W, int64_t m, int64_t n, int l, int k, T* U, int64_t ldu,
            double* S, T* VT, int64_t ldvt) {
   int rc;
   // B^T (in W.z) = Q_B R_B: only R_B is formed; Mt = R_B^T
   if ((rc = orth<T>(P, W.z, n, l, n, nullptr, n, W.Mt, true))) return rc;
-  // one-sided Jacobi on R_B^T = U~ Sigma V_R^T; U~ are B's left singular vectors
+  // R_B^T = U~ Sigma V_R^T; U~ are B's left singular vectors
   T* us_inv = W.Vm;
-  RSVD_CK(launch_jacobi_svd<T>(W.Mt, l, l, W.sig, W.Um, l, nullptr, l, us_inv, W.jw, dstatus(P),
-                               P->stream));
+  double* s_fp64 = (double*)(P->ws + P->lay.refine) + 15 * (size_t)l * l;   // past the scratch
+  if ((rc = small_svd_fp64<T>(P, W, l, us_inv, sizeof(T) == 4 ? s_fp64 : nullptr))) return rc;
   // step 8: U = Q U~ (first k columns)
   if ((rc = gemm<T>(P, W.qm, m, false, W.Um, l, U, ldu, m, l, k))) return rc;
   // V_k = B^T U~_k Sigma_k^-1, then one CholeskyQR pass restores orthonormality
@@ -295,6 +422,8 @@ int finish(rsvd_plan_t P, const Work<T>& W, int64_t m, int64_t n, int l, int k, 
   RSVD_CK(launch_chol_inv<T>(W.G, k, k, W.R1, W.R1i, W.cholw, dstatus(P), P->stream));
   if ((rc = gemm<T>(P, W.tmp, n, false, W.R1i, k, W.qb, n, n, k, k, true))) return rc;
   RSVD_CK(launch_finalize<T>(U, m, ldu, k, W.qb, n, VT, ldvt, W.sig, S, W.sign, P->stream));
+  // the mixed path reports the FP64 singular values of the refined small SVD
+  if (sizeof(T) == 4) RSVD_CK((launch_convert<double, double>(s_fp64, (int64_t)k, S, P->stream)));
   return RSVD_OK;
 }
 
@@ -332,15 +461,27 @@ int solve_plain(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t ld
   Work<double> W = work_of<double>(P);
   int rc;
   // 1. Omega;  2. Y = A Omega;  3. Q = orth(Y)
+  // Only range(Q) carries into the next product, so inside the power steps
+  // one CholeskyQR pass is enough (columns orthonormal to u kappa(Y)^2, the
+  // range exact; it breaks down only past kappa ~ 1e8); the Q that B is
+  // formed from (after the last power step) takes CholeskyQR2.
   RSVD_CK(launch_gaussian(n, l, seed, 0u, RSVD_F64, W.om, n, P->stream));
   if ((rc = gemm<double>(P, A, lda, false, W.om, n, W.y, m, m, n, l))) return rc;
-  if ((rc = orth<double>(P, W.y, m, l, m, W.qm, m, nullptr, false))) return rc;
+  if (q == 0) {
+    if ((rc = orth<double>(P, W.y, m, l, m, W.qm, m, nullptr, false))) return rc;
+  } else if ((rc = orth1<double>(P, W.y, m, l, m, W.qm, m))) {
+    return rc;
+  }
   // 4-5. power steps with orthonormalisation: W = orth(A^T Q), Q = orth(A W)
   for (int j = 0; j < q; ++j) {
     if ((rc = gemm<double>(P, A, lda, true, W.qm, m, W.z, n, n, m, l))) return rc;
-    if ((rc = orth<double>(P, W.z, n, l, n, W.om, n, nullptr, false))) return rc;
+    if ((rc = orth1<double>(P, W.z, n, l, n, W.om, n))) return rc;
     if ((rc = gemm<double>(P, A, lda, false, W.om, n, W.y, m, m, n, l))) return rc;
-    if ((rc = orth<double>(P, W.y, m, l, m, W.qm, m, nullptr, false))) return rc;
+    if (j == q - 1) {
+      if ((rc = orth<double>(P, W.y, m, l, m, W.qm, m, nullptr, false))) return rc;
+    } else if ((rc = orth1<double>(P, W.y, m, l, m, W.qm, m))) {
+      return rc;
+    }
   }
   // 6. B^T = A^T Q;  7-8. small SVD and lift
   if ((rc = gemm<double>(P, A, lda, true, W.qm, m, W.z, n, n, m, l))) return rc;

@@ -38,7 +38,11 @@ struct MixedWork {
   size_t apart_floats;
 };
 
-Layout make_layout(int64_t m, int64_t n, int l, int mode, int num_sms);
+Layout make_layout(int64_t m, int64_t n, int l, int mode, int num_sms, bool f64tc = false);
+// RSVD_MODE_F64_TENSOR: builds A's digit slices and marks A as the matrix
+// whose passes run on the tensor cores until f64tc_end().
+int f64tc_begin(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t lda);
+inline void f64tc_end(rsvd_plan_t P) { P->tc_A = nullptr; }
 template <typename T>
 Work<T> work_of(rsvd_plan_t P);
 MixedWork mixed_work_of(rsvd_plan_t P);
@@ -59,6 +63,11 @@ int gram(rsvd_plan_t P, const T* Y, int64_t ldy, int64_t rows, int l, T* G);
 template <typename T>
 int orth(rsvd_plan_t P, const T* Y, int64_t rows, int l, int64_t ldy, T* Q, int64_t ldq,
          T* Rprod, bool transpose_R);
+
+// One CholeskyQR pass: Q = Y R^-1 (range(Q) = range(Y); columns orthonormal
+// to about u kappa(Y)^2).
+template <typename T>
+int orth1(rsvd_plan_t P, const T* Y, int64_t rows, int l, int64_t ldy, T* Q, int64_t ldq);
 
 // Steps 6-8 after B^T = A^T Q is in W.z and Q in W.qm (m x l): small SVD of
 // B, U = Q U~ and V, truncated to k columns, signs and output layout.

@@ -46,4 +46,52 @@ int launch_apass_fixup(const float* part, int grid, int64_t total, int kt, int b
                        int64_t rows_out, int64_t tiles, float* out, int64_t ldo, int accumulate,
                        cudaStream_t st);
 
+// The split tiles of a stream-K pass and their partial slots, listed on the
+// host (a kernel parameter): grid CTAs share `total` (tile, k-block)
+// iterations with kt k-blocks per tile; CTA c takes [total c / grid,
+// total (c+1) / grid) and writes the partials of its first and last (split)
+// tiles to slots 2c and 2c+1.
+constexpr int kFixMaxTiles = 192;
+constexpr int kFixMaxSrc = 512;
+struct FixList {
+  int n;                          // split tiles
+  int tile[kFixMaxTiles];
+  int off[kFixMaxTiles + 1];      // sources of tile i: src[off[i] .. off[i+1])
+  int src[kFixMaxSrc];            // partial slot (CTA * 2 + 0 first / 1 last tile)
+};
+int64_t host_begin(int64_t total, int c, int grid);
+int host_cta_of(int64_t g, int64_t total, int grid);
+// false when the list does not fit FixList.
+bool build_fix_list(int grid, int64_t total, int kt, int64_t tiles, FixList& fl);
+
+// FP64-accurate passes over A on the tensor cores (exact products of BF16
+// digit slices).  Preparation of A, once per A: its row exponents and six
+// digit slices (slices: 6 x ncol columns of ldsl rows, ncol = n rounded up to
+// 128; rmax: m ints).
+int f64tc_prepare_a(const double* A, int64_t m, int64_t n, int64_t lda, void* slices,
+                    int64_t ldsl, int64_t ncol, int* rmax, int* status, int num_sms,
+                    cudaStream_t st);
+struct F64tcCall {
+  bool ax;                 // true: out = A X (X n x l); false: out = A^T X (X m x l)
+  const void* slices;      // from f64tc_prepare_a
+  int64_t m, n, ldsl, ncol;
+  const int* rmax;
+  const double* X;
+  int64_t ldx;
+  int l;                   // output columns (any; blocks of <= 80 per pass)
+  double* out;
+  int64_t ldo;
+  // workspace
+  void* xslices;           // 6 * 80 rows of ldxs BF16 (ldxs >= rows of X, multiple of 8)
+  int64_t ldxs;
+  int* fexp;               // 80 ints
+  int64_t* raw_t;          // (m or n) x 80 int64
+  float* raw_r;            // (m or n) x 80 float
+  int64_t* part_t;         // partial slots: num_sms * 2 * 128 * 80
+  float* part_r;
+  long long wait_cycles = 0;
+};
+constexpr int kF64tcMaxL = 80;   // output columns per pass (six TMEM regions of <= 80)
+int launch_apass_f64tc(const F64tcCall& c, int num_sms, int* status, cudaStream_t st);
+
 }  // namespace rsvd

@@ -20,7 +20,7 @@ from . import _lib
 
 F64, F32, BF16, FP8E4M3 = 0, 1, 2, 3
 ERR_NOT_REACHED = 8
-PLAIN, MIXED = 0, 1
+PLAIN, MIXED, F64_TENSOR = 0, 1, 2
 STATUS = {0: "ok", 1: "cholesky", 2: "jacobi", 3: "timeout", 4: "workspace", 5: "cuda",
           6: "nonfinite", 7: "unsupported"}
 
@@ -111,6 +111,14 @@ def rsvd_plan_set_stream(plan, stream=None) -> None:
 
 def rsvd_plan_set_wait_limit(plan, cycles) -> int:
     return _lib.load().rsvd_plan_set_wait_limit(plan, int(cycles))
+
+
+def rsvd_plan_prepare_a(plan, A, m, n, lda) -> int:
+    return _lib.load().rsvd_plan_prepare_a(plan, _ptr(A), m, n, lda)
+
+
+def rsvd_plan_release_a(plan) -> int:
+    return _lib.load().rsvd_plan_release_a(plan)
 
 
 def rsvd_set_tile_scales(plan, scales, rows, cols, lds) -> int:
@@ -314,7 +322,7 @@ class Plan:
     def solve_algorithm(self, algorithm, A, m, n, k, p, q, seed, lda=None):
         """Algorithm 2, 3, 4 or 6 of the thesis: (U, S, VT) as solve(); enqueued only."""
         lda = lda or A.shape[1]
-        odt = torch.float64 if self.mode == PLAIN else torch.float32
+        odt = torch.float64 if self.mode != MIXED else torch.float32
         U = torch.empty(k, m, dtype=odt, device=A.device)
         S = torch.empty(k, dtype=torch.float64, device=A.device)
         VT = torch.empty(n, k, dtype=odt, device=A.device)
@@ -399,7 +407,7 @@ class Plan:
         """A: column-major device tensor (n, lda).  Returns (U, S, VT) as
         column-major tensors U (k, m), S (k,), VT (n, k); enqueued only."""
         lda = lda or A.shape[1]
-        odt = torch.float64 if self.mode == PLAIN else torch.float32
+        odt = torch.float64 if self.mode != MIXED else torch.float32
         if out is None:
             U = torch.empty(k, m, dtype=odt, device=A.device)
             S = torch.empty(k, dtype=torch.float64, device=A.device)
