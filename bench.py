@@ -584,7 +584,9 @@ def run_ours(args):
     a_bytes = m * n * 8
     dA = _make_input(w, rank)
     stream = torch.cuda.current_stream()
-    plan = R.Plan(m, n, l)
+    # FP64 results; the passes over A on the tensor cores (exact products of
+    # BF16 digit slices), every other step in FP64 on the CUDA cores
+    plan = R.Plan(m, n, l, mode=R.F64_TENSOR)
     U = torch.empty(k, m, dtype=torch.float64, device="cuda")
     S = torch.empty(k, dtype=torch.float64, device="cuda")
     VT = torch.empty(n, k, dtype=torch.float64, device="cuda")
@@ -627,39 +629,50 @@ def run_ours(args):
     value, ms_max = job_rate(args.steps, ms, world)
     ms_per_step = ms_max / args.steps
 
-    # --- the dominant kernels, timed alone through the step entry points ---
+    # --- the dominant kernel, timed alone: the tensor pass on a prepared A ---
     Om = R.colmajor(n, l)
     Y = R.colmajor(m, l)
     Z = R.colmajor(n, l)
     R.rsvd_gaussian(plan.handle, n, l, seed, 0, R.F64, Om, n)
     Qm = torch.linalg.qr(torch.randn(m, l, dtype=torch.float64, device="cuda"))[0].T.contiguous()
-
+    R._check(R.rsvd_plan_prepare_a(plan.handle, dA, m, n, m), "rsvd_plan_prepare_a")
     t_an, how = _time_calls(plan.handle,
-                            lambda: R.rsvd_apply_a(plan.handle, dA, m, n, m, Om, n, l, Y, m), reps=5)
+                            lambda: R.rsvd_apply_a(plan.handle, dA, m, n, m, Om, n, l, Y, m), reps=10)
     t_at, _ = _time_calls(plan.handle,
-                          lambda: R.rsvd_apply_at(plan.handle, dA, m, n, m, Qm, m, l, Z, n), reps=5)
-    flops = 2.0 * m * n * l
+                          lambda: R.rsvd_apply_at(plan.handle, dA, m, n, m, Qm, m, l, Z, n), reps=10)
+    R.rsvd_plan_release_a(plan.handle)
+    t_prep, _ = _time_calls(plan.handle,
+                            lambda: R.rsvd_plan_prepare_a(plan.handle, dA, m, n, m), reps=3)
+    R.rsvd_plan_release_a(plan.handle)
     peaks, peak_kind = _peaks()
-    sm_max = peaks.get("sm_max_mhz", 2070.0)
-    fp64_peak = 152 * 2 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s: 152 SMs x 2 DFMA/clk x 2 flop
+    hbm = peaks.get("hbm_gbs", 6800.0)
     dom_ms = max(t_an, t_at)
-    dom = "gemm_simt_kernel<double,5,true> (A^T X pass)" if t_at >= t_an else \
-        "gemm_simt_kernel<double,5,false> (A X pass)"
-    achieved = flops / (dom_ms / 1e3) / 1e12
-    traffic = _traffic_from_profile("plain-fp64", "atx" if t_at >= t_an else "ax")
-    roofline = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 4),
-                "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
-                "frac": round(achieved / fp64_peak, 4),
-                "traffic": traffic,
-                "peak_source": f"derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x {sm_max:.0f} MHz",
-                "algorithmic_flops_per_launch": flops,
+    ax_dom = t_an >= t_at
+    dom = "apass_f64tc_kernel<%s,80,28> (%s pass)" % ((1, "A X") if ax_dom else (0, "A^T X"))
+    achieved = a_bytes / (dom_ms / 1e3) / 1e9
+    products = 21          # BF16 digit products kept per pair of FP64 elements
+    mma_flops = products * 2.0 * m * n * l
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
+                "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                "traffic": _traffic_from_profile("plain-fp64-tensor", "ax" if ax_dom else "atx"),
+                "algorithmic_bytes_per_launch": a_bytes,
+                "bytes_streamed_per_launch": m * n * 12,
                 "ms_per_launch": round(dom_ms, 4),
-                "timing": f"{how}: main kernel + split-K reduction per pass"}
+                "tensor_view": {"mma_flops_per_launch": mma_flops,
+                                "achieved_tflops": round(mma_flops / (dom_ms / 1e3) / 1e12, 1),
+                                "peak_bf16_tflops": peaks.get("bf16_tflops"),
+                                "frac": round(mma_flops / (dom_ms / 1e3) / 1e12 /
+                                              peaks.get("bf16_tflops", 1900.0), 4)},
+                "timing": f"{how}: slicing of X + pass + finalize per call, A prepared once "
+                          "(algorithmic bytes = the FP64 A; the pass streams A's six BF16 digit "
+                          "slices, 12 bytes per element)"}
     a_pass = {"ms_ax": round(t_an, 4), "ms_atx": round(t_at, 4),
+              "ms_prepare_a": round(t_prep, 4),
               "gbps_ax": round(a_bytes / (t_an / 1e3) / 1e9, 2),
               "gbps_atx": round(a_bytes / (t_at / 1e3) / 1e9, 2),
               "gbps_in_solve": round(passes * a_bytes / (ms_per_step / 1e3) / 1e9, 2),
-              "hbm_peak_gbs": peaks.get("hbm_gbs"), "passes_per_solve": passes}
+              "hbm_peak_gbs": hbm, "passes_per_solve": passes}
+    plain_simt = run_plain_simt(args, world, dA, w)
 
     # --- end to end through the C ABI with host buffers ---
     A_h = torch.empty(dA.shape, dtype=dA.dtype, pin_memory=True)
@@ -746,6 +759,7 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (A is %.2f GB; L2 129 MB): no flush" % (a_bytes / 1e9)},
         "a_pass": a_pass,
         "roofline": roofline,
+        "plain_simt": plain_simt,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "singlepass": singlepass,
@@ -768,6 +782,62 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_plain_simt(args, world, dA, w):
+    """The same FP64 solve with every pass over A on the CUDA cores (FP64
+    FMA), and that pass alone against the FP64 ALU roofline."""
+    import torch
+
+    from paper_2402_17794_gb300 import rsvd as R
+
+    m, n, k, p, q, seed = w["m"], w["n"], w["k"], w["p"], w["q"], w["seed"]
+    l = k + p
+    plan = R.Plan(m, n, l)
+    U = torch.empty(k, m, dtype=torch.float64, device="cuda")
+    S = torch.empty(k, dtype=torch.float64, device="cuda")
+    VT = torch.empty(n, k, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        R._check(R.rsvd_solve(plan.handle, dA, m, n, m, k, p, q, seed, U, m, S, VT, k),
+                 "rsvd_solve (FP64 on the CUDA cores)")
+
+    step()
+    steps = 3
+    _barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    st = plan.status()
+    if st != 0:
+        raise RuntimeError(f"FP64 CUDA-core solve failed: {R.rsvd_status_string(st)}")
+    ms = _max_over_ranks(e0.elapsed_time(e1), world)
+    Om = R.colmajor(n, l)
+    Y = R.colmajor(m, l)
+    R.rsvd_gaussian(plan.handle, n, l, seed, 0, R.F64, Om, n)
+    t_an, how = _time_calls(plan.handle,
+                            lambda: R.rsvd_apply_a(plan.handle, dA, m, n, m, Om, n, l, Y, m), reps=3)
+    flops = 2.0 * m * n * l
+    peaks, _ = _peaks()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    fp64_peak = 152 * 2 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s: 152 SMs x 2 DFMA/clk x 2 flop
+    achieved = flops / (t_an / 1e3) / 1e12
+    del plan
+    return {"workload": "the same FP64 solve with the passes over A on the CUDA cores (FP64 FMA)",
+            "value": round(steps * world / (ms / 1e3), 4), "unit": "solves/s",
+            "ms_per_solve": round(ms / steps, 4), "dtype": "f64",
+            "roofline": {"bound": "alu", "kernel": "gemm_simt_kernel<double,5,false> (A X pass)",
+                         "achieved": round(achieved, 4), "peak": round(fp64_peak, 4),
+                         "unit": "TFLOP/s", "frac": round(achieved / fp64_peak, 4),
+                         "peak_source": f"derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x "
+                                        f"{sm_max:.0f} MHz",
+                         "ms_per_launch": round(t_an, 4), "timing": how}}
 
 
 def run_singlepass(args, world, dA, w, plan, algorithm=6):
@@ -984,7 +1054,8 @@ def run_reference(args):
 def run_profile_case(args):
     """A reduced case of the same kernels for ncu captures (no timing):
     A 8192 x 4096 FP64 (268 MB, larger than L2), l = 80: two passes of each
-    kind, one full solve and two SRFT sketches; A 16384 x 16384 BF16 and
+    kind and one full solve on the CUDA cores, the same on the tensor cores
+    (A prepared once), and two SRFT sketches; A 16384 x 16384 BF16 and
     FP8, l = 160: two passes of each kind and one mixed solve."""
     import numpy as np
     import torch
@@ -1010,6 +1081,19 @@ def run_profile_case(args):
     st = plan.status()
     if st != 0:
         raise RuntimeError(R.rsvd_status_string(st))
+    # FP64 passes on the tensor cores: A prepared once (six BF16 digit slices,
+    # 403 MB), then two passes of each kind and one full solve
+    tplan = R.Plan(m, n, l, mode=R.F64_TENSOR)
+    R._check(R.rsvd_plan_prepare_a(tplan.handle, dA, m, n, m), "rsvd_plan_prepare_a")
+    for _ in range(2):
+        R.rsvd_apply_a(tplan.handle, dA, m, n, m, Om, n, l, Y, m)
+        R.rsvd_apply_at(tplan.handle, dA, m, n, m, Y, m, l, Z, n)
+    R.rsvd_plan_release_a(tplan.handle)
+    tplan.solve(dA, m, n, k, p, q, 3)
+    st = tplan.status()
+    if st != 0:
+        raise RuntimeError(R.rsvd_status_string(st))
+    del tplan
     # the SRFT sketch through the FFT (n = 4096, a multiple of 64), l = 80
     splan = R.Plan(m, n, 2 * l)
     for _ in range(2):

@@ -195,12 +195,41 @@ __global__ void slice_x_kernel(const double* __restrict__ X, int64_t rows, int l
 // Pass kernel
 // ---------------------------------------------------------------------------
 
-// One tcgen05.mma of the k-block: A slice s times X slices t0 .. t0+cnt-1
-// into regions reg0 .. reg0+cnt-1; tail: regions >= TC_EXACT.
-struct TcMma {
-  int s, t0, cnt, reg0, tail;
-  uint32_t idesc;
+// The MMA schedule of one k-block for region width W, fixed at compile
+// time: per A slice s, the X slices t with s + t < 6, exact regions (g < 4)
+// and tail regions apart, each run cut into balanced pieces of at most
+// 256 / W slices (N = count * W <= 256).  With it the k-block's MMAs
+// unroll into straight-line issue with constant descriptor offsets.
+struct MmaSched {
+  int n;
+  int s[TC_MAX_MMA], t0[TC_MAX_MMA], cnt[TC_MAX_MMA], reg0[TC_MAX_MMA], tail[TC_MAX_MMA];
 };
+
+__host__ __device__ constexpr MmaSched make_sched(int W) {
+  MmaSched m{};
+  const int maxc = 256 / W;
+  for (int s = 0; s < TC_S; ++s) {
+    for (int tail = 0; tail < 2; ++tail) {
+      const int g_lo = tail ? (TC_EXACT > s ? TC_EXACT : s) : s;
+      const int g_hi = tail ? TC_S - 1 : TC_EXACT - 1;
+      if (g_lo > g_hi) continue;
+      const int cnt = g_hi - g_lo + 1;
+      const int pieces = (cnt + maxc - 1) / maxc;
+      int g = g_lo;
+      for (int p = 0; p < pieces; ++p) {
+        const int c = (cnt - (g - g_lo) + (pieces - p) - 1) / (pieces - p);
+        m.s[m.n] = s;
+        m.t0[m.n] = g - s;
+        m.cnt[m.n] = c;
+        m.reg0[m.n] = g;
+        m.tail[m.n] = tail;
+        ++m.n;
+        g += c;
+      }
+    }
+  }
+  return m;
+}
 
 struct TcArgs {
   int64_t rows_out;     // m (AX) or n (A^T X)
@@ -208,9 +237,6 @@ struct TcArgs {
   int kt;
   int l;                // output columns of this pass (<= W)
   int64_t ncol;         // columns per A slice in the slice buffer
-  int n_mma;
-  int first[TC_S + 1];  // MMAs of A slice s: mma[first[s] .. first[s+1])
-  TcMma mma[TC_MAX_MMA];
   int64_t* raw_t;       // full tiles: rows_out x l (ld rows_out)
   float* raw_r;
   int64_t* part_t;      // split tiles: slot (cta * 2 + first/last) of 128 x l (ld 128)
@@ -341,6 +367,7 @@ apass_f64tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     if (lane == 0) {
       constexpr uint64_t a_kstep = AX ? (2048 >> 4) : (32 >> 4);
       constexpr uint64_t b_kstep = 32 >> 4;
+      const uint32_t abuf_u32 = smem_u32(abuf);
       int64_t t = g0 / args.kt;
       int kb = (int)(g0 - t * args.kt);
       int kc = 0;               // k-blocks since the segment began
@@ -366,29 +393,31 @@ apass_f64tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
           break;
         }
         const uint64_t xd = sdesc(smem_u32(xbuf + xs * X_BYTES), 16, 1024);
-        for (int s = 0; s < TC_S && ok; ++s) {
-          if (!mbar_wait(&afull[s], (uint32_t)(i & 1), abort_flag, args.wait_cycles)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t a_base = smem_u32(abuf + s * A_SLAB);
-          // MN-major A (AX): two 64-row MN atoms 8192 bytes apart, 8-row K
-          // groups 1024 apart; K-major A (A^T X): 8-row groups 1024 apart
-          const uint64_t ad = AX ? sdesc(a_base, TC_BK * 128, 1024) : sdesc(a_base, 16, 1024);
-          const int e0 = args.first[s], e1 = args.first[s + 1];
+        constexpr MmaSched SC = make_sched(W);
 #pragma unroll
-          for (int kk = 0; kk < TC_BK / 16; ++kk) {
-            for (int e = e0; e < e1; ++e) {
-              const TcMma& mm = args.mma[e];
-              // X slice t0 starts t0 * X_SLAB bytes into the buffer (16-byte units)
-              const uint64_t bd = xd + (uint64_t)((mm.t0 * X_SLAB) >> 4) + kk * b_kstep;
-              const bool init = (s == 0) && kk == 0 && (mm.tail ? seg_first : chunk_first);
-              umma_bf16(tmem_base + (uint32_t)(mm.reg0 * W), ad + kk * a_kstep, bd, mm.idesc,
-                        init ? 0u : 1u);
+        for (int s = 0; s < TC_S; ++s) {
+          if (ok && !mbar_wait(&afull[s], (uint32_t)(i & 1), abort_flag, args.wait_cycles))
+            ok = false;
+          if (ok) {
+            tc_fence_after();
+            const uint32_t a_base = abuf_u32 + s * A_SLAB;
+            // MN-major A (AX): two 64-row MN atoms 8192 bytes apart, 8-row K
+            // groups 1024 apart; K-major A (A^T X): 8-row groups 1024 apart
+            const uint64_t ad = AX ? sdesc(a_base, TC_BK * 128, 1024) : sdesc(a_base, 16, 1024);
+#pragma unroll
+            for (int kk = 0; kk < TC_BK / 16; ++kk) {
+#pragma unroll
+              for (int e = 0; e < SC.n; ++e) {
+                if (SC.s[e] != s) continue;
+                // X slice t0 starts t0 * X_SLAB bytes into the buffer (16-byte units)
+                const uint64_t bd = xd + (uint64_t)((SC.t0[e] * X_SLAB) >> 4) + kk * b_kstep;
+                const bool init = (s == 0) && kk == 0 && (SC.tail[e] ? seg_first : chunk_first);
+                umma_bf16(tmem_base + (uint32_t)(SC.reg0[e] * W), ad + kk * a_kstep, bd,
+                          idesc_bf16(TC_BM, SC.cnt[e] * W, AX), init ? 0u : 1u);
+              }
             }
+            umma_commit(&aempty[s]);    // A buffer s is free once these finish
           }
-          umma_commit(&aempty[s]);    // A buffer s is free once these finish
         }
         if (!ok) break;
         umma_commit(&xempty[xs]);
@@ -572,37 +601,6 @@ bool make_map_x(CUtensorMap* map, const void* base, int64_t kdim, int rows, int6
   return make_map_bf16(map, base, kdim, rows, ldxs, 64, W);
 }
 
-// The MMA list of one k-block for region width W: per A slice s, the X
-// slices t with s + t < 6, exact regions (g < 4) and tail regions apart,
-// each run cut into pieces of at most 256 / W slices (balanced).
-int build_mma_list(int W, bool ax, TcMma* out) {
-  int n = 0;
-  const int maxc = 256 / W;
-  for (int s = 0; s < TC_S; ++s) {
-    for (int tail = 0; tail < 2; ++tail) {
-      const int g_lo = tail ? std::max(TC_EXACT, s) : s;
-      const int g_hi = tail ? TC_S - 1 : TC_EXACT - 1;
-      if (g_lo > g_hi) continue;
-      const int cnt = g_hi - g_lo + 1;
-      const int pieces = (cnt + maxc - 1) / maxc;
-      int g = g_lo;
-      for (int p = 0; p < pieces; ++p) {
-        const int c = (cnt - (g - g_lo) + (pieces - p) - 1) / (pieces - p);
-        if (n >= TC_MAX_MMA) return -1;
-        out[n].s = s;
-        out[n].t0 = g - s;
-        out[n].cnt = c;
-        out[n].reg0 = g;
-        out[n].tail = tail;
-        out[n].idesc = idesc_bf16(TC_BM, c * W, ax);
-        ++n;
-        g += c;
-      }
-    }
-  }
-  return n;
-}
-
 }  // namespace
 
 int f64tc_prepare_a(const double* A, int64_t m, int64_t n, int64_t lda, void* slices,
@@ -660,12 +658,6 @@ int launch_apass_f64tc(const F64tcCall& c, int num_sms, int* status, cudaStream_
     a.kt = kt;
     a.l = lb;
     a.ncol = c.ncol;
-    a.n_mma = build_mma_list(W, c.ax, a.mma);
-    if (a.n_mma < 0) return RSVD_ERR_UNSUPPORTED;
-    for (int s = 0, e = 0; s <= TC_S; ++s) {   // the list is ordered by slice
-      while (e < a.n_mma && a.mma[e].s < s) ++e;
-      a.first[s] = e;
-    }
     a.raw_t = c.raw_t;
     a.raw_r = c.raw_r;
     a.part_t = c.part_t;
