@@ -1,0 +1,343 @@
+// Cholesky factor R (G = R^T R) and its inverse of the l x l Gram matrix of
+// CholeskyQR (Algorithm 4, steps 3 and 5, Section 3.3), in FP64 arithmetic
+// whatever the element type of G, R and R^-1, spread over the GPU.
+//
+// One SM's FP64 pipe does 2 FMA per clock on this part, so a one-CTA
+// factorisation of l = 80 needs at least 60 us and one of l = 288 several
+// milliseconds; here every step but the 32 x 32 diagonal blocks runs on
+// many SMs.  Right-looking blocked Cholesky with 32-wide panels
+// P = [p0, p0 + 32):
+//   1. R_PP = chol(G_PP) and X_PP = R_PP^-1 (one CTA);
+//   2. the panel row R_PJ = X_PP^T G_PJ for J beyond the panel;
+//   3. the trailing update G_JK -= R_PJ^T R_PK (upper triangle);
+// then X = R^-1 by block rows from the bottom up:
+//   X_IJ = -X_II sum_{I < K <= J} R_IK X_KJ.
+// A pivot d_j <= tol (tol = drop * max diag(G)) marks a dependent column: its
+// row of R and its row and column of R^-1 are zero, as in the one-CTA
+// kernels, and the count goes to DeviceStatus::deficient.  A non-finite
+// diagonal raises RSVD_ERR_NONFINITE and zeroes R and R^-1.
+#include <algorithm>
+#include <cfloat>
+
+#include "internal.h"
+
+namespace rsvd {
+namespace {
+
+constexpr int CB = 32;    // panel width
+constexpr int TB = 16;    // output tile of the panel-row, update and inverse kernels
+
+struct CholCtl {
+  double tol;
+  int bad;
+  int def;
+};
+
+template <typename T>
+__global__ void chol64_setup_kernel(const T* __restrict__ G, int64_t ldg, int l, double drop,
+                                    double* __restrict__ W, double* __restrict__ R,
+                                    double* __restrict__ X, CholCtl* ctl) {
+  if (blockIdx.x == 0) {
+    __shared__ double s_mx[32];
+    __shared__ int s_bad[32];
+    double mx = 0.0;
+    int bad = 0;
+    for (int j = threadIdx.x; j < l; j += blockDim.x) {
+      const double d = (double)G[j + (int64_t)j * ldg];
+      if (!isfinite(d)) bad = 1;
+      mx = fmax(mx, fabs(d));
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+      s_mx[w] = mx;
+      s_bad[w] = bad;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+        mx = fmax(mx, s_mx[i]);
+        bad |= s_bad[i];
+      }
+      ctl->tol = drop * mx;
+      ctl->bad = bad;
+      ctl->def = 0;
+    }
+  }
+  const int64_t ll = (int64_t)l * l;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ll;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % l), j = (int)(t / l);
+    W[t] = i <= j ? (double)G[i + (int64_t)j * ldg] : 0.0;
+    R[t] = 0.0;
+    X[t] = 0.0;
+  }
+}
+
+// Step 1 for the panel at p0: the nb x nb diagonal block, by one elimination
+// on [G_PP | I] (Gauss without pivoting, stable for an SPD matrix): with
+// G_PP = L D L^T, pivot j subtracts (a_ji / d_j) row_j from every row i > j,
+// which turns G's upper triangle into D L^T and the identity into L^-1, so
+//   R_PP = D^1/2 L^T,  R_PP^-1 = L^-T D^-1/2.
+// One matrix holds both halves: A[i][k] for i <= k the upper part, for i > k
+// the strict lower part of L^-1 (unit diagonal implicit).  Each of the 256
+// threads owns four of the 32 x 32 entries; every pivot is one update phase
+// and one barrier, and the thread owning the next pivot forms its scales
+// (1/d, 1/sqrt d, sqrt d) right after updating it.  No divisions elsewhere.
+__device__ __forceinline__ void pivot_scales64(double d, double tol, double* inv, double* rs,
+                                               double* sq, int* def) {
+  if (d > tol) {
+    const double r = sqrt(d);
+    *sq = r;
+    *rs = 1.0 / r;
+    *inv = *rs * *rs;
+  } else {
+    *sq = 0.0;
+    *rs = 0.0;
+    *inv = 0.0;
+    atomicAdd(def, 1);
+  }
+}
+
+__global__ void __launch_bounds__(256) chol64_diag_kernel(const double* __restrict__ W, int l,
+                                                          int p0, double* __restrict__ R,
+                                                          double* __restrict__ X,
+                                                          CholCtl* ctl) {
+  if (ctl->bad) return;
+  __shared__ double A[CB][CB + 1];
+  __shared__ double s_inv[CB], s_rs[CB], s_sq[CB];
+  const int tid = threadIdx.x;
+  const int nb = min(CB, l - p0);
+  const double tol = ctl->tol;
+  for (int e = tid; e < CB * CB; e += 256) {
+    const int i = e & (CB - 1), k = e >> 5;
+    A[i][k] = (i <= k && k < nb) ? W[p0 + i + (int64_t)(p0 + k) * l] : 0.0;
+  }
+  __syncthreads();
+  if (tid == 0) pivot_scales64(A[0][0], tol, &s_inv[0], &s_rs[0], &s_sq[0], &ctl->def);
+  __syncthreads();
+  for (int j = 0; j < nb; ++j) {
+    const double inv = s_inv[j];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + 256 * q;
+      const int i = e & (CB - 1), k = e >> 5;
+      if (i <= j || i >= nb || k >= nb) continue;
+      if (i <= k) {
+        // Schur complement: a_ik -= (a_ji / d_j) a_jk
+        A[i][k] = fma(-A[j][i] * inv, A[j][k], A[i][k]);
+        if (i == j + 1 && k == j + 1)
+          pivot_scales64(A[i][k], tol, &s_inv[i], &s_rs[i], &s_sq[i], &ctl->def);
+      } else if (k <= j) {
+        // L^-1 row i: e_ik -= (a_ji / d_j) e_jk  (e_jj = 1)
+        const double ejk = (k == j) ? 1.0 : A[j][k];
+        A[i][k] = fma(-A[j][i] * inv, ejk, A[i][k]);
+      }
+    }
+    __syncthreads();
+  }
+  // R_PP[i][k] = A[i][k] / sqrt(d_i) (k > i), sqrt(d_i) (k = i);
+  // R_PP^-1[c][i] = (L^-1)[i][c] / sqrt(d_i) (c < i), 1 / sqrt(d_i) (c = i)
+  for (int e = tid; e < CB * CB; e += 256) {
+    const int i = e & (CB - 1), k = e >> 5;
+    if (i >= nb || k >= nb) continue;
+    if (i < k) {
+      R[p0 + i + (int64_t)(p0 + k) * l] = A[i][k] * s_rs[i];
+      X[p0 + i + (int64_t)(p0 + k) * l] = A[k][i] * s_rs[k];
+    } else if (i == k) {
+      R[p0 + i + (int64_t)(p0 + i) * l] = s_sq[i];
+      X[p0 + i + (int64_t)(p0 + i) * l] = s_rs[i];
+    }
+  }
+}
+
+// Step 2: R[P][J0 .. J0+TB) = X_PP^T W[P][J0 .. J0+TB) for columns beyond
+// the panel; one block per TB columns, 256 threads, two outputs each.
+__global__ void chol64_panel_kernel(const double* __restrict__ W, int l, int p0,
+                                    double* __restrict__ R, const double* __restrict__ X,
+                                    const CholCtl* ctl) {
+  if (ctl->bad) return;
+  __shared__ double Xp[CB][CB + 1];
+  __shared__ double Gp[CB][TB + 1];
+  const int tid = threadIdx.x;
+  const int nb = min(CB, l - p0);
+  const int p1 = p0 + nb;
+  const int j0 = p1 + blockIdx.x * TB;
+  for (int e = tid; e < CB * CB; e += blockDim.x) {
+    const int b = e % CB, a = e / CB;
+    Xp[b][a] = (b < nb && a < nb) ? X[p0 + b + (int64_t)(p0 + a) * l] : 0.0;
+  }
+  for (int e = tid; e < CB * TB; e += blockDim.x) {
+    const int b = e % CB, c = e / CB;
+    const int j = j0 + c;
+    Gp[b][c] = (b < nb && j < l) ? W[p0 + b + (int64_t)j * l] : 0.0;
+  }
+  __syncthreads();
+  for (int e = tid; e < CB * TB; e += blockDim.x) {
+    const int a = e % CB, c = e / CB;
+    const int j = j0 + c;
+    if (a >= nb || j >= l) continue;
+    double s = 0.0;
+    for (int b = 0; b <= a; ++b) s = fma(Xp[b][a], Gp[b][c], s);   // X_PP upper: b <= a
+    R[p0 + a + (int64_t)j * l] = s;
+  }
+}
+
+// Step 3: W[i][k] -= sum_a R[p0+a][i] R[p0+a][k] for p1 <= i <= k < l, one
+// block per TB x TB tile (ti <= tk), one output per thread.
+__global__ void chol64_update_kernel(double* __restrict__ W, int l, int p0,
+                                     const double* __restrict__ R, const CholCtl* ctl) {
+  if (ctl->bad) return;
+  // tile pair from the linear block index: tiles over [p1, l), upper only
+  const int nb = min(CB, l - p0);
+  const int p1 = p0 + nb;
+  const int nt = (l - p1 + TB - 1) / TB;
+  int b = blockIdx.x, ti = 0;
+  while (b >= nt - ti) {
+    b -= nt - ti;
+    ++ti;
+  }
+  const int tk = ti + b;
+  __shared__ double Ri[CB][TB + 1];
+  __shared__ double Rk[CB][TB + 1];
+  const int tid = threadIdx.x;
+  const int i0 = p1 + ti * TB, k0 = p1 + tk * TB;
+  for (int e = tid; e < CB * TB; e += blockDim.x) {
+    const int a = e % CB, c = e / CB;
+    Ri[a][c] = (a < nb && i0 + c < l) ? R[p0 + a + (int64_t)(i0 + c) * l] : 0.0;
+    Rk[a][c] = (a < nb && k0 + c < l) ? R[p0 + a + (int64_t)(k0 + c) * l] : 0.0;
+  }
+  __syncthreads();
+  const int ii = tid % TB, kk = tid / TB;
+  const int i = i0 + ii, k = k0 + kk;
+  if (i >= l || k >= l || i > k) return;
+  double s = 0.0;
+#pragma unroll 8
+  for (int a = 0; a < CB; ++a) s = fma(Ri[a][ii], Rk[a][kk], s);
+  W[i + (int64_t)k * l] -= s;
+}
+
+// Inverse, block row I = [q0, q0 + nq): X[I][j] = -X_II sum_{k >= q1} R[I][k] X[k][j]
+// for j in [q1, l) (the rows below are final; X is upper, so the terms with
+// k > j vanish).  One block per TB columns; the sum runs over 32-row chunks
+// staged in shared memory.
+__global__ void __launch_bounds__(256) chol64_inv_kernel(const double* __restrict__ R,
+                                                         double* __restrict__ X, int l, int q0,
+                                                         const CholCtl* ctl) {
+  if (ctl->bad) return;
+  const int nq = min(CB, l - q0);
+  const int q1 = q0 + nq;
+  const int j0 = q1 + blockIdx.x * TB;
+  __shared__ double Rc[CB][CB + 1];
+  __shared__ double Xc[CB][TB + 1];
+  __shared__ double S[CB][TB + 1];
+  const int tid = threadIdx.x;
+  const int a0 = tid & (CB - 1), c0 = tid >> 5;   // outputs (a0, c0) and (a0, c0 + 8)
+  double s0 = 0.0, s1 = 0.0;
+  for (int k0 = q1; k0 < l; k0 += CB) {
+    for (int e = tid; e < CB * CB; e += 256) {
+      const int a = e & (CB - 1), kk = e >> 5;
+      Rc[a][kk] = (a < nq && k0 + kk < l) ? R[q0 + a + (int64_t)(k0 + kk) * l] : 0.0;
+    }
+    for (int e = tid; e < CB * TB; e += 256) {
+      const int kk = e & (CB - 1), c = e >> 5;
+      Xc[kk][c] = (k0 + kk < l && j0 + c < l) ? X[k0 + kk + (int64_t)(j0 + c) * l] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < CB; ++kk) {
+      s0 = fma(Rc[a0][kk], Xc[kk][c0], s0);
+      s1 = fma(Rc[a0][kk], Xc[kk][c0 + 8], s1);
+    }
+    __syncthreads();
+  }
+  S[a0][c0] = s0;
+  S[a0][c0 + 8] = s1;
+  // X_II into Rc (upper)
+  for (int e = tid; e < CB * CB; e += 256) {
+    const int a = e & (CB - 1), b = e >> 5;
+    Rc[a][b] = (a < nq && b < nq && a <= b) ? X[q0 + a + (int64_t)(q0 + b) * l] : 0.0;
+  }
+  __syncthreads();
+  for (int cc = 0; cc < 2; ++cc) {
+    const int c = c0 + 8 * cc, j = j0 + c;
+    if (a0 >= nq || j >= l) continue;
+    double t = 0.0;
+    for (int b = a0; b < nq; ++b) t = fma(Rc[a0][b], S[b][c], t);
+    X[q0 + a0 + (int64_t)j * l] = -t;
+  }
+}
+
+template <typename T>
+__global__ void chol64_out_kernel(const double* __restrict__ R, const double* __restrict__ X,
+                                  int l, T* __restrict__ Ro, T* __restrict__ Xo, CholCtl* ctl,
+                                  DeviceStatus* status) {
+  const int64_t ll = (int64_t)l * l;
+  const bool bad = ctl->bad != 0;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ll;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    Ro[t] = bad ? T(0) : (T)R[t];
+    Xo[t] = bad ? T(0) : (T)X[t];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (bad) atomicOr(&status->flags, 1 << RSVD_ERR_NONFINITE);
+    else if (ctl->def) atomicAdd(&status->deficient, ctl->def);
+  }
+}
+
+}  // namespace
+
+size_t chol64_work_bytes(int l) { return (size_t)3 * l * l * sizeof(double) + 256; }
+
+// drop: FP64 Grams drop pivots below l eps64 max diag(G), FP32 Grams below
+// eps32 max diag(G): the rules of the one-CTA kernels for each element type.
+template <typename T>
+cudaError_t launch_chol64(const T* G, int64_t ldg, int l, T* R, T* Rinv, void* work,
+                          DeviceStatus* status, cudaStream_t st) {
+  const double drop = sizeof(T) == 8 ? (double)l * DBL_EPSILON : (double)FLT_EPSILON;
+  const size_t ll = (size_t)l * l;
+  double* W = (double*)work;
+  double* Rb = W + ll;
+  double* Xb = Rb + ll;
+  CholCtl* ctl = (CholCtl*)(Xb + ll);
+  const int blocks = (int)std::min<size_t>((ll + 255) / 256, 64);
+  chol64_setup_kernel<T><<<blocks, 256, 0, st>>>(G, ldg, l, drop, W, Rb, Xb, ctl);
+  note_launch();
+  cudaError_t e;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  for (int p0 = 0; p0 < l; p0 += CB) {
+    chol64_diag_kernel<<<1, 256, 0, st>>>(W, l, p0, Rb, Xb, ctl);
+    note_launch();
+    const int p1 = std::min(l, p0 + CB);
+    if (p1 < l) {
+      const int nt = (l - p1 + TB - 1) / TB;
+      chol64_panel_kernel<<<nt, 256, 0, st>>>(W, l, p0, Rb, Xb, ctl);
+      note_launch();
+      chol64_update_kernel<<<nt * (nt + 1) / 2, TB * TB, 0, st>>>(W, l, p0, Rb, ctl);
+      note_launch();
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  const int nblk = (l + CB - 1) / CB;
+  for (int I = nblk - 2; I >= 0; --I) {
+    const int q0 = I * CB;
+    const int q1 = std::min(l, q0 + CB);
+    const int nt = (l - q1 + TB - 1) / TB;
+    chol64_inv_kernel<<<nt, 256, 0, st>>>(Rb, Xb, l, q0, ctl);
+    note_launch();
+  }
+  chol64_out_kernel<T><<<blocks, 256, 0, st>>>(Rb, Xb, l, R, Rinv, ctl, status);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_chol64<double>(const double*, int64_t, int, double*, double*, void*,
+                                           DeviceStatus*, cudaStream_t);
+template cudaError_t launch_chol64<float>(const float*, int64_t, int, float*, float*, void*,
+                                          DeviceStatus*, cudaStream_t);
+
+}  // namespace rsvd

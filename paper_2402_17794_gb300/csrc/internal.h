@@ -49,6 +49,7 @@ struct Layout {
   size_t om16, y32;
   size_t small_stride;  // bytes of one l x l FP64 matrix (padded)
   size_t refine;        // FP64 / FP32 l x l scratch of the small SVD (step 7)
+  size_t chol64;        // scratch of the FP64 multi-kernel Cholesky
   // RSVD_MODE_F64_TENSOR: A's digit slices, row exponents, the operand's
   // slices and exponents, raw outputs and partial slots of the passes
   size_t tc_slices, tc_rmax, tc_xs, tc_fexp, tc_rawt, tc_rawr, tc_partt, tc_partr;
@@ -162,6 +163,15 @@ cudaError_t launch_jacobi_svd(const T* M, int l, int64_t ldm, T* sig, T* Um, int
 template <typename T>
 cudaError_t launch_finalize(T* U, int64_t m, int64_t ldu, int k, const T* Vk, int64_t n, T* VT,
                             int64_t ldvt, const T* sig, double* S, T* sign_work, cudaStream_t st);
+
+// Cholesky factor R (upper, G = R^T R) and R^-1 (both l x l, ld l) of the
+// Gram G (ldg) in FP64 arithmetic over many SMs (see chol64.cu); work:
+// chol64_work_bytes(l).  Dropped pivots and non-finite input as
+// launch_chol_inv.
+size_t chol64_work_bytes(int l);
+template <typename T>
+cudaError_t launch_chol64(const T* G, int64_t ldg, int l, T* R, T* Rinv, void* work,
+                          DeviceStatus* status, cudaStream_t st);
 
 // FP64 refinement of an approximate SVD M = U diag(s) V^T (all l x l, ld l),
 // `steps` steps in place (see svd_refine.cu); work: 8 l^2 doubles.

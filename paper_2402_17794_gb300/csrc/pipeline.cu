@@ -135,6 +135,7 @@ Layout make_layout(int64_t m, int64_t n, int l, int mode, int num_sms, bool f64t
   L.sp = take(L.small_stride * kSinglePassSlots + align_up(kSinglePassVecs * (size_t)l * e));
   L.ad = take((size_t)m * l * e);
   L.refine = take(((size_t)16 * l * l + 4 * (size_t)l) * sizeof(double));
+  L.chol64 = take(chol64_work_bytes(l));
   if (mode == RSVD_MODE_MIXED) {
     const int l16 = (l + 15) / 16 * 16;
     L.om16 = take((size_t)round8(mn) * 3 * l16 * sizeof(__nv_bfloat16));
@@ -288,6 +289,19 @@ template int gemm<float>(rsvd_plan_t, const float*, int64_t, bool, const float*,
 template int gram<double>(rsvd_plan_t, const double*, int64_t, int64_t, int, double*);
 template int gram<float>(rsvd_plan_t, const float*, int64_t, int64_t, int, float*);
 
+// R and R^-1 of the Gram G (ld l): the FP64 multi-kernel Cholesky for
+// l >= 32 on both paths (FP64 arithmetic whatever T is), the one-CTA
+// kernels below that.
+template <typename T>
+int chol(rsvd_plan_t P, const T* G, int l, T* R, T* Rinv) {
+  const Work<T> W = work_of<T>(P);
+  if (l >= 32)
+    RSVD_CK(launch_chol64<T>(G, l, l, R, Rinv, P->ws + P->lay.chol64, dstatus(P), P->stream));
+  else
+    RSVD_CK(launch_chol_inv<T>(G, l, l, R, Rinv, W.cholw, dstatus(P), P->stream));
+  return RSVD_OK;
+}
+
 template <typename T>
 int orth(rsvd_plan_t P, const T* Y, int64_t rows, int l, int64_t ldy, T* Q, int64_t ldq, T* Rprod,
          bool transpose_R) {
@@ -296,11 +310,11 @@ int orth(rsvd_plan_t P, const T* Y, int64_t rows, int l, int64_t ldy, T* Q, int6
   int rc;
   // pass 1: G = Y^T Y = R1^T R1, T1 = Y R1^-1
   if ((rc = gram<T>(P, Y, ldy, rows, l, W.G))) return rc;
-  RSVD_CK(launch_chol_inv<T>(W.G, l, l, W.R1, W.R1i, W.cholw, st, P->stream));
+  if ((rc = chol<T>(P, W.G, l, W.R1, W.R1i))) return rc;
   if ((rc = gemm<T>(P, Y, ldy, false, W.R1i, l, W.tmp, rows, rows, l, l, true))) return rc;
   // pass 2: G = T1^T T1 = R2^T R2, Q = T1 R2^-1
   if ((rc = gram<T>(P, W.tmp, rows, rows, l, W.G))) return rc;
-  RSVD_CK(launch_chol_inv<T>(W.G, l, l, W.R2, W.R2i, W.cholw, st, P->stream));
+  if ((rc = chol<T>(P, W.G, l, W.R2, W.R2i))) return rc;
   if (Q && (rc = gemm<T>(P, W.tmp, rows, false, W.R2i, l, Q, ldq, rows, l, l, true))) return rc;
   if (Rprod) RSVD_CK(launch_tri_product<T>(W.R2, W.R1, l, Rprod, transpose_R, P->stream));
   return RSVD_OK;
@@ -317,7 +331,7 @@ int orth1(rsvd_plan_t P, const T* Y, int64_t rows, int l, int64_t ldy, T* Q, int
   Work<T> W = work_of<T>(P);
   int rc;
   if ((rc = gram<T>(P, Y, ldy, rows, l, W.G))) return rc;
-  RSVD_CK(launch_chol_inv<T>(W.G, l, l, W.R1, W.R1i, W.cholw, dstatus(P), P->stream));
+  if ((rc = chol<T>(P, W.G, l, W.R1, W.R1i))) return rc;
   return gemm<T>(P, Y, ldy, false, W.R1i, l, Q, ldq, rows, l, l, true);
 }
 template int orth1<float>(rsvd_plan_t, const float*, int64_t, int, int64_t, float*, int64_t);
@@ -338,7 +352,7 @@ int orth_shifted(rsvd_plan_t P, const T* Y, int64_t rows, int l, int64_t ldy, T*
   const double u = (sizeof(T) == 8) ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
   RSVD_CK(launch_shift_diag<T>(W.G, l, l, 11.0 * ((double)rows * l + (double)l * (l + 1)) * u,
                                P->stream));
-  RSVD_CK(launch_chol_inv<T>(W.G, l, l, W.R1, W.R1i, W.cholw, st, P->stream));
+  if ((rc = chol<T>(P, W.G, l, W.R1, W.R1i))) return rc;
   if ((rc = gemm<T>(P, Y, ldy, false, W.R1i, l, Q, ldq, rows, l, l, true))) return rc;
   return orth<T>(P, Q, rows, l, ldq, Q, ldq, nullptr, false);
 }
@@ -419,7 +433,7 @@ int finish(rsvd_plan_t P, const Work<T>& W, int64_t m, int64_t n, int l, int k, 
   // to rounding (the product carries relative errors ~ eps sigma_1/sigma_i)
   if ((rc = gemm<T>(P, W.z, n, false, us_inv, l, W.tmp, n, n, l, k))) return rc;
   if ((rc = gram<T>(P, W.tmp, n, n, k, W.G))) return rc;
-  RSVD_CK(launch_chol_inv<T>(W.G, k, k, W.R1, W.R1i, W.cholw, dstatus(P), P->stream));
+  if ((rc = chol<T>(P, W.G, k, W.R1, W.R1i))) return rc;
   if ((rc = gemm<T>(P, W.tmp, n, false, W.R1i, k, W.qb, n, n, k, k, true))) return rc;
   RSVD_CK(launch_finalize<T>(U, m, ldu, k, W.qb, n, VT, ldvt, W.sig, S, W.sign, P->stream));
   // the mixed path reports the FP64 singular values of the refined small SVD
