@@ -444,6 +444,25 @@ int rsvd_apply_at(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t
                   const void* X, int64_t ldx, int l, void* Z, int64_t ldz);
 
 /*
+ * rsvd_apply_split: one pass over A as the mixed solve runs it (Algorithm 4
+ * steps 2, 5 and 6, Section 3.3): out = A X (trans = 0; X n x l, out m x l)
+ * or out = A^T X (trans = 1; X m x l, out n x l), with X FP32 (ldx) split on
+ * the device into slices whose sum carries its leading bits: BF16 plans use
+ * `slices` BF16 slices (about 8 significant bits each); FP8 plans use
+ * 2 x `slices` E4M3 slices (4 bits each, one power-of-two weight per slice
+ * and 64-row chunk) on block-scaled MMAs (kind::mxf8f6f4) with A's tile
+ * scales as the tensor core's block scales.  out is FP32 (ldo), FP32
+ * accumulation; A as for rsvd_apply_a (FP8: rsvd_set_tile_scales first).
+ * Mixed plans only (else RSVD_ERR_UNSUPPORTED).  X and out are caller-owned
+ * device buffers; nothing is allocated.
+ * Errors: -2 A; -3 m; -4 n; -5 lda; -6 trans; -7 X; -8 ldx; -9 l;
+ * -10 slices not in 1..3; -11 out; -12 ldo.
+ */
+int rsvd_apply_split(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t lda,
+                     int trans, const float* X, int64_t ldx, int l, int slices, float* out,
+                     int64_t ldo);
+
+/*
  * rsvd_orth: Q = orth(Y) by CholeskyQR2 (Algorithm 4 step 3; the thesis
  * leaves the orthonormalisation method open).  Y rows x l (ldy), Q rows x l
  * (ldq) and, if non-NULL, R (l x l, ldr) are FP64 in plain mode and FP32 in

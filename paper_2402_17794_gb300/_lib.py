@@ -65,6 +65,8 @@ SIGNATURES = {
                              c_int, c_void_p, c_int64]),
     "rsvd_apply_at": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_int64, c_void_p, c_int64,
                               c_int, c_void_p, c_int64]),
+    "rsvd_apply_split": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_int64, c_int, c_void_p,
+                                 c_int64, c_int, c_int, c_void_p, c_int64]),
     "rsvd_orth": (c_int, [c_void_p, P_double, c_int64, c_int, c_int64, P_double, c_int64,
                           P_double, c_int64]),
     "rsvd_small_svd": (c_int, [c_void_p, P_double, c_int, c_int64, P_double, P_double, c_int64,

@@ -605,6 +605,29 @@ int rsvd_apply_at(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t
   return mixed_apply(plan, A, m, n, lda, X, ldx, l, (float*)Z, ldz, true);
 }
 
+int rsvd_apply_split(rsvd_plan_t plan, const void* A, int64_t m, int64_t n, int64_t lda,
+                     int trans, const float* X, int64_t ldx, int l, int slices, float* out,
+                     int64_t ldo) {
+  if (!plan) return -1;
+  if (!A) return -2;
+  if (m < 1) return -3;
+  if (n < 1) return -4;
+  if (lda < m) return -5;
+  if (trans != 0 && trans != 1) return -6;
+  const int64_t rows = trans ? m : n, rows_out = trans ? n : m;
+  if (!X) return -7;
+  if (ldx < rows) return -8;
+  if (l < 1) return -9;
+  if (slices < 1 || slices > 3) return -10;
+  if (!out) return -11;
+  if (ldo < rows_out) return -12;
+  if (plan->mode != RSVD_MODE_MIXED) return RSVD_ERR_UNSUPPORTED;
+  if (!ready(plan) || m > plan->m_max || n > plan->n_max || l > plan->l_max)
+    return RSVD_ERR_WORKSPACE;
+  if (plan->dtype == RSVD_FP8E4M3 && !fp8_ready(plan, m, n, lda)) return RSVD_ERR_UNSUPPORTED;
+  return mixed_apply_split(plan, A, m, n, lda, X, ldx, l, slices, out, ldo, trans != 0);
+}
+
 int rsvd_orth(rsvd_plan_t plan, const void* Y, int64_t rows, int l, int64_t ldy, void* Q,
               int64_t ldq, void* R, int64_t ldr) {
   if (!plan) return -1;

@@ -83,24 +83,28 @@ __global__ void chol64_setup_kernel(const T* __restrict__ G, int64_t ldg, int l,
 // G_PP = L D L^T, pivot j subtracts (a_ji / d_j) row_j from every row i > j,
 // which turns G's upper triangle into D L^T and the identity into L^-1, so
 //   R_PP = D^1/2 L^T,  R_PP^-1 = L^-T D^-1/2.
-// One matrix holds both halves: A[i][k] for i <= k the upper part, for i > k
-// the strict lower part of L^-1 (unit diagonal implicit).  Each of the 256
-// threads owns four of the 32 x 32 entries; every pivot is one update phase
-// and one barrier, and the thread owning the next pivot forms its scales
-// (1/d, 1/sqrt d, sqrt d) right after updating it.  No divisions elsewhere.
-__device__ __forceinline__ void pivot_scales64(double d, double tol, double* inv, double* rs,
-                                               double* sq, int* def) {
-  if (d > tol) {
-    const double r = sqrt(d);
-    *sq = r;
-    *rs = 1.0 / r;
-    *inv = *rs * *rs;
-  } else {
-    *sq = 0.0;
-    *rs = 0.0;
-    *inv = 0.0;
-    atomicAdd(def, 1);
-  }
+// One 32 x 32 array holds both halves: entry (i, k) is the upper part for
+// k >= i and the strict lower part of L^-1 for k < i (unit diagonal
+// implicit).  Warp w keeps rows 4w .. 4w+3 in registers, lane k column k.
+// For pivot j the warp owning row j publishes the row (a_j) and the row
+// times 1/d_j (r_j, with r_jj = 1/d_j for L^-1's unit diagonal) in shared
+// memory; every later row i then takes one FMA per entry,
+//   e_ik -= a_ji r_jk   for k >= i (upper part) or k <= j (L^-1 part),
+// and the owner of row j + 1 forms the next pivot as soon as its own rows
+// are updated.  Pivot rows are double-buffered, so each pivot costs one
+// barrier; warps whose rows are all above the pivot skip the update.
+// 1/sqrt(d) comes from the FP32 reciprocal square root of d scaled into
+// [1, 4), refined by two Newton steps y <- y (3 - d y^2) / 2 in FP64 (each
+// step squares the relative error: about 2^-22 -> 2^-44 -> FP64 rounding).
+__device__ __forceinline__ double rsqrt64(double d) {
+  const long long b = __double_as_longlong(d);
+  const int e = (int)((b >> 52) & 0x7FF) - 1023;      // d normal and positive here
+  const int h = e >> 1;                                // d 2^-2h in [1, 4)
+  const double dn = d * __longlong_as_double((long long)(1023 - 2 * h) << 52);
+  double y = (double)rsqrtf((float)dn);
+  y = y * fma(-0.5 * dn, y * y, 1.5);
+  y = y * fma(-0.5 * dn, y * y, 1.5);
+  return y * __longlong_as_double((long long)(1023 - h) << 52);
 }
 
 __global__ void __launch_bounds__(256) chol64_diag_kernel(const double* __restrict__ W, int l,
@@ -108,49 +112,70 @@ __global__ void __launch_bounds__(256) chol64_diag_kernel(const double* __restri
                                                           double* __restrict__ X,
                                                           CholCtl* ctl) {
   if (ctl->bad) return;
-  __shared__ double A[CB][CB + 1];
-  __shared__ double s_inv[CB], s_rs[CB], s_sq[CB];
-  const int tid = threadIdx.x;
+  __shared__ double pa[2][CB], pr[2][CB];
+  __shared__ double s_rs[CB], s_sq[CB];
+  const int warp = threadIdx.x >> 5, k = threadIdx.x & 31;
   const int nb = min(CB, l - p0);
   const double tol = ctl->tol;
-  for (int e = tid; e < CB * CB; e += 256) {
-    const int i = e & (CB - 1), k = e >> 5;
-    A[i][k] = (i <= k && k < nb) ? W[p0 + i + (int64_t)(p0 + k) * l] : 0.0;
-  }
-  __syncthreads();
-  if (tid == 0) pivot_scales64(A[0][0], tol, &s_inv[0], &s_rs[0], &s_sq[0], &ctl->def);
-  __syncthreads();
-  for (int j = 0; j < nb; ++j) {
-    const double inv = s_inv[j];
+  double a[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = tid + 256 * q;
-      const int i = e & (CB - 1), k = e >> 5;
-      if (i <= j || i >= nb || k >= nb) continue;
-      if (i <= k) {
-        // Schur complement: a_ik -= (a_ji / d_j) a_jk
-        A[i][k] = fma(-A[j][i] * inv, A[j][k], A[i][k]);
-        if (i == j + 1 && k == j + 1)
-          pivot_scales64(A[i][k], tol, &s_inv[i], &s_rs[i], &s_sq[i], &ctl->def);
-      } else if (k <= j) {
-        // L^-1 row i: e_ik -= (a_ji / d_j) e_jk  (e_jj = 1)
-        const double ejk = (k == j) ? 1.0 : A[j][k];
-        A[i][k] = fma(-A[j][i] * inv, ejk, A[i][k]);
-      }
-    }
-    __syncthreads();
+  for (int q = 0; q < 4; ++q) {
+    const int i = 4 * warp + q;
+    a[q] = (i <= k && k < nb) ? W[p0 + i + (int64_t)(p0 + k) * l] : 0.0;
   }
-  // R_PP[i][k] = A[i][k] / sqrt(d_i) (k > i), sqrt(d_i) (k = i);
-  // R_PP^-1[c][i] = (L^-1)[i][c] / sqrt(d_i) (c < i), 1 / sqrt(d_i) (c = i)
-  for (int e = tid; e < CB * CB; e += 256) {
-    const int i = e & (CB - 1), k = e >> 5;
-    if (i >= nb || k >= nb) continue;
-    if (i < k) {
-      R[p0 + i + (int64_t)(p0 + k) * l] = A[i][k] * s_rs[i];
-      X[p0 + i + (int64_t)(p0 + k) * l] = A[k][i] * s_rs[k];
-    } else if (i == k) {
+  // the owner of row j (this warp, register q) publishes pivot j
+  auto publish = [&](int j, double v, int buf) {
+    const double d = __shfl_sync(0xffffffffu, v, j);
+    double rs = 0.0, sq = 0.0;
+    if (d > tol && d >= DBL_MIN) {
+      rs = rsqrt64(d);
+      sq = d * rs;
+    } else if (k == 0) {
+      atomicAdd(&ctl->def, 1);
+    }
+    const double inv = rs * rs;
+    pa[buf][k] = v;
+    pr[buf][k] = (k == j) ? inv : v * inv;
+    if (k == 0) {
+      s_rs[j] = rs;
+      s_sq[j] = sq;
+    }
+  };
+  if (warp == 0) publish(0, a[0], 0);
+  __syncthreads();
+  for (int t = 0; t < 8; ++t) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = 4 * t + u;
+      if (j >= nb) break;
+      const int buf = j & 1;
+      if (4 * warp + 3 > j) {
+        const double rk = pr[buf][k];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int i = 4 * warp + q;
+          if (i > j && (k >= i || k <= j)) a[q] = fma(-pa[buf][i], rk, a[q]);
+        }
+      }
+      if (j + 1 < nb && warp == ((j + 1) >> 2)) publish(j + 1, a[(u + 1) & 3], buf ^ 1);
+      __syncthreads();
+    }
+  }
+  // R_PP[i][k] = a_ik / sqrt(d_i) (k > i), sqrt(d_i) (k = i);
+  // R_PP^-1[k][i] = (L^-1)_ik / sqrt(d_i) (k < i), 1 / sqrt(d_i) (k = i)
+  if (k >= nb) return;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = 4 * warp + q;
+    if (i >= nb) continue;
+    const double rs = s_rs[i];
+    if (k > i) {
+      R[p0 + i + (int64_t)(p0 + k) * l] = a[q] * rs;
+    } else if (k == i) {
       R[p0 + i + (int64_t)(p0 + i) * l] = s_sq[i];
-      X[p0 + i + (int64_t)(p0 + i) * l] = s_rs[i];
+      X[p0 + i + (int64_t)(p0 + i) * l] = rs;
+    } else {
+      X[p0 + k + (int64_t)(p0 + i) * l] = a[q] * rs;
     }
   }
 }
@@ -221,55 +246,55 @@ __global__ void chol64_update_kernel(double* __restrict__ W, int l, int p0,
   W[i + (int64_t)k * l] -= s;
 }
 
-// Inverse, block row I = [q0, q0 + nq): X[I][j] = -X_II sum_{k >= q1} R[I][k] X[k][j]
-// for j in [q1, l) (the rows below are final; X is upper, so the terms with
-// k > j vanish).  One block per TB columns; the sum runs over 32-row chunks
-// staged in shared memory.
-__global__ void __launch_bounds__(256) chol64_inv_kernel(const double* __restrict__ R,
-                                                         double* __restrict__ X, int l, int q0,
-                                                         const CholCtl* ctl) {
+// Inverse, block row I = [q0, q0 + nq), in two steps (the rows below are
+// final; X is upper, so the terms with k > j vanish):
+//   S[a][j] = sum_{q1 <= k <= j} R[q0 + a][k] X[k][j]     (chol64_inv_s_kernel)
+//   X[q0 + a][j] = -sum_{a <= b < nq} X_II[a][b] S[b][j]  (chol64_inv_x_kernel)
+// for j in [q1, l).  8 x 8 output tiles, one output per thread, so the FP64
+// work of a block row spreads over many SMs.  S: nq x (l - q1), ld CB.
+constexpr int IT = 8;
+__global__ void __launch_bounds__(64) chol64_inv_s_kernel(const double* __restrict__ R,
+                                                          const double* __restrict__ X, int l,
+                                                          int q0, double* __restrict__ S,
+                                                          const CholCtl* ctl) {
   if (ctl->bad) return;
   const int nq = min(CB, l - q0);
   const int q1 = q0 + nq;
-  const int j0 = q1 + blockIdx.x * TB;
-  __shared__ double Rc[CB][CB + 1];
-  __shared__ double Xc[CB][TB + 1];
-  __shared__ double S[CB][TB + 1];
-  const int tid = threadIdx.x;
-  const int a0 = tid & (CB - 1), c0 = tid >> 5;   // outputs (a0, c0) and (a0, c0 + 8)
-  double s0 = 0.0, s1 = 0.0;
-  for (int k0 = q1; k0 < l; k0 += CB) {
-    for (int e = tid; e < CB * CB; e += 256) {
-      const int a = e & (CB - 1), kk = e >> 5;
-      Rc[a][kk] = (a < nq && k0 + kk < l) ? R[q0 + a + (int64_t)(k0 + kk) * l] : 0.0;
-    }
-    for (int e = tid; e < CB * TB; e += 256) {
-      const int kk = e & (CB - 1), c = e >> 5;
-      Xc[kk][c] = (k0 + kk < l && j0 + c < l) ? X[k0 + kk + (int64_t)(j0 + c) * l] : 0.0;
+  const int c = threadIdx.x & (IT - 1), a = threadIdx.x / IT;
+  const int j0 = q1 + blockIdx.x * IT, a0 = blockIdx.y * IT;
+  __shared__ double Rc[IT][CB + 1];
+  __shared__ double Xc[CB][IT + 1];
+  const int j = j0 + c, ar = a0 + a;
+  const int kend = min(l, j0 + IT);   // X[k][j] = 0 for k > j
+  double s = 0.0;
+  for (int k0 = q1; k0 < kend; k0 += CB) {
+    for (int e = threadIdx.x; e < IT * CB; e += 64) {
+      const int rr = e / CB, kk = e % CB;
+      Rc[rr][kk] = (a0 + rr < nq && k0 + kk < l) ? R[q0 + a0 + rr + (int64_t)(k0 + kk) * l] : 0.0;
+      const int kx = e % CB, cx = e / CB;
+      Xc[kx][cx] = (k0 + kx < l && j0 + cx < l) ? X[k0 + kx + (int64_t)(j0 + cx) * l] : 0.0;
     }
     __syncthreads();
 #pragma unroll 8
-    for (int kk = 0; kk < CB; ++kk) {
-      s0 = fma(Rc[a0][kk], Xc[kk][c0], s0);
-      s1 = fma(Rc[a0][kk], Xc[kk][c0 + 8], s1);
-    }
+    for (int kk = 0; kk < CB; ++kk) s = fma(Rc[a][kk], Xc[kk][c], s);
     __syncthreads();
   }
-  S[a0][c0] = s0;
-  S[a0][c0 + 8] = s1;
-  // X_II into Rc (upper)
-  for (int e = tid; e < CB * CB; e += 256) {
-    const int a = e & (CB - 1), b = e >> 5;
-    Rc[a][b] = (a < nq && b < nq && a <= b) ? X[q0 + a + (int64_t)(q0 + b) * l] : 0.0;
-  }
-  __syncthreads();
-  for (int cc = 0; cc < 2; ++cc) {
-    const int c = c0 + 8 * cc, j = j0 + c;
-    if (a0 >= nq || j >= l) continue;
-    double t = 0.0;
-    for (int b = a0; b < nq; ++b) t = fma(Rc[a0][b], S[b][c], t);
-    X[q0 + a0 + (int64_t)j * l] = -t;
-  }
+  if (ar < nq && j < l) S[ar + (int64_t)(j - q1) * CB] = s;
+}
+
+__global__ void __launch_bounds__(64) chol64_inv_x_kernel(double* __restrict__ X, int l, int q0,
+                                                          const double* __restrict__ S,
+                                                          const CholCtl* ctl) {
+  if (ctl->bad) return;
+  const int nq = min(CB, l - q0);
+  const int q1 = q0 + nq;
+  const int c = threadIdx.x & (IT - 1), a = threadIdx.x / IT;
+  const int j = q1 + blockIdx.x * IT + c, ar = blockIdx.y * IT + a;
+  if (ar >= nq || j >= l) return;
+  double t = 0.0;
+  for (int b = ar; b < nq; ++b)
+    t = fma(X[q0 + ar + (int64_t)(q0 + b) * l], S[b + (int64_t)(j - q1) * CB], t);
+  X[q0 + ar + (int64_t)j * l] = -t;
 }
 
 template <typename T>
@@ -291,7 +316,9 @@ __global__ void chol64_out_kernel(const double* __restrict__ R, const double* __
 
 }  // namespace
 
-size_t chol64_work_bytes(int l) { return (size_t)3 * l * l * sizeof(double) + 256; }
+size_t chol64_work_bytes(int l) {
+  return (size_t)3 * l * l * sizeof(double) + (size_t)CB * l * sizeof(double) + 256;
+}
 
 // drop: FP64 Grams drop pivots below l eps64 max diag(G), FP32 Grams below
 // eps32 max diag(G): the rules of the one-CTA kernels for each element type.
@@ -303,7 +330,8 @@ cudaError_t launch_chol64(const T* G, int64_t ldg, int l, T* R, T* Rinv, void* w
   double* W = (double*)work;
   double* Rb = W + ll;
   double* Xb = Rb + ll;
-  CholCtl* ctl = (CholCtl*)(Xb + ll);
+  double* Sb = Xb + ll;
+  CholCtl* ctl = (CholCtl*)(Sb + (size_t)CB * l);
   const int blocks = (int)std::min<size_t>((ll + 255) / 256, 64);
   chol64_setup_kernel<T><<<blocks, 256, 0, st>>>(G, ldg, l, drop, W, Rb, Xb, ctl);
   note_launch();
@@ -326,8 +354,10 @@ cudaError_t launch_chol64(const T* G, int64_t ldg, int l, T* R, T* Rinv, void* w
   for (int I = nblk - 2; I >= 0; --I) {
     const int q0 = I * CB;
     const int q1 = std::min(l, q0 + CB);
-    const int nt = (l - q1 + TB - 1) / TB;
-    chol64_inv_kernel<<<nt, 256, 0, st>>>(Rb, Xb, l, q0, ctl);
+    const dim3 g((unsigned)((l - q1 + IT - 1) / IT), (unsigned)((q1 - q0 + IT - 1) / IT));
+    chol64_inv_s_kernel<<<g, 64, 0, st>>>(Rb, Xb, l, q0, Sb, ctl);
+    note_launch();
+    chol64_inv_x_kernel<<<g, 64, 0, st>>>(Xb, l, q0, Sb, ctl);
     note_launch();
   }
   chol64_out_kernel<T><<<blocks, 256, 0, st>>>(Rb, Xb, l, R, Rinv, ctl, status);

@@ -28,6 +28,7 @@ namespace {
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
+int64_t round16(int64_t x) { return (x + 15) / 16 * 16; }
 
 // x = x_1 + x_2 + ... : slice s of column c (blockIdx.y = s * stride + c)
 // holds the BF16 rounding of what the earlier slices left over.
@@ -57,16 +58,60 @@ int split_operand(rsvd_plan_t P, const float* X, int64_t rows, int l, int64_t ld
   return RSVD_OK;
 }
 
+// FP8 A: the same pass with block-scaled E4M3 MMAs, the operand in
+// 2 x `slices` E4M3 slices (4 significant bits each, so the same precision
+// as `slices` BF16 slices).
+int mx8_pass(rsvd_plan_t P, bool ax, const void* A, int64_t m, int64_t n, int64_t lda,
+             const float* X, int64_t ldxf, int l, int slices, float* out, int64_t ldo,
+             bool accumulate) {
+  MixedWork MW = mixed_work_of(P);
+  const int64_t rows = ax ? n : m;
+  const int64_t ldx = round16(rows);
+  const int l16 = (l + 15) / 16 * 16;
+  const int S = 2 * slices;
+  if ((size_t)ldx * S * l16 > MW.xcat_elems * sizeof(__nv_bfloat16)) return RSVD_ERR_WORKSPACE;
+  uint8_t* x8 = reinterpret_cast<uint8_t*>(MW.xcat);
+  const int chunk = mx8_chunk_rows(ax, m, n, l, S);
+  if (!chunk) return RSVD_ERR_UNSUPPORTED;
+  int rc = launch_split_e4m3(X, rows, l, ldxf, S, chunk, x8, ldx, MW.xexp, MW.colscale,
+                             MW.colbits, P->stream);
+  if (rc) return rc;
+  Mx8Call c;
+  c.ax = ax;
+  c.A = A;
+  c.m = m;
+  c.n = n;
+  c.lda = lda;
+  c.scales = P->scales;
+  c.lds = P->lds;
+  c.X = x8;
+  c.ldx = ldx;
+  c.xexp = MW.xexp;
+  c.colscale = MW.colscale;
+  c.chunk = chunk;
+  c.slices = S;
+  c.l = l;
+  c.out = out;
+  c.ldo = ldo;
+  c.part = MW.apart;
+  c.part_floats = MW.apart_floats;
+  c.accumulate = accumulate;
+  c.wait_cycles = P->wait_cycles;
+  return launch_apass_mx8(c, P->num_sms, &dstatus(P)->flags, P->stream);
+}
+
 // One tcgen05 pass: out = A X (ax) or A^T X with X = `slices`-way BF16 split of
 // the FP32 operand (rows x l, ld rows).
-int mixed_pass(rsvd_plan_t P, bool ax, const void* A, int64_t m, int64_t n, int64_t lda,
-               const float* X, int l, int slices, float* out, int64_t ldo) {
+int mixed_pass_ld(rsvd_plan_t P, bool ax, const void* A, int64_t m, int64_t n, int64_t lda,
+                  const float* X, int64_t ldxf, int l, int slices, float* out, int64_t ldo) {
+  if (P->dtype == RSVD_FP8E4M3)
+    return mx8_pass(P, ax, A, m, n, lda, X, ldxf, l, slices, out, ldo, false);
   MixedWork MW = mixed_work_of(P);
   const int64_t rows = ax ? n : m;
   const int64_t ldx = round8(rows);
   const int l16 = (l + 15) / 16 * 16;
   if ((size_t)ldx * slices * l16 > MW.xcat_elems) return RSVD_ERR_WORKSPACE;
-  int rc = split_operand(P, X, rows, l, rows, slices, l16, MW.xcat, ldx);
+  int rc = split_operand(P, X, rows, l, ldxf, slices, l16, MW.xcat, ldx);
   if (rc) return rc;
   ApassCall c;
   c.ax = ax;
@@ -100,6 +145,11 @@ int mixed_pass(rsvd_plan_t P, bool ax, const void* A, int64_t m, int64_t n, int6
   c.x_cols = l16;
   c.accumulate = true;
   return launch_apass_bf16(c, P->num_sms, &dstatus(P)->flags, P->stream);
+}
+
+int mixed_pass(rsvd_plan_t P, bool ax, const void* A, int64_t m, int64_t n, int64_t lda,
+               const float* X, int l, int slices, float* out, int64_t ldo) {
+  return mixed_pass_ld(P, ax, A, m, n, lda, X, ax ? n : m, l, slices, out, ldo);
 }
 
 }  // namespace
@@ -138,7 +188,10 @@ Layout make_layout(int64_t m, int64_t n, int l, int mode, int num_sms, bool f64t
   L.chol64 = take(chol64_work_bytes(l));
   if (mode == RSVD_MODE_MIXED) {
     const int l16 = (l + 15) / 16 * 16;
-    L.om16 = take((size_t)round8(mn) * 3 * l16 * sizeof(__nv_bfloat16));
+    // BF16 operand slices (up to three), or up to six E4M3 slices and the
+    // chunk exponents of an FP8 plan's operand
+    L.om16 = take((size_t)round16(mn) * 3 * l16 * sizeof(__nv_bfloat16) +
+                  (size_t)mx8_xexp_count(mn) * sizeof(int) + (size_t)2 * 256 * sizeof(float));
     L.y32 = take(apass_partial_floats(num_sms, l) * sizeof(float));
   }
   if (f64tc) {
@@ -199,7 +252,10 @@ MixedWork mixed_work_of(rsvd_plan_t P) {
   const int64_t mn = P->m_max > P->n_max ? P->m_max : P->n_max;
   const int l16 = (P->l_max + 15) / 16 * 16;
   M.xcat = (__nv_bfloat16*)(P->ws + P->lay.om16);
-  M.xcat_elems = (size_t)round8(mn) * 3 * l16;
+  M.xcat_elems = (size_t)round16(mn) * 3 * l16;
+  M.xexp = (int*)(M.xcat + M.xcat_elems);
+  M.colscale = (float*)(M.xexp + mx8_xexp_count(mn));
+  M.colbits = (unsigned*)(M.colscale + 256);
   M.apart = (float*)(P->ws + P->lay.y32);
   M.apart_floats = apass_partial_floats(P->num_sms, P->l_max);
   return M;
@@ -558,6 +614,12 @@ int mixed_apply(rsvd_plan_t P, const void* A, int64_t m, int64_t n, int64_t lda,
   c.lds = P->lds;
   c.wait_cycles = P->wait_cycles;
   return launch_apass_bf16(c, P->num_sms, &dstatus(P)->flags, P->stream);
+}
+
+int mixed_apply_split(rsvd_plan_t P, const void* A, int64_t m, int64_t n, int64_t lda,
+                      const float* X, int64_t ldx, int l, int slices, float* out, int64_t ldo,
+                      bool trans) {
+  return mixed_pass_ld(P, !trans, A, m, n, lda, X, ldx, l, slices, out, ldo);
 }
 
 }  // namespace rsvd

@@ -32,8 +32,11 @@ struct Work {
 // Mixed-path extras: the BF16 operand (up to three slices side by side) and
 // the partial slots of the tcgen05 passes.
 struct MixedWork {
-  __nv_bfloat16* xcat;
+  __nv_bfloat16* xcat;      // also the E4M3 slices of an FP8 plan's operand
   size_t xcat_elems;
+  int* xexp;                // FP8: exponent of each 64-row chunk of the operand
+  float* colscale;          // FP8: power-of-two column scales of the operand (256)
+  unsigned* colbits;        // FP8: column maxima scratch (256)
   float* apart;
   size_t apart_floats;
 };
@@ -141,6 +144,12 @@ int sketch_srft(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t ld
 int solve_srft(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64_t lda, int k, int p,
                uint64_t seed, double* U, int64_t ldu, double* S, double* VT, int64_t ldvt);
 
+// One pass exactly as the mixed solve runs it: the FP32 operand X (ld ldx)
+// split into `slices` BF16 slices (BF16 A) or 2 x `slices` E4M3 slices with
+// block-scaled MMAs (FP8 A).
+int mixed_apply_split(rsvd_plan_t P, const void* A, int64_t m, int64_t n, int64_t lda,
+                      const float* X, int64_t ldx, int l, int slices, float* out, int64_t ldo,
+                      bool trans);
 // Step entry: one tcgen05 pass with a BF16 operand X (ldx) of `l` columns.
 int mixed_apply(rsvd_plan_t P, const void* A, int64_t m, int64_t n, int64_t lda, const void* X,
                 int64_t ldx, int l, float* out, int64_t ldo, bool trans);

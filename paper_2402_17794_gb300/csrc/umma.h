@@ -94,4 +94,40 @@ struct F64tcCall {
 constexpr int kF64tcMaxL = 80;   // output columns per pass (six TMEM regions of <= 80)
 int launch_apass_f64tc(const F64tcCall& c, int num_sms, int* status, cudaStream_t st);
 
+// FP8 passes with block-scaled MMA (kind::mxf8f6f4).  The operand: the FP32
+// X (rows x l <= 256, ld ldx) split by launch_split_e4m3 into `slices` E4M3
+// slices of its column-normalised values (slice j column c at
+// out[(j * l16 + c) * ldo + r], l16 = l rounded up to 16, ldo >= rows,
+// ldo % 16 == 0), one exponent per 64-row chunk (mx8_xexp_count(rows) ints)
+// and the power-of-two column scales (l16 floats) the pass multiplies its
+// output columns by; colbits: l unsigned of scratch.
+// The chunk (64 or 128 rows, the stage depth the pass will use) comes from
+// mx8_chunk_rows; 0 means the shape is not supported.
+int64_t mx8_xexp_count(int64_t rows);   // chunk exponents for 64-row chunks (an upper bound)
+int mx8_chunk_rows(bool ax, int64_t m, int64_t n, int l, int slices);
+int launch_split_e4m3(const float* X, int64_t rows, int l, int64_t ldx, int slices, int chunk,
+                      uint8_t* out, int64_t ldo, int* xexp, float* colscale, unsigned* colbits,
+                      cudaStream_t st);
+struct Mx8Call {
+  bool ax;                 // true: Y = A X (contracts n); false: Z = A^T X (contracts m)
+  const void* A;           // E4M3 m x n, column-major, lda % 16 == 0, 16-byte aligned
+  int64_t m, n, lda;
+  const float* scales;     // power-of-two scale of each 128 x 128 tile, (I, J) at I + J * lds
+  int64_t lds;
+  const void* X;           // E4M3 slices from launch_split_e4m3 (n rows for ax, m otherwise)
+  int64_t ldx;
+  const int* xexp;
+  const float* colscale;
+  int chunk;               // rows per exponent: mx8_chunk_rows of this call
+  int slices;              // 2, 4 or 6
+  int l;                   // output columns (<= 256)
+  float* out;              // FP32 (m or n) x l, column-major
+  int64_t ldo;
+  float* part;             // partial slots, as for the BF16 passes
+  size_t part_floats;
+  bool accumulate = false;
+  long long wait_cycles = 0;
+};
+int launch_apass_mx8(const Mx8Call& c, int num_sms, int* status, cudaStream_t st);
+
 }  // namespace rsvd

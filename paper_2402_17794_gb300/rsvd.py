@@ -200,6 +200,11 @@ def rsvd_apply_at(plan, A, m, n, lda, X, ldx, l, Z, ldz) -> int:
     return _lib.load().rsvd_apply_at(plan, _ptr(A), m, n, lda, _ptr(X), ldx, l, _ptr(Z), ldz)
 
 
+def rsvd_apply_split(plan, A, m, n, lda, trans, X, ldx, l, slices, out, ldo) -> int:
+    return _lib.load().rsvd_apply_split(plan, _ptr(A), m, n, lda, trans, _ptr(X), ldx, l, slices,
+                                        _ptr(out), ldo)
+
+
 def rsvd_orth(plan, Y, rows, l, ldy, Q, ldq, R=None, ldr=0) -> int:
     return _lib.load().rsvd_orth(plan, _ptr(Y), rows, l, ldy, _ptr(Q), ldq, _ptr(R), ldr)
 

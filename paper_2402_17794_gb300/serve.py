@@ -106,6 +106,11 @@ class LaneSpec:
     rows_total: int         # sum of m over a batch
     cols_total: int         # sum of n over a batch
     l_max: int
+    # "grouped": one grouped solve per batch (rsvd_solve_batched); "tensor":
+    # one request at a time on an FP64 plan whose passes over A run on the
+    # tensor cores (max_count 1; rows_total, cols_total bound m and n)
+    engine: str = "grouped"
+    lanes: int = 0          # lanes of this class (0: the server's default)
 
 
 @dataclass
@@ -132,7 +137,9 @@ class Server:
         self.in_use = 0
         self.lanes: List[Lane] = []
         for spec in lane_specs:
-            for i in range(lanes_per_class):
+            if spec.engine == "tensor" and (spec.max_count != 1 or spec.name.startswith("f32")):
+                raise ValueError("tensor lanes serve FP64 requests one at a time")
+            for i in range(spec.lanes or lanes_per_class):
                 lane = Lane(spec, i)
                 backend.create_lane(lane)
                 self.lanes.append(lane)
@@ -240,12 +247,17 @@ def percentile(xs: List[float], pct: float) -> float:
     return s[i]
 
 
-def run(server: Server, requests: List[Request], now_fn, max_wall: float = 600.0) -> dict:
+def run(server: Server, requests: List[Request], now_fn, max_wall: float = 600.0,
+        drain_s: Optional[float] = None) -> dict:
     """Feeds requests at their arrival times (now_fn: seconds since start)
-    until every request has completed."""
+    until every request has completed.  With drain_s, stops waiting drain_s
+    after the last arrival: requests not finished by then are counted as
+    unserved (their work still completes on the device, the results are
+    dropped), and latencies cover the served requests only."""
     order = sorted(requests, key=lambda r: r.arrival)
     i = 0
     t0 = now_fn()
+    last = order[-1].arrival if order else 0.0
     while True:
         now = now_fn() - t0
         while i < len(order) and order[i].arrival <= now:
@@ -254,11 +266,14 @@ def run(server: Server, requests: List[Request], now_fn, max_wall: float = 600.0
         server.step(now)
         if i == len(order) and server.pending() == 0:
             break
+        if drain_s is not None and i == len(order) and now > last + drain_s:
+            break
         if now > max_wall:
             raise RuntimeError("serving run exceeded its wall-clock limit")
     wall = now_fn() - t0
     lat = [r.latency for r in server.finished]
-    return {"completed": len(server.finished), "wall_s": wall,
+    unserved = len(order) - len(server.finished)
+    return {"completed": len(server.finished), "unserved": unserved, "wall_s": wall,
             "throughput_rps": len(server.finished) / wall if wall > 0 else float("nan"),
             "p50_ms": percentile(lat, 50) * 1e3, "p99_ms": percentile(lat, 99) * 1e3,
             "max_ms": max(lat) * 1e3 if lat else float("nan"),
@@ -285,9 +300,14 @@ class TorchBackend:
         # ahead of a big batch's pending blocks as SMs free up
         stream = torch.cuda.Stream(priority=-1 if lane.spec.name.endswith("small") else 0)
         dt = R.F32 if lane.spec.name.startswith("f32") else R.F64
-        plan = R.BatchPlan(lane.spec.max_count, lane.spec.rows_total, lane.spec.cols_total,
-                           lane.spec.l_max, dt, stream=stream)
-        self.state[lane.key] = {"stream": stream, "plan": plan, "event": None, "dt": dt}
+        if lane.spec.engine == "tensor":
+            plan = R.Plan(lane.spec.rows_total, lane.spec.cols_total, lane.spec.l_max,
+                          mode=R.F64_TENSOR, stream=stream)
+        else:
+            plan = R.BatchPlan(lane.spec.max_count, lane.spec.rows_total, lane.spec.cols_total,
+                               lane.spec.l_max, dt, stream=stream)
+        self.state[lane.key] = {"stream": stream, "plan": plan, "event": None, "dt": dt,
+                                "tensor": lane.spec.engine == "tensor"}
 
     def launch(self, lane: Lane, batch: List[Request]):
         torch, R = self.torch, self.R
@@ -298,7 +318,11 @@ class TorchBackend:
             for r in batch:
                 A = r.A if r.A.dtype == dtype else r.A.to(dtype)
                 items.append((A, r.m, r.n, r.k, r.p, r.q, r.seed))
-            res = st["plan"].solve(items)
+            if st["tensor"]:
+                res = [st["plan"].solve(A, m, n, k, p, q, seed)
+                       for (A, m, n, k, p, q, seed) in items]
+            else:
+                res = st["plan"].solve(items)
             ev = torch.cuda.Event()
             ev.record(st["stream"])
         for r, out in zip(batch, res):
@@ -310,7 +334,10 @@ class TorchBackend:
         return self.state[lane.key]["event"].query()
 
     def statuses(self, lane: Lane) -> List[int]:
-        return self.state[lane.key]["plan"].status()
+        st = self.state[lane.key]
+        if st["tensor"]:
+            return [st["plan"].status()] * len(lane.batch)
+        return st["plan"].status()
 
     def sigmas(self, lane: Lane):
         """Host copies of each finished request's singular values (the lane's

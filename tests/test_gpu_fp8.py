@@ -77,6 +77,72 @@ def test_fp8_pass_matches_fp64_product(m, n, l, ax):
     assert np.abs(got - ref).max() <= 2e-6 * mag
 
 
+@pytest.mark.parametrize("m,n,l", [(1000, 777, 37), (3000, 2000, 160), (129, 4100, 80),
+                                   (4096, 640, 256), (20000, 300, 48)])
+@pytest.mark.parametrize("trans", [0, 1])
+@pytest.mark.parametrize("dtype", ["fp8", "bf16"])
+def test_split_pass_within_slicing_bound(m, n, l, trans, dtype):
+    """rsvd_apply_split, the pass as the solve runs it: an FP32 operand split
+    on the device into slices.  BF16 plans: `s` BF16 slices, each leaving at
+    most 2^-8 of what it rounds.  FP8 plans: 2s E4M3 slices on block-scaled
+    MMAs, each leaving at most 2^-4.  Either way the operand is carried to
+    2^-8s relative per element, so with FP32 accumulation
+    |Y - A X| <= (2^-8s + K 2^-23) (|A| |X|) elementwise (A exact: the
+    dequantised codes, or BF16)."""
+    rng = np.random.default_rng(m + 3 * n + l + trans)
+    lda = (m + 15) // 16 * 16 + (16 if m % 3 == 0 else 0)
+    if dtype == "fp8":
+        dA, dS, Aq = _fp8_matrix(rng.standard_normal((m, n)), lda, spread_scales=True)
+        plan = R.Plan(m, n, l, a_dtype=R.FP8E4M3, mode=R.MIXED)
+        plan.set_tile_scales(dS)
+    else:
+        a16 = torch.zeros(n, lda, dtype=torch.bfloat16)
+        a16[:, :m] = torch.from_numpy(rng.standard_normal((n, m))).to(torch.bfloat16)
+        Aq = np.asfortranarray(a16[:, :m].double().numpy().T)
+        dA = a16.cuda()
+        plan = R.Plan(m, n, l, a_dtype=R.BF16, mode=R.MIXED)
+    rows, orows = (m, n) if trans else (n, m)
+    ldx = rows + 5
+    X = np.zeros((l, ldx), dtype=np.float32)
+    # columns of very different magnitude, and a zero column
+    X[:, :rows] = (rng.standard_normal((l, rows)) *
+                   np.exp2(rng.integers(-20, 20, size=(l, 1)))).astype(np.float32)
+    X[l // 2, :rows] = 0.0
+    dX = torch.from_numpy(X).cuda()
+    X64 = X[:, :rows].T.astype(np.float64)
+    AT = Aq.T if trans else Aq
+    ref = AT @ X64
+    mag = np.abs(AT) @ np.abs(X64)
+    K = m if trans else n
+    for s in (1, 2, 3):
+        Y = torch.full((l, orows + 3), float("nan"), dtype=torch.float32, device="cuda")
+        assert R.rsvd_apply_split(plan.handle, dA, m, n, lda, trans, dX, ldx, l, s, Y,
+                                  orows + 3) == 0
+        _ok(plan)
+        got = Y[:, :orows].cpu().numpy().T.astype(np.float64)
+        assert np.isfinite(got).all()
+        bound = (2.0 ** (-8 * s) + K * 2.0 ** -23) * mag
+        assert (np.abs(got - ref) <= bound + 1e-300).all(), (s, (np.abs(got - ref) / (bound + 1e-300)).max())
+        assert (got[:, l // 2] == 0).all()
+
+
+def test_split_pass_argument_errors():
+    m, n, l = 256, 128, 16
+    plan = R.Plan(m, n, l, a_dtype=R.FP8E4M3, mode=R.MIXED)
+    plan.set_tile_scales(torch.ones(1, 2, device="cuda"))
+    A = torch.zeros(n, m, dtype=torch.uint8, device="cuda")
+    X = torch.zeros(l, m, device="cuda")
+    Y = torch.zeros(l, m, device="cuda")
+    f = R.rsvd_apply_split
+    assert f(plan.handle, A, m, n, m, 2, X, n, l, 1, Y, m) == -6
+    assert f(plan.handle, A, m, n, m, 0, X, n - 1, l, 1, Y, m) == -8
+    assert f(plan.handle, A, m, n, m, 0, X, n, l, 4, Y, m) == -10
+    assert f(plan.handle, A, m, n, m, 1, X, m, l, 0, Y, n) == -10
+    assert f(plan.handle, A, m, n, m, 0, X, n, l, 1, Y, m - 1) == -12
+    pplan = R.Plan(m, n, l)
+    assert f(pplan.handle, A, m, n, m, 0, X, n, l, 1, Y, m) == 7
+
+
 def _fp8_solve_and_compare(A, k, p, q, seed, lda_pad=0):
     m, n = A.shape
     lda = (m + 15) // 16 * 16 + lda_pad
