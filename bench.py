@@ -297,31 +297,39 @@ def run_mixed(args, world, rank, sampler_uuid, wname="mixed-bf16"):
                            scales if fp8 else None, steps)
 
     # the tcgen05 passes alone (one BF16 operand slice, l = 160)
-    X_n = torch.randn(l, n, device="cuda").to(torch.bfloat16)
-    X_m = torch.randn(l, m, device="cuda").to(torch.bfloat16)
+    # the pass of the power steps as the solve runs it: an FP32 operand split
+    # into one BF16 slice (BF16 A) or two E4M3 slices (FP8 A), then the pass
+    X_n = torch.randn(l, n, device="cuda") / n ** 0.5
+    X_m = torch.randn(l, m, device="cuda") / m ** 0.5
     Y = torch.empty(l, m, dtype=torch.float32, device="cuda")
     Z = torch.empty(l, n, dtype=torch.float32, device="cuda")
 
     t_ax, how = _time_calls(plan.handle,
-                            lambda: R.rsvd_apply_a(plan.handle, dA, m, n, m, X_n, n, l, Y, m))
+                            lambda: R.rsvd_apply_split(plan.handle, dA, m, n, m, 0, X_n, n, l, 1,
+                                                       Y, m))
     t_atx, _ = _time_calls(plan.handle,
-                           lambda: R.rsvd_apply_at(plan.handle, dA, m, n, m, X_m, m, l, Z, n))
+                           lambda: R.rsvd_apply_split(plan.handle, dA, m, n, m, 1, X_m, m, l, 1,
+                                                      Z, n))
     st = plan.status()
     if st != 0:
         raise RuntimeError(f"mixed pass failed: {R.rsvd_status_string(st)}")
     peaks, _ = _peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
     dom_ms = max(t_ax, t_atx)
-    f8 = ",fp8" if fp8 else ""
-    dom = f"apass_bf16_kernel<true,2{f8}> (Y = A X)" if t_ax >= t_atx else \
-        f"apass_bf16_kernel<false,2{f8}> (Z = A^T X)"
+    if fp8:
+        dom = "apass_mx8_kernel<true,2,2,128> (Y = A X)" if t_ax >= t_atx else \
+            "apass_mx8_kernel<false,2,2,128> (Z = A^T X)"
+    else:
+        dom = "apass_bf16_kernel<true,2> (Y = A X)" if t_ax >= t_atx else \
+            "apass_bf16_kernel<false,2> (Z = A^T X)"
     achieved = a_bytes / (dom_ms / 1e3) / 1e9
     out = {
         "workload": w["desc"], "value": round(steps * world / (ms / 1e3), 3), "unit": "solves/s",
         "ms_per_solve": round(ms / steps, 4),
         "p50_ms": round(per[len(per) // 2], 4), "p99_ms": round(per[min(len(per) - 1, int(0.99 * len(per)))], 4),
         "two_streams": two,
-        "dtype": ("fp8 e4m3 A (tile scales), bf16 operands" if fp8 else "bf16 A") +
+        "dtype": ("fp8 e4m3 A (tile scales as UE8M0 block scales), e4m3 operand slices "
+                  "(block-scaled MMA)" if fp8 else "bf16 A, bf16 operand slices") +
                  ", fp32 accumulate", "passes_per_solve": passes, "jacobi_sweeps": sweeps,
         "a_pass": {"ms_ax": round(t_ax, 4), "ms_atx": round(t_atx, 4),
                    "gbps_ax": round(a_bytes / (t_ax / 1e3) / 1e9, 1),
@@ -332,7 +340,8 @@ def run_mixed(args, world, rank, sampler_uuid, wname="mixed-bf16"):
                      "traffic": _traffic_from_profile(wname, "ax" if t_ax >= t_atx else "atx"),
                      "algorithmic_bytes_per_launch": a_bytes,
                      "ms_per_launch": round(dom_ms, 4),
-                     "timing": f"{how}: main kernel + split-tile fixup per pass"},
+                     "timing": f"{how}: operand split + main kernel + split-tile fixup per "
+                               "pass (one BF16 / two E4M3 operand slices, as in the power steps)"},
         "clocks": clocks,
     }
     # the CPU oracle on the exactly dequantised A (q + 1 power steps, as the

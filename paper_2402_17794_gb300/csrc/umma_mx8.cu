@@ -12,20 +12,20 @@
 //   x_rc = 2^(d_c) sum_j 2^(e_k - 4 j) x_j,rc      (x_j E4M3, j = 0 .. S-1),
 // d_c a power-of-two normalisation of column c (undone exactly in the
 // epilogue, so columns of any magnitude keep their precision) and e_k one
-// exponent per 64-row chunk k of the normalised X, chosen so that the
-// chunk's largest magnitude lands in [128, 256) in slice 0.  Each slice peels off
+// exponent per chunk k of the normalised X (BK rows, one stage), chosen so
+// that the chunk's largest magnitude lands in [128, 256) in slice 0.  Each slice peels off
 // the E4M3 rounding of what the earlier ones left, so S slices carry about
 // 4 S significant bits of every element (E4M3: 4 significant bits).  The
 // slice products of one output tile accumulate into one FP32 TMEM
 // accumulator; each slice's power-of-two weight is its UE8M0 block scale.
 // All scale factors are constant over a stage (A: per 128 x 128 tile; X: per
-// 64-row chunk and slice), so every byte of a scale-factor region holds the
+// chunk and slice), so every byte of a scale-factor region holds the
 // same value and the MMA reads it wherever its layout places a row's or a
 // column's scale.
 //
 // Shape and schedule follow the BF16 passes: persistent grid with stream-K
 // ranges of (tile, k-block) iterations (tile = MT x 128 output rows,
-// k-block = 64 of the contraction), split tiles written as per-CTA partials
+// k-block = BK of the contraction), split tiles written as per-CTA partials
 // and summed by the fixup kernel.  Warp roles: warp 0 TMA producer, warp 1
 // MMA issuer (one lane), warps 2-5 epilogue (tcgen05.ld, FP32 stores), warps
 // 6-9 write the scale factors of each stage into TMEM with tcgen05.st (one
@@ -126,7 +126,7 @@ struct Mx8Args {
   const float* scales;     // A tile scales, tile (I, J) at scales[I + J * lds]
   int64_t lds;
   int sc_rows, sc_cols;
-  const int* xexp;         // exponent e_k of each 64-row chunk of X
+  const int* xexp;         // exponent e_k of each BK-row chunk of X
   const float* colscale;   // 2^(d_c) of each column of X
   long long wait_cycles;
 };
