@@ -51,8 +51,9 @@ WORKLOADS = {
         seed_a=0, seed=2, dtype="bf16"),
     "mixed-fp8": dict(
         desc="mixed precision, FP8 storage: the same A 65536x16384 stored as FP8 E4M3 with one "
-             "power-of-two FP32 scale per 128x128 tile; k=128, p=32, q=3 (+1 bf16x2 refinement "
-             "step, bf16x3 final B); FP32 accumulate",
+             "power-of-two FP32 scale per 128x128 tile; k=128, p=32, q=3 (+1 refinement step); "
+             "block-scaled E4M3 MMAs, operand in 2/4/6 E4M3 slices (power steps / refinement / "
+             "final B); FP32 accumulate",
         m=65536, n=16384, k=128, p=32, q=3, spectrum=("exp", 40.0), terms=640, noise=1e-4,
         seed_a=0, seed=2, dtype="fp8"),
 }
@@ -1286,7 +1287,8 @@ def run_profile_case(args):
     A 8192 x 4096 FP64 (268 MB, larger than L2), l = 80: two passes of each
     kind and one full solve on the CUDA cores, the same on the tensor cores
     (A prepared once), and two SRFT sketches; A 16384 x 16384 BF16 and
-    FP8, l = 160: two passes of each kind and one mixed solve."""
+    FP8, l = 160: two passes of each kind and one mixed solve, and for FP8
+    two block-scaled passes of each kind with a two-slice E4M3 operand."""
     import numpy as np
     import torch
 
@@ -1358,10 +1360,51 @@ def run_profile_case(args):
     for _ in range(2):
         R.rsvd_apply_a(plan.handle, codes, m, n, m, Xn, n, l, Y, m)
         R.rsvd_apply_at(plan.handle, codes, m, n, m, Xn, m, l, Y, n)
+    # the block-scaled FP8 passes of the FP8 solve's power steps: an FP32
+    # operand split into two E4M3 slices, twice each kind
+    Xf = torch.randn(l, n, device="cuda") / n ** 0.5
+    for _ in range(2):
+        for t in (0, 1):
+            R._check(R.rsvd_apply_split(plan.handle, codes, m, n, m, t, Xf, n, l, 1, Y, m),
+                     "rsvd_apply_split")
     st = plan.status()
     if st != 0:
         raise RuntimeError(R.rsvd_status_string(st))
     print("profile case done")
+
+
+def run_launch_case(args):
+    """Two full solves of each timed workload, for an ncu launch list (no
+    timing): the plain FP64 solve on the tensor cores (16384 x 8192), then the
+    mixed solve on BF16 and on FP8 storage (65536 x 16384)."""
+    import torch
+
+    import __graft_entry__
+    from paper_2402_17794_gb300 import rsvd as R
+
+    __graft_entry__.build()
+    for wname in ("plain-fp64", "mixed-bf16", "mixed-fp8"):
+        w = WORKLOADS[wname]
+        m, n, k, p, q = w["m"], w["n"], w["k"], w["p"], w["q"]
+        if w["dtype"] == "fp8":
+            dA, scales = _make_input(w, 0)
+            plan = R.Plan(m, n, k + p, a_dtype=R.FP8E4M3, mode=R.MIXED)
+            plan.set_tile_scales(scales)
+        elif w["dtype"] == "bf16":
+            dA = _make_input(w, 0)
+            plan = R.Plan(m, n, k + p, a_dtype=R.BF16, mode=R.MIXED)
+        else:
+            dA = _make_input(w, 0)
+            plan = R.Plan(m, n, k + p, mode=R.F64_TENSOR)
+        for _ in range(2):
+            plan.solve(dA, m, n, k, p, q, w["seed"], lda=dA.shape[1])
+        torch.cuda.synchronize()
+        st = plan.status()
+        if st != 0:
+            raise RuntimeError(f"{wname}: {R.rsvd_status_string(st)}")
+        del dA, plan
+        torch.cuda.empty_cache()
+    print("launch case done")
 
 
 def main():
@@ -1381,9 +1424,14 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=30.0,
                     help="seconds of Poisson arrivals in the serving run (the workload "
                          "definition uses 30)")
+    ap.add_argument("--launch-case", action="store_true",
+                    help="two full solves of each timed workload, for an ncu launch list")
     ap.add_argument("--profile-case", action="store_true",
                     help="run a reduced case of the same kernels for ncu (no timing)")
     args = ap.parse_args()
+    if args.launch_case:
+        run_launch_case(args)
+        return
     if args.profile_case:
         run_profile_case(args)
         return

@@ -93,18 +93,32 @@ __global__ void chol64_setup_kernel(const T* __restrict__ G, int64_t ldg, int l,
 // and the owner of row j + 1 forms the next pivot as soon as its own rows
 // are updated.  Pivot rows are double-buffered, so each pivot costs one
 // barrier; warps whose rows are all above the pivot skip the update.
-// 1/sqrt(d) comes from the FP32 reciprocal square root of d scaled into
-// [1, 4), refined by two Newton steps y <- y (3 - d y^2) / 2 in FP64 (each
-// step squares the relative error: about 2^-22 -> 2^-44 -> FP64 rounding).
+// On that critical path only 1/d_j is needed: the FP32 reciprocal of d
+// scaled into [1, 2), refined by two Newton steps y <- y (2 - d y) in FP64
+// (each squares the relative error: about 2^-22 -> 2^-44 -> FP64 rounding).
+// The square roots for R and R^-1 (same Newton scheme on 1/sqrt(d),
+// y <- y (3 - d y^2) / 2) are formed once, after the elimination.
+__device__ __forceinline__ double pow2_of(int e) {   // 2^e, |e| <= 1022
+  return __longlong_as_double((long long)(1023 + e) << 52);
+}
+__device__ __forceinline__ int exp_of(double d) {    // d normal and positive
+  return (int)((__double_as_longlong(d) >> 52) & 0x7FF) - 1023;
+}
+__device__ __forceinline__ double rcp64(double d) {
+  const int e = exp_of(d);
+  const double dn = d * pow2_of(-e);                  // [1, 2)
+  double y = (double)__frcp_rn((float)dn);
+  y = y * fma(-dn, y, 2.0);
+  y = y * fma(-dn, y, 2.0);
+  return y * pow2_of(-e);
+}
 __device__ __forceinline__ double rsqrt64(double d) {
-  const long long b = __double_as_longlong(d);
-  const int e = (int)((b >> 52) & 0x7FF) - 1023;      // d normal and positive here
-  const int h = e >> 1;                                // d 2^-2h in [1, 4)
-  const double dn = d * __longlong_as_double((long long)(1023 - 2 * h) << 52);
+  const int h = exp_of(d) >> 1;                        // d 2^-2h in [1, 4)
+  const double dn = d * pow2_of(-2 * h);
   double y = (double)rsqrtf((float)dn);
   y = y * fma(-0.5 * dn, y * y, 1.5);
   y = y * fma(-0.5 * dn, y * y, 1.5);
-  return y * __longlong_as_double((long long)(1023 - h) << 52);
+  return y * pow2_of(-h);
 }
 
 __global__ void __launch_bounds__(256) chol64_diag_kernel(const double* __restrict__ W, int l,
@@ -113,7 +127,7 @@ __global__ void __launch_bounds__(256) chol64_diag_kernel(const double* __restri
                                                           CholCtl* ctl) {
   if (ctl->bad) return;
   __shared__ double pa[2][CB], pr[2][CB];
-  __shared__ double s_rs[CB], s_sq[CB];
+  __shared__ double s_d[CB], s_rs[CB];
   const int warp = threadIdx.x >> 5, k = threadIdx.x & 31;
   const int nb = min(CB, l - p0);
   const double tol = ctl->tol;
@@ -123,23 +137,20 @@ __global__ void __launch_bounds__(256) chol64_diag_kernel(const double* __restri
     const int i = 4 * warp + q;
     a[q] = (i <= k && k < nb) ? W[p0 + i + (int64_t)(p0 + k) * l] : 0.0;
   }
-  // the owner of row j (this warp, register q) publishes pivot j
+  // the owner of row j (this warp, register q) publishes pivot j; a dropped
+  // pivot (d <= tol) publishes a zero scaled row and records d = 0
   auto publish = [&](int j, double v, int buf) {
-    const double d = __shfl_sync(0xffffffffu, v, j);
-    double rs = 0.0, sq = 0.0;
+    double d = __shfl_sync(0xffffffffu, v, j);
+    double inv = 0.0;
     if (d > tol && d >= DBL_MIN) {
-      rs = rsqrt64(d);
-      sq = d * rs;
-    } else if (k == 0) {
-      atomicAdd(&ctl->def, 1);
+      inv = rcp64(d);
+    } else {
+      d = 0.0;
+      if (k == 0) atomicAdd(&ctl->def, 1);
     }
-    const double inv = rs * rs;
     pa[buf][k] = v;
     pr[buf][k] = (k == j) ? inv : v * inv;
-    if (k == 0) {
-      s_rs[j] = rs;
-      s_sq[j] = sq;
-    }
+    if (k == 0) s_d[j] = d;
   };
   if (warp == 0) publish(0, a[0], 0);
   __syncthreads();
@@ -161,6 +172,8 @@ __global__ void __launch_bounds__(256) chol64_diag_kernel(const double* __restri
       __syncthreads();
     }
   }
+  if (warp == 0) s_rs[k] = (k < nb && s_d[k] > 0.0) ? rsqrt64(s_d[k]) : 0.0;
+  __syncthreads();
   // R_PP[i][k] = a_ik / sqrt(d_i) (k > i), sqrt(d_i) (k = i);
   // R_PP^-1[k][i] = (L^-1)_ik / sqrt(d_i) (k < i), 1 / sqrt(d_i) (k = i)
   if (k >= nb) return;
@@ -172,7 +185,7 @@ __global__ void __launch_bounds__(256) chol64_diag_kernel(const double* __restri
     if (k > i) {
       R[p0 + i + (int64_t)(p0 + k) * l] = a[q] * rs;
     } else if (k == i) {
-      R[p0 + i + (int64_t)(p0 + i) * l] = s_sq[i];
+      R[p0 + i + (int64_t)(p0 + i) * l] = s_d[i] * rs;
       X[p0 + i + (int64_t)(p0 + i) * l] = rs;
     } else {
       X[p0 + k + (int64_t)(p0 + i) * l] = a[q] * rs;

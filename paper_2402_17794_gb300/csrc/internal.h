@@ -53,6 +53,8 @@ struct Layout {
   // RSVD_MODE_F64_TENSOR: A's digit slices, row exponents, the operand's
   // slices and exponents, raw outputs and partial slots of the passes
   size_t tc_slices, tc_rmax, tc_xs, tc_fexp, tc_rawt, tc_rawr, tc_partt, tc_partr;
+  size_t tc_ys, tc_yrmax;          // digit slices and row exponents of a sample Y (orth)
+  int64_t tc_yncol;
   int64_t tc_ncol, tc_ldsl, tc_ldxs;
 };
 

@@ -207,6 +207,9 @@ Layout make_layout(int64_t m, int64_t n, int l, int mode, int num_sms, bool f64t
     L.tc_rawr = take((size_t)mn * lw * 4);
     L.tc_partt = take((size_t)num_sms * 2 * 128 * lw * 8);
     L.tc_partr = take((size_t)num_sms * 2 * 128 * lw * 4);
+    L.tc_yncol = ((int64_t)l + 127) / 128 * 128;
+    L.tc_ys = take((size_t)6 * L.tc_yncol * L.tc_ldxs * 2);
+    L.tc_yrmax = take(sizeof(int) * (size_t)L.tc_ldxs);
   }
   L.total = off;
   return L;
@@ -312,6 +315,43 @@ int f64tc_pass(rsvd_plan_t P, bool ax, const double* X, int64_t ldx, double* C, 
   return launch_apass_f64tc(c, P->num_sms, &dstatus(P)->flags, P->stream);
 }
 
+// The same tensor-core FP64 products with a sample Y (rows x cols, ldy) in
+// the role of A, for the CholeskyQR pass inside the power steps: Y's digit
+// slices are cut once (f64tc_slice_y), then G = Y^T Y and Q = Y R^-1 are
+// passes over them (f64tc_y_pass).  The plan's prepared A is left alone.
+int f64tc_slice_y(rsvd_plan_t P, const double* Y, int64_t rows, int cols, int64_t ldy) {
+  const Layout& L = P->lay;
+  if (rows > L.tc_ldxs || cols > L.tc_yncol) return RSVD_ERR_UNSUPPORTED;
+  return f64tc_prepare_a(Y, rows, cols, ldy, P->ws + L.tc_ys, L.tc_ldxs, L.tc_yncol,
+                         (int*)(P->ws + L.tc_yrmax), &dstatus(P)->flags, P->num_sms, P->stream);
+}
+int f64tc_y_pass(rsvd_plan_t P, int64_t rows, int cols, bool ax, const double* X, int64_t ldx,
+                 double* C, int64_t ldc, int N) {
+  const Layout& L = P->lay;
+  F64tcCall c;
+  c.ax = ax;
+  c.slices = P->ws + L.tc_ys;
+  c.m = rows;
+  c.n = cols;
+  c.ldsl = L.tc_ldxs;
+  c.ncol = L.tc_yncol;
+  c.rmax = (const int*)(P->ws + L.tc_yrmax);
+  c.X = X;
+  c.ldx = ldx;
+  c.l = N;
+  c.out = C;
+  c.ldo = ldc;
+  c.xslices = P->ws + L.tc_xs;
+  c.ldxs = L.tc_ldxs;
+  c.fexp = (int*)(P->ws + L.tc_fexp);
+  c.raw_t = (int64_t*)(P->ws + L.tc_rawt);
+  c.raw_r = (float*)(P->ws + L.tc_rawr);
+  c.part_t = (int64_t*)(P->ws + L.tc_partt);
+  c.part_r = (float*)(P->ws + L.tc_partr);
+  c.wait_cycles = P->wait_cycles;
+  return launch_apass_f64tc(c, P->num_sms, &dstatus(P)->flags, P->stream);
+}
+
 }  // namespace
 
 template <typename T>
@@ -347,11 +387,12 @@ template int gram<float>(rsvd_plan_t, const float*, int64_t, int64_t, int, float
 
 // R and R^-1 of the Gram G (ld l): the FP64 multi-kernel Cholesky for
 // l >= 32 on both paths (FP64 arithmetic whatever T is), the one-CTA
-// kernels below that.
+// kernels below that or where `fp64` is false (the single CholeskyQR pass
+// inside the mixed power steps, whose Q only carries its range forward).
 template <typename T>
-int chol(rsvd_plan_t P, const T* G, int l, T* R, T* Rinv) {
+int chol(rsvd_plan_t P, const T* G, int l, T* R, T* Rinv, bool fp64 = true) {
   const Work<T> W = work_of<T>(P);
-  if (l >= 32)
+  if (l >= 32 && fp64)
     RSVD_CK(launch_chol64<T>(G, l, l, R, Rinv, P->ws + P->lay.chol64, dstatus(P), P->stream));
   else
     RSVD_CK(launch_chol_inv<T>(G, l, l, R, Rinv, W.cholw, dstatus(P), P->stream));
@@ -386,8 +427,19 @@ template <typename T>
 int orth1(rsvd_plan_t P, const T* Y, int64_t rows, int l, int64_t ldy, T* Q, int64_t ldq) {
   Work<T> W = work_of<T>(P);
   int rc;
+  if constexpr (sizeof(T) == 8) {
+    // tensor-core FP64 plans: the Gram and Y R^-1 as exact digit-slice
+    // products (about 2^-43 relative to the row and column scales; only
+    // range(Q) carries forward from this pass)
+    if (P->f64tc && l <= kF64tcMaxL) {
+      if ((rc = f64tc_slice_y(P, Y, rows, l, ldy))) return rc;
+      if ((rc = f64tc_y_pass(P, rows, l, false, Y, ldy, W.G, l, l))) return rc;
+      if ((rc = chol<T>(P, W.G, l, W.R1, W.R1i))) return rc;
+      return f64tc_y_pass(P, rows, l, true, W.R1i, l, Q, ldq, l);
+    }
+  }
   if ((rc = gram<T>(P, Y, ldy, rows, l, W.G))) return rc;
-  if ((rc = chol<T>(P, W.G, l, W.R1, W.R1i))) return rc;
+  if ((rc = chol<T>(P, W.G, l, W.R1, W.R1i, sizeof(T) == 8))) return rc;
   return gemm<T>(P, Y, ldy, false, W.R1i, l, Q, ldq, rows, l, l, true);
 }
 template int orth1<float>(rsvd_plan_t, const float*, int64_t, int, int64_t, float*, int64_t);

@@ -773,6 +773,29 @@ __device__ __forceinline__ int rr_player(int pos, int r, int twoP) {
   return 1 + v;
 }
 
+// Rotation (c, s) that zeroes the cosine of columns p, q with |c_p|^2 = a,
+// |c_q|^2 = b, c_p.c_q = g (Rutishauser): zeta = (b - a) / (2g),
+// t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1 / sqrt(1 + t^2), s = c t.
+// Near convergence the angles are tiny: for |zeta| > Z the same t is
+// g / (b - a) to relative 1 / (4 zeta^2) and c = 1 - t^2 / 2 to 3 t^4 / 8,
+// both below the rounding unit (Z = 1e8 in FP64, 1e4 in FP32), which saves
+// two divisions and two square roots on FP64's slow pipe.
+template <typename T>
+__device__ __forceinline__ void jacobi_cs(T a, T b, T g, T& c, T& sn) {
+  const T d = b - a;
+  const T zmax = sizeof(T) == 8 ? T(2e8) : T(2e4);   // 2 Z
+  if (fabs(d) > zmax * fabs(g)) {
+    const T t = g / d;
+    c = fma(T(-0.5) * t, t, T(1));
+    sn = c * t;
+    return;
+  }
+  const T zeta = d / (T(2) * g);
+  const T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, T(1))));
+  c = rsqrt(fma(t, t, T(1)));
+  sn = c * t;
+}
+
 // Threads a Jacobi CTA runs with: P column pairs x G threads per pair, G a
 // power of two chosen so that P * G <= JACOBI_THREADS.
 constexpr int JACOBI_THREADS = 640;
@@ -826,7 +849,7 @@ __device__ __forceinline__ void jacobi_body(const T* __restrict__ M, int l, int6
   const int P = twoP / 2;
   const bool want_v = Vm != nullptr;
   T* Wv = Wm + (int64_t)ldw * twoP;
-  __shared__ int s_rot;
+  __shared__ int s_rot, s_big;
   __shared__ T s_norm[RSVD_L_MAX + 1];
   __shared__ T s_abg[kFused ? 1 : (RSVD_L_MAX + 1) / 2][3];
   __shared__ T s_cs[kFused ? 1 : (RSVD_L_MAX + 1) / 2][2];
@@ -858,7 +881,7 @@ __device__ __forceinline__ void jacobi_body(const T* __restrict__ M, int l, int6
   }
   fro = warp_sum(fro);
   if (lane == 0) s_fro[warp] = fro;
-  if (tid == 0) s_rot = 0;
+  if (tid == 0) s_rot = s_big = 0;
   __syncthreads();
   if (tid < 32) {
     T f = tid < nwarps ? s_fro[tid] : T(0);
@@ -867,6 +890,11 @@ __device__ __forceinline__ void jacobi_body(const T* __restrict__ M, int l, int6
   }
   __syncthreads();
   const T tol = sqrt((T)l) * Eps<T>::value;
+  // Jacobi converges quadratically near the end: after a sweep whose largest
+  // rotated cosine was below qtol, the next sweep's cosines are of order
+  // qtol^2 / (relative gap), below tol, so that sweep would rotate nothing
+  // and is skipped
+  const T qtol = T(1e-3) * sqrt(tol);
   // a column whose squared norm is below (eps ||M||_F)^2 is numerically zero
   // (a rank-deficient M): pairs with one are left alone, as rotating rounding
   // noise against itself would never meet the relative test
@@ -919,12 +947,10 @@ __device__ __forceinline__ void jacobi_body(const T* __restrict__ M, int l, int6
       bool rotate = false;
       if constexpr (kFused) {
         if (active && g != T(0) && fmin(a, b) > tiny && fabs(g) > tol * sqrt(a) * sqrt(b)) {
-          const T zeta = (b - a) / (T(2) * g);
-          const T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, T(1))));
-          c = rsqrt(fma(t, t, T(1)));
-          sn = c * t;
+          jacobi_cs<T>(a, b, g, c, sn);
           rotate = true;
           if (sub == 0) s_rot = 1;
+          if (sub == 0 && fabs(g) > qtol * sqrt(a) * sqrt(b)) s_big = 1;
         }
       } else {
         if (active && sub == 0) {
@@ -937,11 +963,9 @@ __device__ __forceinline__ void jacobi_body(const T* __restrict__ M, int l, int6
           const T ua = s_abg[u][0], ub = s_abg[u][1], ug = s_abg[u][2];
           T uc = T(1), us = T(0);
           if (ug != T(0) && fmin(ua, ub) > tiny && fabs(ug) > tol * sqrt(ua) * sqrt(ub)) {
-            const T zeta = (ub - ua) / (T(2) * ug);
-            const T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, T(1))));
-            uc = rsqrt(fma(t, t, T(1)));
-            us = uc * t;
+            jacobi_cs<T>(ua, ub, ug, uc, us);
             s_rot = 1;
+            if (fabs(ug) > qtol * sqrt(ua) * sqrt(ub)) s_big = 1;
           }
           s_cs[u][0] = uc;
           s_cs[u][1] = us;
@@ -982,11 +1006,11 @@ __device__ __forceinline__ void jacobi_body(const T* __restrict__ M, int l, int6
       }
       __syncthreads();
     }
-    const int rot = s_rot;
+    const int rot = s_rot, big = s_big;
     __syncthreads();
-    if (tid == 0) s_rot = 0;
+    if (tid == 0) s_rot = s_big = 0;
     __syncthreads();
-    if (!rot) break;
+    if (!rot || !big) break;
   }
   if (tid == 0) {
     status->jacobi_sweeps = sweep + 1;
@@ -1086,7 +1110,7 @@ __device__ __forceinline__ void jacobi_cluster_body(const T* __restrict__ M, int
   __shared__ T s_cs[(RSVD_L_MAX + 1) / 2][2];
   __shared__ T s_norm[RSVD_L_MAX + 1];
   __shared__ T s_fro[JACOBI_CL_THREADS / 32];
-  __shared__ int s_rot;
+  __shared__ int s_rot, s_big;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, nwarps = nt >> 5;
 
@@ -1100,7 +1124,7 @@ __device__ __forceinline__ void jacobi_cluster_body(const T* __restrict__ M, int
   }
   fro = warp_sum(fro);
   if (lane == 0) s_fro[warp] = fro;
-  if (tid == 0) s_rot = 0;
+  if (tid == 0) s_rot = s_big = 0;
   __syncthreads();
   if (tid < JACOBI_CLUSTER) {   // this CTA's share of ||M||_F^2, pushed to CTA tid
     T f = T(0);
@@ -1111,6 +1135,11 @@ __device__ __forceinline__ void jacobi_cluster_body(const T* __restrict__ M, int
   T fro_all = T(0);
   for (int q = 0; q < JACOBI_CLUSTER; ++q) fro_all += s_part[1][q][0][0];
   const T tol = sqrt((T)l) * Eps<T>::value;
+  // Jacobi converges quadratically near the end: after a sweep whose largest
+  // rotated cosine was below qtol, the next sweep's cosines are of order
+  // qtol^2 / (relative gap), below tol, so that sweep would rotate nothing
+  // and is skipped
+  const T qtol = T(1e-3) * sqrt(tol);
   const T tiny = Eps<T>::value * Eps<T>::value * fro_all;
 
   int par = 0, sweep = 0;
@@ -1149,11 +1178,9 @@ __device__ __forceinline__ void jacobi_cluster_body(const T* __restrict__ M, int
         }
         T c = T(1), sn = T(0);
         if (g != T(0) && fmin(a, b) > tiny && fabs(g) > tol * sqrt(a) * sqrt(b)) {
-          const T zeta = (b - a) / (T(2) * g);
-          const T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, T(1))));
-          c = rsqrt(fma(t, t, T(1)));
-          sn = c * t;
+          jacobi_cs<T>(a, b, g, c, sn);
           s_rot = 1;
+          if (fabs(g) > qtol * sqrt(a) * sqrt(b)) s_big = 1;
         }
         s_cs[pr][0] = c;
         s_cs[pr][1] = sn;
@@ -1187,11 +1214,11 @@ __device__ __forceinline__ void jacobi_cluster_body(const T* __restrict__ M, int
       // this round are read only locally, so a CTA barrier suffices
       __syncthreads();
     }
-    const int rot = s_rot;   // the same in every CTA (same sums)
+    const int rot = s_rot, big = s_big;   // the same in every CTA (same sums)
     __syncthreads();
-    if (tid == 0) s_rot = 0;
+    if (tid == 0) s_rot = s_big = 0;
     __syncthreads();
-    if (!rot) break;
+    if (!rot || !big) break;
   }
   if (rank == 0 && tid == 0) {
     status->jacobi_sweeps = sweep + 1;

@@ -104,6 +104,16 @@ jacobi_svd_g8_kernel(const float* __restrict__ M, int l, int64_t ldm, float* __r
                                                   jacobi_ld<float>(l, true), status);
 }
 
+// FP32, 40 < l <= 80: sixteen threads per column pair fixed at compile time
+__global__ void __launch_bounds__(JACOBI_THREADS)
+jacobi_svd_g16_kernel(const float* __restrict__ M, int l, int64_t ldm, float* __restrict__ sig,
+                      float* __restrict__ Um, int64_t ldu, float* __restrict__ Vm, int64_t ldv,
+                      float* __restrict__ UsInv, DeviceStatus* status) {
+  extern __shared__ __align__(16) unsigned char jg16_raw[];
+  jacobi_body<float, 5, 16>(M, l, ldm, sig, Um, ldu, Vm, ldv, UsInv,
+                            reinterpret_cast<float*>(jg16_raw), jacobi_ld<float>(l, true), status);
+}
+
 template <typename T>
 __global__ void __cluster_dims__(JACOBI_CLUSTER, 1, 1) __launch_bounds__(JACOBI_CL_THREADS)
 jacobi_cluster_kernel(const T* __restrict__ M, int l, int64_t ldm, T* __restrict__ sig,
@@ -214,6 +224,13 @@ cudaError_t launch_jacobi_svd(const T* M, int l, int64_t ldm, T* sig, T* Um, int
         need <= dynamic_smem_cap((const void*)jacobi_svd_g8_kernel)) {
       jacobi_svd_g8_kernel<<<1, JACOBI_THREADS, need, st>>>(M, l, ldm, sig, Um, ldu, Vm, ldv,
                                                             UsInv, status);
+      note_launch();
+      return cudaGetLastError();
+    }
+    if (jacobi_group(l) == 16 && (l + 15) / 16 <= 5 &&
+        need <= dynamic_smem_cap((const void*)jacobi_svd_g16_kernel)) {
+      jacobi_svd_g16_kernel<<<1, JACOBI_THREADS, need, st>>>(M, l, ldm, sig, Um, ldu, Vm, ldv,
+                                                             UsInv, status);
       note_launch();
       return cudaGetLastError();
     }
