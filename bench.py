@@ -586,24 +586,39 @@ def run_batched(args, stream):
     # the problems FP32 cannot resolve to the tolerance (fixed by the inputs)
     promote = [i for i, (_, S, _) in enumerate(outs) if not serve.fp32_meets(S.cpu().tolist(), tol)]
     items64 = [(items[i][0].to(torch.float64),) + tuple(items[i][1:]) for i in promote]
-    plan64 = None
-    outs64 = []
+    outs64 = [(torch.empty(k, m, dtype=torch.float64, device="cuda"),
+               torch.empty(k, dtype=torch.float64, device="cuda"),
+               torch.empty(n, k, dtype=torch.float64, device="cuda"))
+              for (_, m, n, k, _, _, _) in items64]
+    # the FP64 re-solves: tensor-core FP64 plans on eight streams, so their
+    # l x l steps (one or a few SMs each) overlap
+    nside = min(8, len(items64))
+    side = [torch.cuda.Stream() for _ in range(nside)]
+    tplans = []
     if items64:
-        plan64 = R.BatchPlan(len(items64), sum(it[1] for it in items64),
-                             sum(it[2] for it in items64), l_max, R.F64)
-        outs64 = [(torch.empty(k, m, dtype=torch.float64, device="cuda"),
-                   torch.empty(k, dtype=torch.float64, device="cuda"),
-                   torch.empty(n, k, dtype=torch.float64, device="cuda"))
-                  for (_, m, n, k, _, _, _) in items64]
+        mmax = max(it[1] for it in items64)
+        nmax = max(it[2] for it in items64)
+        tplans = [R.Plan(mmax, nmax, l_max, mode=R.F64_TENSOR, stream=sd) for sd in side]
 
     def step():
         plan.solve(items, outs)
-        if plan64 is not None:
-            plan64.solve(items64, outs64)
+        if not items64:
+            return
+        go = torch.cuda.Event()
+        go.record(stream)
+        for sd in side:
+            sd.wait_event(go)
+        for j, (A, m, n, k, p, q, seed) in enumerate(items64):
+            tplans[j % nside].solve(A, m, n, k, p, q, seed, out=outs64[j])
+        for sd in side:
+            done = torch.cuda.Event()
+            done.record(sd)
+            stream.wait_event(done)
 
     for _ in range(3):
         step()
-    codes = plan.status() + (plan64.status() if plan64 is not None else [])
+    torch.cuda.synchronize()
+    codes = plan.status() + [tp.status() for tp in tplans]
     steps = 5
     torch.cuda.synchronize()
     a = torch.cuda.Event(enable_timing=True)
@@ -634,11 +649,12 @@ def run_batched(args, stream):
     peaks, _ = _peaks()
     fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     achieved = flops / (ms / 1e3) / 1e12
-    del plan, plan64
+    del plan, tplans
     return {"workload": "512 FP32 matrices, m log-uniform [256,4096], n uniform [256,2048], "
                         "sigma_i=exp(-i/r), r~U[5,50]; k~U{10..64}, p=10, q=1; one grouped solve; "
                         "each problem to 1e-3 relative on every sigma (FP64 re-solve where FP32 "
-                        "cannot resolve sigma_k)",
+                        "cannot resolve sigma_k, on tensor-core FP64 plans over 8 streams; the "
+                        "set is fixed by the inputs and found once before timing)",
             "value": round(len(items) / (ms / 1e3), 1), "unit": "solves/s",
             "ms_per_batch": round(ms, 3), "problems": len(items),
             "promoted_to_fp64": len(promote),
@@ -921,7 +937,7 @@ def run_ours(args):
         S_h.copy_(S, non_blocking=True)
         VT_h.copy_(VT, non_blocking=True)
 
-    e2e_steps = max(1, min(args.steps, 5))
+    e2e_steps = max(1, min(args.steps, 10))
     e2e_step(0)
     torch.cuda.synchronize()
     _barrier(world)

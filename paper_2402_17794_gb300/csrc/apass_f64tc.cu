@@ -544,13 +544,15 @@ apass_f64tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
 // out (rows_out x l, ldo, FP64) = 2^(e_row + f_c - 14) (T 2^-24 + R 2^-32),
 // with T, R summed over the tile's sources: the raw buffer for tiles one CTA
 // wrote whole, the partial slots for split tiles (FixList).  Grid: (tile,
-// column group of 8); one thread per tile row.
+// column group of cpb columns); one thread per tile row.  Few tiles (a Gram's
+// single tile split over many CTAs) take one column per block, so the sums
+// over the partial slots spread over more SMs.
 __global__ void f64tc_finalize_kernel(const int64_t* __restrict__ raw_t,
                                       const float* __restrict__ raw_r, int64_t rows_out, int l,
                                       const int64_t* __restrict__ part_t,
                                       const float* __restrict__ part_r,
                                       const int* __restrict__ rmax, const int* __restrict__ fexp,
-                                      double* __restrict__ out, int64_t ldo,
+                                      double* __restrict__ out, int64_t ldo, int cpb,
                                       const __grid_constant__ FixList fl) {
   const int t = blockIdx.x;
   __shared__ int s_idx;
@@ -566,8 +568,8 @@ __global__ void f64tc_finalize_kernel(const int64_t* __restrict__ raw_t,
   const int64_t row = (int64_t)t * TC_BM + r;
   if (row >= rows_out) return;
   const int per_tile = TC_BM * l;
-  for (int cc = 0; cc < 8; ++cc) {
-    const int c = blockIdx.y * 8 + cc;
+  for (int cc = 0; cc < cpb; ++cc) {
+    const int c = blockIdx.y * cpb + cc;
     if (c >= l) break;
     long long T = 0;
     double R = 0.0;
@@ -689,10 +691,11 @@ int launch_apass_f64tc(const F64tcCall& c, int num_sms, int* status, cudaStream_
 #undef RSVD_F64TC
     note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail("apass_f64tc_kernel", e);
-    const dim3 fgrid((unsigned)tiles, (unsigned)((lb + 7) / 8));
+    const int cpb = tiles * ((lb + 7) / 8) < 2 * num_sms ? 1 : 8;
+    const dim3 fgrid((unsigned)tiles, (unsigned)((lb + cpb - 1) / cpb));
     f64tc_finalize_kernel<<<fgrid, TC_BM, 0, st>>>(c.raw_t, c.raw_r, rows_out, lb, c.part_t,
                                                    c.part_r, c.ax ? c.rmax : nullptr, c.fexp,
-                                                   c.out + (int64_t)c0 * c.ldo, c.ldo, fl);
+                                                   c.out + (int64_t)c0 * c.ldo, c.ldo, cpb, fl);
     note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail("f64tc_finalize_kernel", e);
   }

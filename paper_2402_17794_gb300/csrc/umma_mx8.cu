@@ -405,13 +405,19 @@ __device__ __forceinline__ int pow2_floor_exp(unsigned bits) {
   return (e == 0 || e == 0xFF) ? 0 : e - 127;
 }
 
+// 2^k as an FP32 (k in [-126, 127]): exact power-of-two scaling by a multiply.
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }
+
 // X (FP32, rows x l, ld ldx) -> S E4M3 slices of the column-normalised
 // x 2^-d_c (d_c from the column maxima), slice j column c at
 // out[(j * l16 + c) * ldo + r] (columns l .. l16 zero), and the exponent of
 // each chunk of `chunk` rows (64 or 128, the pass's stage depth):
 // e_k = floor(log2 max |x 2^-d_c|) - 7 over the chunk (0 for an all-zero
 // chunk), so slice 0 holds magnitudes below 256.  Block 0 also writes
-// colscale[c] = 2^d_c.  One block per chunk.
+// colscale[c] = 2^d_c.  One block per chunk; each thread takes four
+// consecutive rows of a column and stores each slice's four codes as one
+// 32-bit word.  Every scaling is by a power of two (exact), and each
+// residual is exact: v minus its E4M3 rounding.
 __global__ void __launch_bounds__(256) split_e4m3_kernel(const float* __restrict__ X, int64_t rows,
                                                          int l, int64_t ldx, int l16, int S,
                                                          int chunk,
@@ -420,22 +426,28 @@ __global__ void __launch_bounds__(256) split_e4m3_kernel(const float* __restrict
                                                          int* __restrict__ xexp,
                                                          float* __restrict__ colscale) {
   __shared__ float s_mx[8];
-  __shared__ int s_d[256];
+  __shared__ float s_inv[256];   // 2^-d_c
   const int64_t r0 = (int64_t)blockIdx.x * chunk;
   const int tid = threadIdx.x;
   for (int c = tid; c < l16; c += 256) {
     const int d = c < l ? max(-120, min(120, pow2_floor_exp(colbits[c]))) : 0;
-    s_d[c] = d;
-    if (blockIdx.x == 0) colscale[c] = ldexpf(1.f, d);
+    s_inv[c] = pow2f(-d);
+    if (blockIdx.x == 0) colscale[c] = pow2f(d);
   }
   __syncthreads();
-  const int phases = 256 / chunk;
-  const int rr = tid % chunk, cq = tid / chunk;   // row in chunk, column phase
-  const int64_t r = r0 + rr;
+  const int quads = chunk / 4, phases = 256 / quads;
+  const int qd = tid % quads, cq = tid / quads;   // row quad in the chunk, column phase
+  const int64_t r = r0 + 4 * qd;
+  const int64_t left = rows - r;
+  const int nr = left <= 0 ? 0 : (left >= 4 ? 4 : (int)left);   // rows of this quad
   float mx = 0.f;
-  if (r < rows)
-    for (int c = cq; c < l; c += phases)
-      mx = fmaxf(mx, fabsf(ldexpf(X[r + (int64_t)c * ldx], -s_d[c])));
+  for (int c = cq; c < l; c += phases) {
+    const float* x = X + r + (int64_t)c * ldx;
+    const float sc = s_inv[c];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (k < nr) mx = fmaxf(mx, fabsf(x[k] * sc));
+  }
 #pragma unroll
   for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if ((tid & 31) == 0) s_mx[tid >> 5] = mx;
@@ -447,15 +459,28 @@ __global__ void __launch_bounds__(256) split_e4m3_kernel(const float* __restrict
   if (mx > 0.f && isfinite(mx)) e = (int)((__float_as_uint(mx) >> 23) & 0xFF) - 127 - 7;
   e = max(-100, min(100, e));
   if (tid == 0) xexp[blockIdx.x] = e;
-  if (r >= rows) return;
+  if (nr == 0) return;
   for (int c = cq; c < l16; c += phases) {
-    float v = c < l ? ldexpf(X[r + (int64_t)c * ldx], -s_d[c]) : 0.f;
-    int ej = e;
+    float v[4];
+    const float sc = s_inv[c];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = (c < l && k < nr) ? X[r + k + (int64_t)c * ldx] * sc : 0.f;
+    uint8_t* o = out + (int64_t)c * ldo + r;
     for (int j = 0; j < S; ++j) {
-      const __nv_fp8_e4m3 q(ldexpf(v, -ej));   // round to nearest, saturating
-      out[(int64_t)(j * l16 + c) * ldo + r] = q.__x;
-      v -= ldexpf(float(q), ej);               // exact: the rounding error of v
-      ej -= 4;
+      const float down = pow2f(-(e - 4 * j)), up = pow2f(e - 4 * j);
+      uint32_t word = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const __nv_fp8_e4m3 q(v[k] * down);   // round to nearest, saturating
+        word |= (uint32_t)q.__x << (8 * k);
+        v[k] -= float(q) * up;                // exact: the rounding error of v
+      }
+      uint8_t* oj = o + (int64_t)j * l16 * ldo;
+      if (nr == 4) {
+        *reinterpret_cast<uint32_t*>(oj) = word;
+      } else {
+        for (int k = 0; k < nr; ++k) oj[k] = (uint8_t)(word >> (8 * k));
+      }
     }
   }
 }
