@@ -153,11 +153,13 @@ cudaError_t launch_tri_product(const T* R2, const T* R1, int l, T* out, bool tra
 
 // One-CTA one-sided Jacobi SVD of the l x l matrix M (ldm): M = Um diag(sig) Vm^T.
 // Vm may be NULL (rotations not accumulated); UsInv (ld l), if non-NULL,
-// receives Um diag(1/sig).  work holds 2 * l_even * l elements.
+// receives Um diag(1/sig).  work holds 2 * l_even * l elements.  skip (device,
+// may be NULL): when *skip is nonzero at launch time the kernel returns at
+// once and writes nothing (FP64 only).
 template <typename T>
 cudaError_t launch_jacobi_svd(const T* M, int l, int64_t ldm, T* sig, T* Um, int64_t ldu, T* Vm,
                               int64_t ldv, T* UsInv, T* work, DeviceStatus* status,
-                              cudaStream_t st);
+                              cudaStream_t st, const int* skip = nullptr);
 
 // Sign convention + outputs of the lift: flips columns of U (m x k, ldu) so
 // each column's largest-|.| entry is positive, writes S[i] = sig[i] and
@@ -180,6 +182,11 @@ cudaError_t launch_chol64(const T* G, int64_t ldg, int l, T* R, T* Rinv, void* w
 cudaError_t launch_svd_refine(const double* M, int l, double* U, double* V, double* s, int steps,
                               double cluster_tol, double* work, cudaStream_t st);
 // Us = U diag(1/s) (0 where s_i <= 0); V = M^T Us; C = A B (all l x l, ld l, FP64).
+// accept = 1 when the refined SVD (U, V, s) of M passes the convergence check
+// of svd_refine.cu (U, V orthogonal to 1e-13, U^T M V diagonal to 1e-12 of
+// each pair's larger sigma), else 0.  work: 4 l^2 doubles.
+cudaError_t launch_svd_accept(const double* M, int l, const double* U, const double* V,
+                              const double* s, double* work, int* accept, cudaStream_t st);
 cudaError_t launch_scale_cols(const double* U, const double* s, int l, double* Us,
                               cudaStream_t st);
 cudaError_t launch_right_vectors(const double* M, const double* Us, int l, double* V,

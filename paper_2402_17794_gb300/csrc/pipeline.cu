@@ -184,7 +184,7 @@ Layout make_layout(int64_t m, int64_t n, int l, int mode, int num_sms, bool f64t
                  align_up(((size_t)l * l + 33 * (size_t)(l + 64)) * e));
   L.sp = take(L.small_stride * kSinglePassSlots + align_up(kSinglePassVecs * (size_t)l * e));
   L.ad = take((size_t)m * l * e);
-  L.refine = take(((size_t)16 * l * l + 4 * (size_t)l) * sizeof(double));
+  L.refine = take(((size_t)20 * l * l + 8 * (size_t)l) * sizeof(double));
   L.chol64 = take(chol64_work_bytes(l));
   if (mode == RSVD_MODE_MIXED) {
     const int l16 = (l + 15) / 16 * 16;
@@ -497,11 +497,24 @@ int small_svd_fp64(rsvd_plan_t P, const Work<T>& W, int l, T* us_inv, double* si
     // much: two Newton-Schulz steps make it orthogonal to FP64 rounding
     RSVD_CK(launch_orthonormalize(V64, l, 2, work, st));
     RSVD_CK(launch_small_product(W.Mt, V64, l, M64, st));          // Mt V
+    // FP64 refinement of the FP32 SVD (three Ogita-Aishima steps on copies),
+    // kept when the check finds U, V orthogonal and U^T Mt V diagonal to FP64
+    // rounding; otherwise (close singular values, a poor FP32 start) the FP64
+    // one-sided Jacobi of Mt V recomputes the outputs
+    double *Ur = d + 16 * ll, *Vr = d + 17 * ll;
+    int* accept = (int*)(d + 18 * ll);
+    RSVD_CK((launch_convert<float, double>(U32, (int64_t)ll, Ur, st)));
+    RSVD_CK((launch_convert<double, double>(V64, (int64_t)ll, Vr, st)));
+    RSVD_CK((launch_convert<float, double>(s32, (int64_t)l, s64, st)));
+    RSVD_CK(launch_svd_refine(W.Mt, l, Ur, Vr, s64, 3, 1e-6, work, st));
+    RSVD_CK(launch_svd_accept(W.Mt, l, Ur, Vr, s64, work, accept, st));
+    RSVD_CK((launch_convert<double, double>(s64, (int64_t)l, W.sig, st)));
+    RSVD_CK((launch_convert<double, double>(Ur, (int64_t)ll, W.Um, st)));
+    RSVD_CK(launch_scale_cols(Ur, s64, l, us_inv, st));
     RSVD_CK(launch_jacobi_svd<double>(M64, l, l, W.sig, W.Um, l, nullptr, l, us_inv, W.jw,
-                                      status, st));
+                                      status, st, accept));
     (void)U64;
     (void)Us64;
-    (void)s64;
     (void)sig64;
   } else {
     RSVD_CK(launch_jacobi_svd<float>(W.Mt, l, l, W.sig, W.Um, l, nullptr, l, nullptr, W.jw,

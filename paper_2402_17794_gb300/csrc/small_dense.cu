@@ -86,7 +86,8 @@ __global__ void __launch_bounds__(JACOBI_THREADS)
 jacobi_svd_kernel(const T* __restrict__ M, int l, int64_t ldm, T* __restrict__ sig,
                   T* __restrict__ Um, int64_t ldu, T* __restrict__ Vm, int64_t ldv,
                   T* __restrict__ UsInv, T* __restrict__ gwork, int use_smem,
-                  DeviceStatus* status) {
+                  DeviceStatus* status, const int* __restrict__ skip) {
+  if (skip && *skip) return;
   extern __shared__ __align__(16) unsigned char jsm_raw[];
   T* Wm = use_smem ? reinterpret_cast<T*>(jsm_raw) : gwork;
   jacobi_body<T>(M, l, ldm, sig, Um, ldu, Vm, ldv, UsInv, Wm, jacobi_ld<T>(l, use_smem != 0),
@@ -118,7 +119,10 @@ template <typename T>
 __global__ void __cluster_dims__(JACOBI_CLUSTER, 1, 1) __launch_bounds__(JACOBI_CL_THREADS)
 jacobi_cluster_kernel(const T* __restrict__ M, int l, int64_t ldm, T* __restrict__ sig,
                       T* __restrict__ Um, int64_t ldu, T* __restrict__ Vm, int64_t ldv,
-                      T* __restrict__ UsInv, DeviceStatus* status) {
+                      T* __restrict__ UsInv, DeviceStatus* status, const int* __restrict__ skip) {
+  // every CTA of the cluster reads the same flag and leaves before any
+  // cluster barrier
+  if (skip && *skip) return;
   extern __shared__ __align__(16) unsigned char jcl_raw[];
   jacobi_cluster_body<T>(M, l, ldm, sig, Um, ldu, Vm, ldv, UsInv, reinterpret_cast<T*>(jcl_raw),
                          status);
@@ -202,7 +206,8 @@ cudaError_t launch_tri_product(const T* R2, const T* R1, int l, T* out, bool tra
 template <typename T>
 cudaError_t launch_jacobi_svd(const T* M, int l, int64_t ldm, T* sig, T* Um, int64_t ldu, T* Vm,
                               int64_t ldv, T* UsInv, T* work, DeviceStatus* status,
-                              cudaStream_t st) {
+                              cudaStream_t st, const int* skip) {
+  if (sizeof(T) == 4) skip = nullptr;
   // FP64, l >= 24: the cluster version (rows over JACOBI_CLUSTER SMs), as one
   // SM's FP64 pipe (2 FMA per clock) bounds the one-CTA kernel; measured
   // 3.9 ms against 6.7 ms at l = 80.  FP32 (and small l) stay on one CTA: a
@@ -212,7 +217,7 @@ cudaError_t launch_jacobi_svd(const T* M, int l, int64_t ldm, T* sig, T* Um, int
     const size_t cneed = jacobi_cluster_elems(l, Vm != nullptr) * sizeof(T);
     if (cneed <= dynamic_smem_cap((const void*)jacobi_cluster_kernel<T>)) {
       jacobi_cluster_kernel<T><<<JACOBI_CLUSTER, JACOBI_CL_THREADS, cneed, st>>>(
-          M, l, ldm, sig, Um, ldu, Vm, ldv, UsInv, status);
+          M, l, ldm, sig, Um, ldu, Vm, ldv, UsInv, status, skip);
       note_launch();
       return cudaGetLastError();
     }
@@ -237,7 +242,7 @@ cudaError_t launch_jacobi_svd(const T* M, int l, int64_t ldm, T* sig, T* Um, int
   }
   const bool smem = need <= dynamic_smem_cap((const void*)jacobi_svd_kernel<T>);
   jacobi_svd_kernel<T><<<1, JACOBI_THREADS, smem ? need : 0, st>>>(
-      M, l, ldm, sig, Um, ldu, Vm, ldv, UsInv, work, smem ? 1 : 0, status);
+      M, l, ldm, sig, Um, ldu, Vm, ldv, UsInv, work, smem ? 1 : 0, status, skip);
   note_launch();
   return cudaGetLastError();
 }
@@ -271,7 +276,8 @@ cudaError_t launch_sign_columns(T* U, int64_t m, int64_t ldu, int k, T* sign_wor
   template cudaError_t launch_tri_product<T>(const T*, const T*, int, T*, bool, cudaStream_t); \
   template cudaError_t launch_shift_diag<T>(T*, int, int64_t, double, cudaStream_t);           \
   template cudaError_t launch_jacobi_svd<T>(const T*, int, int64_t, T*, T*, int64_t, T*,       \
-                                            int64_t, T*, T*, DeviceStatus*, cudaStream_t);     \
+                                            int64_t, T*, T*, DeviceStatus*, cudaStream_t,      \
+                                            const int*);                                       \
   template cudaError_t launch_finalize<T>(T*, int64_t, int64_t, int, const T*, int64_t, T*,    \
                                           int64_t, const T*, double*, T*, cudaStream_t);       \
   template cudaError_t launch_sign_columns<T>(T*, int64_t, int64_t, int, T*, cudaStream_t);

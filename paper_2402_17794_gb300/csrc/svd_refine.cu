@@ -172,6 +172,62 @@ cudaError_t launch_svd_refine(const double* M, int l, double* U, double* V, doub
   return cudaSuccess;
 }
 
+namespace {
+// accept[0] = 1 when U, V are orthogonal to 1e-13 (max |I - U^T U|,
+// max |I - V^T V|) and U^T M V is diagonal to 1e-12 of the larger singular
+// value of each pair (|T_ij| <= 1e-12 max(s_i, s_j, eps s_1)), everything
+// finite; else 0.  Then the refined s carries each sigma to about
+// T_ij^2 / (s_i |s_i - s_j|) <= 1e-24 s / |s_i - s_j| relative, far below
+// the rounding of the FP64 solve except for pairs closer than ~1e-10, whose
+// sigmas the bound still holds to ~1e-14.  One block.
+__global__ void svd_accept_kernel(const double* __restrict__ UtU, const double* __restrict__ VtV,
+                                  const double* __restrict__ T, const double* __restrict__ s,
+                                  int l, int* __restrict__ accept) {
+  __shared__ int s_bad;
+  __shared__ double s_max;
+  if (threadIdx.x == 0) {
+    s_bad = 0;
+    double mx = 0.0;
+    for (int i = 0; i < l; ++i) mx = fmax(mx, fabs(s[i]));
+    s_max = mx;
+  }
+  __syncthreads();
+  const double floor_s = 2.220446049250313e-16 * s_max;
+  int bad = !(s_max > 0.0) || !isfinite(s_max);
+  for (int t = threadIdx.x; t < l * l; t += blockDim.x) {
+    const int i = t % l, j = t / l;
+    const double e = i == j ? 1.0 : 0.0;
+    const double u = UtU[t], v = VtV[t], x = T[t];
+    if (!(fabs(e - u) <= 1e-13) || !(fabs(e - v) <= 1e-13)) bad = 1;
+    if (i != j) {
+      const double den = fmax(fmax(fabs(s[i]), fabs(s[j])), floor_s);
+      if (!(fabs(x) <= 1e-12 * den)) bad = 1;
+    }
+  }
+  if (bad) atomicOr(&s_bad, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) *accept = s_bad ? 0 : 1;
+}
+}  // namespace
+
+cudaError_t launch_svd_accept(const double* M, int l, const double* U, const double* V,
+                              const double* s, double* work, int* accept, cudaStream_t st) {
+  const size_t ll = (size_t)l * l;
+  double *P = work, *UtU = work + ll, *VtV = work + 2 * ll, *T = work + 3 * ll;
+  cudaError_t e;
+  Prods a;
+  a.p[0] = prod(M, 0, V, 0, P);          // P = M V
+  a.p[1] = prod(U, 1, U, 0, UtU);        // U^T U
+  a.p[2] = prod(V, 1, V, 0, VtV);        // V^T V
+  if ((e = prods(a, 3, l, st)) != cudaSuccess) return e;
+  Prods b;
+  b.p[0] = prod(U, 1, P, 0, T);          // T = U^T M V
+  if ((e = prods(b, 1, l, st)) != cudaSuccess) return e;
+  svd_accept_kernel<<<1, 1024, 0, st>>>(UtU, VtV, T, s, l, accept);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_scale_cols(const double* U, const double* s, int l, double* Us,
                               cudaStream_t st) {
   scale_cols_kernel<<<(l * l + 255) / 256, 256, 0, st>>>(U, s, l, Us);

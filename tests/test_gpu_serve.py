@@ -93,3 +93,36 @@ def test_served_results_equal_solo_results_and_meet_their_tolerance():
             assert rel <= 1e-10, (r.rid, rel)
     # the acceptance rule's bound on FP32 sigma errors holds with room to spare
     assert worst <= serve.FP32_ERR_COEF * serve.FP32_UNIT, worst
+
+
+def test_tensor_lane_serves_fp64_requests_like_a_solo_tensor_plan():
+    """FP64 big requests on "tensor" lanes (one request at a time on a
+    tensor-core FP64 plan): each result equals the same request solved alone
+    on such a plan, and meets the plain FP64 bar against the oracle."""
+    rng = np.random.default_rng(3)
+    A = syn.lowrank_matrix(2000, 1500, syn.spectrum("poly", 1500, alpha=1.0), seed=19)
+    dA = R.from_numpy_f(A)
+    torch.cuda.synchronize()
+    reqs = []
+    t = 0.0
+    for i in range(6):
+        t += float(rng.exponential(0.003))
+        k, p, q = (100, 20, 2) if i % 2 == 0 else (40, 10, 1)
+        reqs.append(serve.Request(i, 2000, 1500, k, p, q, 1e-6, 300 + i, t, A=dA))
+    specs = [serve.LaneSpec("f64-small", 4, 4 * 2000, 4 * 1500, 80),
+             serve.LaneSpec("f64-big", 1, 2000, 1500, 288, engine="tensor", lanes=2)]
+    srv = serve.Server(specs, serve.TorchBackend(), 8 * 10**9, lanes_per_class=1)
+    stats = serve.run(srv, reqs, time.perf_counter, max_wall=120.0)
+    torch.cuda.synchronize()
+    assert stats["completed"] == 6 and stats["failed"] == 0
+    for r in srv.finished:
+        ref = oracle.rsvd(A, r.k, r.p, r.q, r.seed)
+        s = r.result[1].cpu().numpy()
+        assert (np.abs(s - ref.S) / ref.S).max() <= 1e-10, r.rid
+        if serve.request_class(r) == "f64-big":
+            solo = R.Plan(2000, 1500, r.l, mode=R.F64_TENSOR)
+            U, S, VT = solo.solve(dA, r.m, r.n, r.k, r.p, r.q, r.seed)
+            torch.cuda.synchronize()
+            assert solo.status() == 0
+            for x, y in zip((U, S, VT), r.result):
+                assert torch.equal(x, y), r.rid

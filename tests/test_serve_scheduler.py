@@ -208,3 +208,29 @@ def test_tight_tolerance_goes_straight_to_fp64():
     stats = serve.run(srv, [r], clock)
     assert stats["completed"] == 1 and stats["promotions"] == 0
     assert r.lane.startswith("f64") and not r.promoted
+
+
+def test_tensor_lanes_take_fp64_requests_one_at_a_time():
+    clock = Clock()
+    import pytest
+    bad = [serve.LaneSpec("f64-big", 2, 2 * 8192, 2 * 8192, 288, engine="tensor")]
+    with pytest.raises(ValueError):
+        serve.Server(bad, FakeBackend(clock), 10**12)
+    bad = [serve.LaneSpec("f32-big", 1, 8192, 8192, 288, engine="tensor")]
+    with pytest.raises(ValueError):
+        serve.Server(bad, FakeBackend(clock), 10**12)
+    ok = [serve.LaneSpec("f64-big", 1, 8192, 8192, 288, engine="tensor", lanes=3),
+          serve.LaneSpec("f64-small", 8, 8 * 4096, 8 * 2048, 80)]
+    srv = serve.Server(ok, FakeBackend(clock), 10**12, lanes_per_class=2)
+    assert sum(1 for l in srv.lanes if l.spec.name == "f64-big") == 3
+    assert sum(1 for l in srv.lanes if l.spec.name == "f64-small") == 2
+
+
+def test_drain_cap_counts_unserved_requests():
+    clock = Clock()
+    srv = serve.Server(SPECS, FakeBackend(clock), 10**12, lanes_per_class=1)
+    reqs = _requests(400, seed=5, rate=1e6)
+    stats = serve.run(srv, reqs, clock, max_wall=1e9, drain_s=0.0)
+    assert stats["completed"] + stats["unserved"] == 400
+    assert stats["unserved"] > 0
+    assert len(srv.finished) == stats["completed"]
