@@ -149,6 +149,44 @@ __global__ void slice_a_kernel(const double* __restrict__ A, int64_t m, int64_t 
   }
 }
 
+// The same with two consecutive rows per thread (A 16-byte aligned, lda and
+// ldsl even): one 16-byte load and one 4-byte store per slice for the pair,
+// so each warp writes whole 128-byte lines.
+__global__ void slice_a2_kernel(const double* __restrict__ A, int64_t m, int64_t n, int64_t lda,
+                                const int* __restrict__ rmax, __nv_bfloat16* __restrict__ sl,
+                                int64_t ldsl, int64_t ncol) {
+  const int64_t i = 2 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+  if (i >= m) return;
+  const bool pair = i + 1 < m;
+  const size_t sstride = (size_t)ncol * ldsl;
+  const int e0 = rmax[i] - 1022, e1 = pair ? rmax[i + 1] - 1022 : 0;
+  for (int64_t j = blockIdx.y; j < ncol; j += gridDim.y) {
+    float d0[TC_S], d1[TC_S];
+    if (j < n) {
+      double2 a;
+      if (pair) {
+        a = *reinterpret_cast<const double2*>(A + i + j * lda);
+      } else {
+        a.x = A[i + j * lda];
+        a.y = 0.0;
+      }
+      digits6(a.x, e0, d0);
+      digits6(a.y, e1, d1);
+    } else {
+#pragma unroll
+      for (int t = 0; t < TC_S; ++t) d0[t] = d1[t] = 0.f;
+    }
+    __nv_bfloat16* o = sl + i + j * ldsl;
+#pragma unroll
+    for (int t = 0; t < TC_S; ++t) {
+      if (pair)
+        *reinterpret_cast<__nv_bfloat162*>(o + t * sstride) = __floats2bfloat162_rn(d0[t], d1[t]);
+      else
+        o[t * sstride] = __float2bfloat16_rn(d0[t]);
+    }
+  }
+}
+
 // The six digit slices of X (rows x l, ldx), one block per column c < W:
 // f_c from the column's largest exponent (after the 2^r_k row scaling when
 // rmax is given), slice t of element (k, c) at xs[(t * W + c) * ldxs + k].
@@ -615,10 +653,19 @@ int f64tc_prepare_a(const double* A, int64_t m, int64_t n, int64_t lda, void* sl
   rowexp_kernel<<<g1, 256, 0, st>>>(A, m, n, lda, cpb, rmax, status);
   note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail("rowexp_kernel", e);
-  const int64_t rb = (m + 255) / 256;
-  const int64_t cy = std::max<int64_t>(1, std::min<int64_t>(ncol, ((int64_t)num_sms * 32 + rb - 1) / rb));
-  slice_a_kernel<<<dim3((unsigned)rb, (unsigned)std::min<int64_t>(cy, 65535)), 256, 0, st>>>(
-      A, m, n, lda, rmax, (__nv_bfloat16*)slices, ldsl, ncol);
+  if (lda % 2 == 0 && ldsl % 2 == 0 && (uintptr_t)A % 16 == 0 && (uintptr_t)slices % 4 == 0) {
+    const int64_t rb = (m + 511) / 512;
+    const int64_t cy =
+        std::max<int64_t>(1, std::min<int64_t>(ncol, ((int64_t)num_sms * 32 + rb - 1) / rb));
+    slice_a2_kernel<<<dim3((unsigned)rb, (unsigned)std::min<int64_t>(cy, 65535)), 256, 0, st>>>(
+        A, m, n, lda, rmax, (__nv_bfloat16*)slices, ldsl, ncol);
+  } else {
+    const int64_t rb = (m + 255) / 256;
+    const int64_t cy =
+        std::max<int64_t>(1, std::min<int64_t>(ncol, ((int64_t)num_sms * 32 + rb - 1) / rb));
+    slice_a_kernel<<<dim3((unsigned)rb, (unsigned)std::min<int64_t>(cy, 65535)), 256, 0, st>>>(
+        A, m, n, lda, rmax, (__nv_bfloat16*)slices, ldsl, ncol);
+  }
   note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail("slice_a_kernel", e);
   return RSVD_OK;

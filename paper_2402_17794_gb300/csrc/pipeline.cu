@@ -478,6 +478,45 @@ template int orth_shifted<double>(rsvd_plan_t, const double*, int64_t, int, int6
 //  * FP32 (mixed): the FP32 one-sided Jacobi, then two FP64 refinement steps
 //    of (U, sig, V = Mt^T U diag(1/sig)) against the FP64 copy of Mt; sig64
 //    receives the FP64 singular values for the output.
+// FP64-accurate M = U diag(sig) W^T of an l x l FP64 matrix M (ld l), U (ld
+// l) and sig only.  An FP32 one-sided Jacobi, three FP64 Ogita-Aishima
+// refinement steps on copies, and the convergence check; when the check
+// fails, the FP64 one-sided Jacobi of M V (V the FP32 rotations made
+// orthogonal in FP64 by two Newton-Schulz steps) recomputes U and sig (the
+// kernel reads the check's flag, so no host round trip).  Scratch: the plan's
+// refinement region.
+int svd64_u(rsvd_plan_t P, const double* M, int l, double* sig, double* U) {
+  const Work<double> W = work_of<double>(P);
+  const size_t ll = (size_t)l * l;
+  double* d = (double*)(P->ws + P->lay.refine);
+  double *M64 = d, *V64 = d + 2 * ll, *work = d + 4 * ll;
+  double* s64 = d + 12 * ll;
+  float* f = (float*)(d + 12 * ll + l);
+  float *M32 = f, *U32 = f + ll, *V32 = f + 2 * ll, *s32 = f + 3 * ll;
+  double *Ur = d + 16 * ll, *Vr = d + 17 * ll;
+  int* accept = (int*)(d + 18 * ll);
+  cudaStream_t st = P->stream;
+  DeviceStatus* status = dstatus(P);
+  RSVD_CK((launch_convert<double, float>(M, (int64_t)ll, M32, st)));
+  RSVD_CK(launch_jacobi_svd<float>(M32, l, l, s32, U32, l, V32, l, nullptr, (float*)W.jw,
+                                   status, st));
+  RSVD_CK((launch_convert<float, double>(V32, (int64_t)ll, V64, st)));
+  // V32 is orthogonal to about 1e-6, which would move sigma(M V) by as much:
+  // two Newton-Schulz steps make it orthogonal to FP64 rounding
+  RSVD_CK(launch_orthonormalize(V64, l, 2, work, st));
+  RSVD_CK(launch_small_product(M, V64, l, M64, st));          // M V
+  RSVD_CK((launch_convert<float, double>(U32, (int64_t)ll, Ur, st)));
+  RSVD_CK((launch_convert<double, double>(V64, (int64_t)ll, Vr, st)));
+  RSVD_CK((launch_convert<float, double>(s32, (int64_t)l, s64, st)));
+  RSVD_CK(launch_svd_refine(M, l, Ur, Vr, s64, 3, 1e-6, work, st));
+  RSVD_CK(launch_svd_accept(M, l, Ur, Vr, s64, work, accept, st));
+  RSVD_CK((launch_convert<double, double>(s64, (int64_t)l, sig, st)));
+  RSVD_CK((launch_convert<double, double>(Ur, (int64_t)ll, U, st)));
+  RSVD_CK(launch_jacobi_svd<double>(M64, l, l, sig, U, l, nullptr, l, nullptr, W.jw, status, st,
+                                    accept));
+  return RSVD_OK;
+}
+
 template <typename T>
 int small_svd_fp64(rsvd_plan_t P, const Work<T>& W, int l, T* us_inv, double* sig64) {
   const size_t ll = (size_t)l * l;
@@ -489,33 +528,19 @@ int small_svd_fp64(rsvd_plan_t P, const Work<T>& W, int l, T* us_inv, double* si
   cudaStream_t st = P->stream;
   DeviceStatus* status = dstatus(P);
   if constexpr (sizeof(T) == 8) {
-    RSVD_CK((launch_convert<double, float>(W.Mt, (int64_t)ll, M32, st)));
-    RSVD_CK(launch_jacobi_svd<float>(M32, l, l, s32, U32, l, V32, l, nullptr, (float*)W.jw,
-                                     status, st));
-    RSVD_CK((launch_convert<float, double>(V32, (int64_t)ll, V64, st)));
-    // V32 is orthogonal to about 1e-6, which would move sigma(Mt V) by as
-    // much: two Newton-Schulz steps make it orthogonal to FP64 rounding
-    RSVD_CK(launch_orthonormalize(V64, l, 2, work, st));
-    RSVD_CK(launch_small_product(W.Mt, V64, l, M64, st));          // Mt V
-    // FP64 refinement of the FP32 SVD (three Ogita-Aishima steps on copies),
-    // kept when the check finds U, V orthogonal and U^T Mt V diagonal to FP64
-    // rounding; otherwise (close singular values, a poor FP32 start) the FP64
-    // one-sided Jacobi of Mt V recomputes the outputs
-    double *Ur = d + 16 * ll, *Vr = d + 17 * ll;
-    int* accept = (int*)(d + 18 * ll);
-    RSVD_CK((launch_convert<float, double>(U32, (int64_t)ll, Ur, st)));
-    RSVD_CK((launch_convert<double, double>(V64, (int64_t)ll, Vr, st)));
-    RSVD_CK((launch_convert<float, double>(s32, (int64_t)l, s64, st)));
-    RSVD_CK(launch_svd_refine(W.Mt, l, Ur, Vr, s64, 3, 1e-6, work, st));
-    RSVD_CK(launch_svd_accept(W.Mt, l, Ur, Vr, s64, work, accept, st));
-    RSVD_CK((launch_convert<double, double>(s64, (int64_t)l, W.sig, st)));
-    RSVD_CK((launch_convert<double, double>(Ur, (int64_t)ll, W.Um, st)));
-    RSVD_CK(launch_scale_cols(Ur, s64, l, us_inv, st));
-    RSVD_CK(launch_jacobi_svd<double>(M64, l, l, W.sig, W.Um, l, nullptr, l, us_inv, W.jw,
-                                      status, st, accept));
+    if (int rc = svd64_u(P, W.Mt, l, W.sig, W.Um)) return rc;
+    RSVD_CK(launch_scale_cols(W.Um, W.sig, l, us_inv, st));
+    (void)M64;
     (void)U64;
+    (void)V64;
     (void)Us64;
+    (void)work;
     (void)sig64;
+    (void)M32;
+    (void)U32;
+    (void)V32;
+    (void)s32;
+    (void)status;
   } else {
     RSVD_CK(launch_jacobi_svd<float>(W.Mt, l, l, W.sig, W.Um, l, nullptr, l, nullptr, W.jw,
                                      status, st));

@@ -49,6 +49,10 @@ inline void f64tc_end(rsvd_plan_t P) { P->tc_A = nullptr; }
 template <typename T>
 Work<T> work_of(rsvd_plan_t P);
 MixedWork mixed_work_of(rsvd_plan_t P);
+// FP64-accurate SVD M = U diag(sig) W^T of an l x l FP64 matrix (ld l): U (ld
+// l) and sig, from an FP32 Jacobi refined in FP64 and checked, with the FP64
+// Jacobi as the fallback (pipeline.cu).  Uses the plan's refinement scratch.
+int svd64_u(rsvd_plan_t P, const double* M, int l, double* sig, double* U);
 DeviceStatus* dstatus(rsvd_plan_t P);
 bool plan_ready(rsvd_plan_t P);
 

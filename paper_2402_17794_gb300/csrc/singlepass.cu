@@ -152,8 +152,8 @@ int solve_singlepass(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64
   // 3. Y = Q1 R (Q1 in place of Y), R = Ur diag(s) W^T
   if ((rc = orth<T>(P, W.y, m, l, m, W.y, m, Rc, false))) return rc;
   if ((rc = orth<T>(P, W.z, n, l, n, W.z, n, Rr, false))) return rc;
-  RSVD_CK(launch_jacobi_svd<T>(Rc, l, l, sc, Uc, l, nullptr, l, nullptr, W.jw, status, st));
-  RSVD_CK(launch_jacobi_svd<T>(Rr, l, l, sr, Ur, l, nullptr, l, nullptr, W.jw, status, st));
+  if ((rc = svd64_u(P, Rc, l, sc, Uc))) return rc;
+  if ((rc = svd64_u(P, Rr, l, sr, Ur))) return rc;
   // 4. the joint least-squares system
   if ((rc = gemm<T>(P, W.qm, m, true, W.y, m, E, l, l, m, l))) return rc;    // Omega_r^T Q1c
   if ((rc = gemm<T>(P, W.om, n, true, W.z, n, E2, l, l, n, l))) return rc;   // Omega_c^T Q1r
@@ -165,8 +165,8 @@ int solve_singlepass(rsvd_plan_t P, const double* A, int64_t m, int64_t n, int64
   RSVD_CK(small_gemm<T>(Rt, l, true, Nt, l, false, F, k, k, k, l, true, st));     // + R N^T
   RSVD_CK(small_gemm<T>(Mm, l, true, Mm, l, false, A1, k, k, k, l, false, st));   // M^T M
   RSVD_CK(small_gemm<T>(Nt, l, true, Nt, l, false, B1, k, k, k, l, false, st));   // N N^T
-  RSVD_CK(launch_jacobi_svd<T>(A1, k, k, la, Va, k, nullptr, k, nullptr, W.jw, status, st));
-  RSVD_CK(launch_jacobi_svd<T>(B1, k, k, lb, Vb, k, nullptr, k, nullptr, W.jw, status, st));
+  if ((rc = svd64_u(P, A1, k, la, Va))) return rc;
+  if ((rc = svd64_u(P, B1, k, lb, Vb))) return rc;
   RSVD_CK(small_gemm<T>(Va, k, true, F, k, false, T1, k, k, k, k, false, st));    // Va^T F
   RSVD_CK(small_gemm<T>(T1, k, false, Vb, k, false, G, k, k, k, k, false, st));   // ... Vb
   sylvester_scale_kernel<T><<<(k * k + 255) / 256, 256, 0, st>>>(G, k, la, lb);
@@ -221,14 +221,14 @@ int solve_hermitian(rsvd_plan_t P, const double* A, int64_t n, int64_t lda, int 
   if ((rc = gemm<T>(P, A, lda, false, W.om, n, W.y, n, n, n, l))) return rc;
   // 3
   if ((rc = orth<T>(P, W.y, n, l, n, W.y, n, R, false))) return rc;
-  RSVD_CK(launch_jacobi_svd<T>(R, l, l, sr, Ur, l, nullptr, l, nullptr, W.jw, status, st));
+  if ((rc = svd64_u(P, R, l, sr, Ur))) return rc;
   // 4: E = Omega^T Q1 (l x l); N^T = E Ur_k (l x k); H^T = R^T Ur_k (l x k)
   if ((rc = gemm<T>(P, W.om, n, true, W.y, n, E, l, l, n, l))) return rc;
   RSVD_CK(small_gemm<T>(E, l, false, Ur, l, false, Nt, l, l, k, l, false, st));
   RSVD_CK(small_gemm<T>(R, l, true, Ur, l, false, Ht, l, l, k, l, false, st));
   RSVD_CK(small_gemm<T>(Ht, l, true, Nt, l, false, F, k, k, k, l, false, st));    // H N^T
   RSVD_CK(small_gemm<T>(Nt, l, true, Nt, l, false, B1, k, k, k, l, false, st));   // N N^T
-  RSVD_CK(launch_jacobi_svd<T>(B1, k, k, lb, Vb, k, nullptr, k, nullptr, W.jw, status, st));
+  if ((rc = svd64_u(P, B1, k, lb, Vb))) return rc;
   RSVD_CK(small_gemm<T>(F, k, false, Vb, k, false, G, k, k, k, k, false, st));    // F Vb
   RSVD_CK(cudaMemsetAsync(la, 0, sizeof(T) * (size_t)k, st));
   sylvester_scale_kernel<T><<<(k * k + 255) / 256, 256, 0, st>>>(G, k, la, lb);   // / lb_j
