@@ -1302,6 +1302,27 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_profile_batched(args):
+    """A reduced batched case for ncu captures (no timing): 96 problems of the
+    batched distribution (about 0.6 GB of FP32 A, larger than L2), two
+    grouped FP32 solves on the tensor engine."""
+    import torch
+
+    import __graft_entry__
+    from paper_2402_17794_gb300 import rsvd as R
+
+    __graft_entry__.build()
+    items = _batched_problems(96, 11)
+    plan = R.BatchPlan(len(items), sum(it[1] for it in items), sum(it[2] for it in items),
+                       max(it[3] + it[4] for it in items), R.F32)
+    for _ in range(2):
+        plan.solve(items)
+    torch.cuda.synchronize()
+    if any(c != 0 for c in plan.status()):
+        raise RuntimeError("batched: a problem failed")
+    print("profile batched done")
+
+
 def run_profile_case(args):
     """A reduced case of the same kernels for ncu captures (no timing):
     A 8192 x 4096 FP64 (268 MB, larger than L2), l = 80: two passes of each
@@ -1395,8 +1416,9 @@ def run_profile_case(args):
 
 def run_launch_case(args):
     """Two full solves of each timed workload, for an ncu launch list (no
-    timing): the plain FP64 solve on the tensor cores (16384 x 8192), then the
-    mixed solve on BF16 and on FP8 storage (65536 x 16384)."""
+    timing): the plain FP64 solve on the tensor cores (16384 x 8192), the
+    mixed solve on BF16 and on FP8 storage (65536 x 16384), then two grouped
+    FP32 solves of the 512-problem batch."""
     import torch
 
     import __graft_entry__
@@ -1424,6 +1446,19 @@ def run_launch_case(args):
             raise RuntimeError(f"{wname}: {R.rsvd_status_string(st)}")
         del dA, plan
         torch.cuda.empty_cache()
+    # the batched workload: two grouped FP32 solves of the 512 problems
+    items = _batched_problems(512, 11)
+    bplan = R.BatchPlan(len(items), sum(it[1] for it in items), sum(it[2] for it in items),
+                        max(it[3] + it[4] for it in items), R.F32)
+    outs = [(torch.empty(k, m, dtype=torch.float32, device="cuda"),
+             torch.empty(k, dtype=torch.float64, device="cuda"),
+             torch.empty(n, k, dtype=torch.float32, device="cuda"))
+            for (_, m, n, k, _, _, _) in items]
+    for _ in range(2):
+        bplan.solve(items, outs)
+    torch.cuda.synchronize()
+    if any(c != 0 for c in bplan.status()):
+        raise RuntimeError("batched: a problem failed")
     print("launch case done")
 
 
@@ -1448,7 +1483,12 @@ def main():
                     help="two full solves of each timed workload, for an ncu launch list")
     ap.add_argument("--profile-case", action="store_true",
                     help="run a reduced case of the same kernels for ncu (no timing)")
+    ap.add_argument("--profile-batched", action="store_true",
+                    help="run a reduced batched case (tensor engine) for ncu (no timing)")
     args = ap.parse_args()
+    if args.profile_batched:
+        run_profile_batched(args)
+        return
     if args.launch_case:
         run_launch_case(args)
         return

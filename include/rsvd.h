@@ -139,7 +139,10 @@ int rsvd_set_workspace(rsvd_plan_t plan, void* dev_ptr, size_t bytes);
 /*
  * rsvd_plan_status: waits for the plan's stream, then returns the status of
  * the work enqueued since the previous call (RSVD_OK or a positive code) and
- * clears it.  RSVD_ERR_CUDA if the stream reported an error.
+ * clears it.  RSVD_ERR_CUDA if the stream reported an error.  For a batch
+ * plan this is the plan-wide word of the tensor engine (RSVD_ERR_TIMEOUT
+ * when a grouped launch's bounded wait expired); per-problem codes come from
+ * rsvd_batch_status.
  */
 int rsvd_plan_status(rsvd_plan_t plan);
 
@@ -510,9 +513,11 @@ typedef struct rsvd_problem_s {
  * rsvd_batch_plan_create: a plan for batches of up to max_count problems
  * whose m's sum to at most rows_total and whose n's sum to at most
  * cols_total, each with k + p <= l_max.  a_dtype RSVD_F64 (every step in
- * FP64) or RSVD_F32 (every step in FP32) on the CUDA cores.  Workspace is
- * queried and set as for other plans.  Allocates pinned host memory for the
- * per-batch problem table and an event, nothing on the device.
+ * FP64 on the CUDA cores) or RSVD_F32 (every step in FP32: the grouped
+ * products on the tensor cores by default, see rsvd_batch_set_engine).
+ * Workspace is queried and set as for other plans.  Allocates pinned host
+ * memory for the per-batch problem table and an event, nothing on the
+ * device.
  * Errors: -1 plan; -2 max_count < 1; -3 rows_total < 1; -4 cols_total < 1;
  * -5 l_max outside 1..RSVD_L_MAX; -6 dtype; RSVD_ERR_CUDA.
  */
@@ -538,6 +543,70 @@ int rsvd_solve_batched(rsvd_plan_t plan, int count, const rsvd_problem_t* proble
  * the host array codes[0..count-1].
  */
 int rsvd_batch_status(rsvd_plan_t plan, int count, int* codes);
+
+/*
+ * Engines of an FP32 batch plan's grouped products (the passes over each A,
+ * the Gram and R^-1 products of CholeskyQR2 and the products with the small
+ * SVD's factors, Algorithm 4 steps 2-8):
+ *   RSVD_BATCH_ENGINE_TENSOR (default for FP32): one persistent tcgen05
+ *     launch per step over all problems.  Each FP32 value is split exactly
+ *     into three BF16 values and the six slice products with i + j <= 4 are
+ *     accumulated in FP32 (the accuracy of an FP32 product).  Work units
+ *     (128-row x column-tile output tiles, optionally split along the
+ *     contraction) are dealt to the SMs longest first.
+ *   RSVD_BATCH_ENGINE_SIMT: grouped CUDA-core launches (the only engine of
+ *     FP64 batch plans).
+ * rsvd_batch_set_engine errors: -1 plan is not a batch plan; -2 engine;
+ * RSVD_ERR_UNSUPPORTED for the tensor engine on an FP64 plan.
+ */
+#define RSVD_BATCH_ENGINE_SIMT 0
+#define RSVD_BATCH_ENGINE_TENSOR 1
+int rsvd_batch_set_engine(rsvd_plan_t plan, int engine);
+
+/*
+ * rsvd_batch_autotune: times the tensor engine's schedule candidates on the
+ * products of this batch (same arguments as rsvd_solve_batched) and keeps
+ * the fastest per shape bucket in a process-wide table:
+ *   - the contraction chunk (split-K: 16, 32, 64, 128 or 256 blocks of 64)
+ *     for each form and contraction-length bucket (64 2^(b-1), 64 2^b];
+ *   - the column-tile limit (48, 64 or 80) for each l bucket above 80.
+ * The first value recorded for a bucket stays for the life of the process,
+ * so every later solve gives a problem the same schedule -- and the same
+ * bits -- alone or in any batch.  Untuned buckets use 64 blocks and 80
+ * columns.  Enqueues trial runs on the plan's stream and waits for them;
+ * overwrites the plan's workspace (not the problems' outputs).
+ * Errors: as rsvd_solve_batched; RSVD_ERR_UNSUPPORTED unless the plan is an
+ * FP32 batch plan on the tensor engine.
+ */
+int rsvd_batch_autotune(rsvd_plan_t plan, int count, const rsvd_problem_t* problems);
+
+/*
+ * rsvd_grouped_gemm_f32: the tensor engine's grouped product on its own:
+ * for every entry, C (M x N, ldc >= M) = A X (trans = 0; A M x K, lda >= M)
+ * or A^T X (trans = 1; A stored K x M, lda >= K), X K x N (ldx >= K); all
+ * FP32 device memory, FP32-accurate (three BF16 slices of each operand).
+ * x_upper != 0: X is upper triangular (entries below its diagonal are read
+ * as zero).  M = 0 skips an entry.  Uses an FP32 batch plan's workspace and
+ * stream (up to max_count entries; the operand slices of all entries must
+ * fit the plan's slice space, 6 (rows_total + cols_total + 64 max_count)
+ * (l_max rounded up to 16, + 80) bytes); a timeout (an expired bounded
+ * wait, RSVD_ERR_TIMEOUT) shows in rsvd_plan_status of the batch plan.
+ * Errors: -1 not an FP32 batch plan on the tensor engine; -2 count outside
+ * 1..max_count; -3 gemms NULL; -(100 + i) entry i invalid;
+ * RSVD_ERR_WORKSPACE; RSVD_ERR_CUDA.
+ */
+typedef struct rsvd_gemm_s {
+  const float* A;
+  int64_t lda;
+  const float* X;
+  int64_t ldx;
+  float* C;
+  int64_t ldc;
+  int64_t M, K;
+  int N;
+  int x_upper;
+} rsvd_gemm_t;
+int rsvd_grouped_gemm_f32(rsvd_plan_t plan, int count, const rsvd_gemm_t* gemms, int trans);
 
 /* ---------------------------------------------------------------------- */
 /* Allocation-free entry point                                             */

@@ -22,6 +22,13 @@ class RsvdProblem(ctypes.Structure):
                 ("ldvt", c_int64)]
 
 
+class RsvdGemm(ctypes.Structure):
+    """rsvd_gemm_t of include/rsvd.h."""
+    _fields_ = [("A", c_void_p), ("lda", c_int64), ("X", c_void_p), ("ldx", c_int64),
+                ("C", c_void_p), ("ldc", c_int64), ("M", c_int64), ("K", c_int64),
+                ("N", c_int), ("x_upper", c_int)]
+
+
 # name -> (restype, argtypes), in the order of include/rsvd.h
 SIGNATURES = {
     "rsvd_plan_create": (c_int, [ctypes.POINTER(c_void_p), c_int64, c_int64, c_int, c_int, c_int,
@@ -75,6 +82,9 @@ SIGNATURES = {
                                        c_int, c_void_p]),
     "rsvd_solve_batched": (c_int, [c_void_p, c_int, ctypes.POINTER(RsvdProblem)]),
     "rsvd_batch_status": (c_int, [c_void_p, c_int, ctypes.POINTER(c_int)]),
+    "rsvd_batch_set_engine": (c_int, [c_void_p, c_int]),
+    "rsvd_batch_autotune": (c_int, [c_void_p, c_int, ctypes.POINTER(RsvdProblem)]),
+    "rsvd_grouped_gemm_f32": (c_int, [c_void_p, c_int, ctypes.POINTER(RsvdGemm), c_int]),
     "rsvd_apply_a_f64_static": (c_int, [c_void_p, c_int64, c_int64, c_int64, c_void_p, c_int64,
                                         c_int, c_void_p, c_int64, c_void_p]),
 }

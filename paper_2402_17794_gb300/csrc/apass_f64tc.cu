@@ -495,7 +495,9 @@ apass_f64tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
       const bool full_tile = (kb0 == 0) && (gend - t * args.kt == args.kt);
       for (int64_t c0 = g; c0 < gend; c0 += TC_CHUNK) {
         const bool last = c0 + TC_CHUNK >= gend;
-        if (!mbar_wait(acc_full, (uint32_t)(chunks & 1), abort_flag, args.wait_cycles)) {
+        // warp-uniform outcome: tcgen05.ld below is a warp-wide instruction
+        if (!__all_sync(0xffffffffu, mbar_wait(acc_full, (uint32_t)(chunks & 1), abort_flag,
+                                               args.wait_cycles))) {
           ok = false;
           break;
         }

@@ -18,6 +18,7 @@
 
 #include "batched.h"
 #include "gemm_body.cuh"
+#include "grouped_tc.h"
 #include "omega_body.cuh"
 #include "pipeline.h"
 #include "small_body.cuh"
@@ -45,6 +46,7 @@ struct Ctx {
   T *om, *y, *qm, *tmp, *z, *qb;
   T *G, *R1, *R1i, *R2, *R2i, *Mt, *Um, *UsInv, *jw, *sig, *sign, *cholw;
   DeviceStatus* status;
+  void* xs;   // tensor engine: this problem's slab of BF16 operand slices
 };
 
 // GEMM operands of each grouped step for one problem.
@@ -100,6 +102,35 @@ grouped_gemm_kernel(const Ctx<T>* __restrict__ ctx, int op, int iter) {
   const int c0 = blockIdx.z * 16 * TN;
   if (r0 >= g.M || c0 >= g.N) return;
   simt::gemm_tile<T, TN, TRANS>(g.A, g.lda, g.X, g.ldx, g.C, g.ldc, g.M, g.N, r0, c0, 0, g.K);
+}
+
+// Tensor engine: the grouped step's product table, one entry per problem
+// (M = 0 for problems outside this power iteration).  The column tile follows
+// the same rule as the host schedule, from the tile limits in `caps`.
+__global__ void gtc_table_kernel(const Ctx<float>* __restrict__ ctx, int count, int op, int iter,
+                                 int x_upper, GtcCaps caps, GtcGemm* __restrict__ tab) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const Ctx<float>& P = ctx[i];
+  const GemmArgs<float> a = op_args(P, op);
+  GtcGemm g;
+  g.A = a.A;
+  g.X = a.X;
+  g.C = a.C;
+  g.xs = reinterpret_cast<uint16_t*>(P.xs);
+  g.lda = a.lda;
+  g.ldx = a.ldx;
+  g.ldc = a.ldc;
+  g.M = active(P.q, iter) ? (int)a.M : 0;
+  g.K = (int)a.K;
+  g.N = a.N;
+  g.x_upper = x_upper;
+  g.kpad = (g.K + kGtcBlockK - 1) / kGtcBlockK * kGtcBlockK;
+  const int t = gtc_tile_rule(g.N, caps.cap[gtc_bucket(g.N)]);
+  g.ncols = (g.N + t - 1) / t * t;
+  g.t = t;
+  g.pad_ = 0;
+  tab[i] = g;
 }
 
 // Cholesky + inverse: which 0 -> (G, l) into R1/R1i, 1 -> into R2/R2i,
@@ -218,6 +249,168 @@ size_t small_elems(int l) {
          33 * (size_t)(l + 64);
 }
 
+// ---- tensor engine (FP32 batches) ----
+// The grouped products of a solve come in ten shapes (M, K, N per problem);
+// each has one work schedule, built on the host when the batch's shapes
+// change and kept on the device.
+constexpr int kGeo = 10;
+int geo_of(int op) {
+  switch (op) {
+    case OP_A_OM_Y: return 0;
+    case OP_AT_QM_Z: return 1;
+    case OP_GRAM_Y: case OP_GRAM_TM: return 2;
+    case OP_GRAM_Z: case OP_GRAM_TN: return 3;
+    case OP_TRSM_Y: case OP_TRSM_TM_QM: return 4;
+    case OP_TRSM_Z: case OP_TRSM_TN_OM: return 5;
+    case OP_LIFT_U: return 6;
+    case OP_LIFT_V: return 7;
+    case OP_GRAM_V: return 8;
+    default: return 9;   // OP_TRSM_V
+  }
+}
+bool geo_ax(int g) { return !(g == 1 || g == 2 || g == 3 || g == 8); }
+bool op_upper(int op) {
+  return op == OP_TRSM_Y || op == OP_TRSM_Z || op == OP_TRSM_TM_QM || op == OP_TRSM_TN_OM ||
+         op == OP_TRSM_V;
+}
+GtcShape geo_shape(int g, int64_t m64, int64_t n64, int l, int k) {
+  const int m = (int)m64, n = (int)n64;
+  switch (g) {
+    case 0: return {m, n, l};
+    case 1: return {n, m, l};
+    case 2: return {l, m, l};
+    case 3: return {l, n, l};
+    case 4: return {m, l, l};
+    case 5: return {n, l, l};
+    case 6: return {m, l, k};
+    case 7: return {n, l, k};
+    case 8: return {k, n, k};
+    default: return {n, k, k};
+  }
+}
+// a representative op of each shape (tuning runs)
+int geo_op(int g) {
+  const int ops[kGeo] = {OP_A_OM_Y, OP_AT_QM_Z, OP_GRAM_Y, OP_GRAM_Z, OP_TRSM_Y,
+                         OP_TRSM_Z, OP_LIFT_U, OP_LIFT_V, OP_GRAM_V, OP_TRSM_V};
+  return ops[g];
+}
+
+struct BatchTc {
+  std::vector<int64_t> sig;   // shapes and tuning generation the schedules were built for
+  GtcSchedule s[kGeo];
+  size_t uoff[kGeo], coff[kGeo], foff[kGeo];
+  std::vector<char> blob;
+};
+
+size_t align16(size_t x) { return (x + 15) / 16 * 16; }
+
+// Lays out schedules (units, CTA offsets, fix entries) in one blob at the
+// start of the plan's schedule region and copies it there (stream-ordered).
+int tc_upload(rsvd_plan_t P, BatchTc& S, int first, int last) {
+  const BatchLayout& L = *P->batch_lay;
+  S.blob.clear();
+  size_t off = 0;
+  for (int g = first; g < last; ++g) {
+    const GtcSchedule& sc = S.s[g];
+    S.uoff[g] = off;
+    off = align16(off + sc.units.size() * sizeof(GtcUnit));
+    S.coff[g] = off;
+    off = align16(off + sc.cta_off.size() * sizeof(int));
+    S.foff[g] = off;
+    off = align16(off + sc.fix.size() * sizeof(GtcFix));
+  }
+  if (off > L.sched_bytes) return RSVD_ERR_WORKSPACE;
+  S.blob.assign(off, 0);
+  for (int g = first; g < last; ++g) {
+    const GtcSchedule& sc = S.s[g];
+    if (!sc.units.empty())
+      std::memcpy(S.blob.data() + S.uoff[g], sc.units.data(), sc.units.size() * sizeof(GtcUnit));
+    std::memcpy(S.blob.data() + S.coff[g], sc.cta_off.data(), sc.cta_off.size() * sizeof(int));
+    if (!sc.fix.empty())
+      std::memcpy(S.blob.data() + S.foff[g], sc.fix.data(), sc.fix.size() * sizeof(GtcFix));
+  }
+  if (off) RSVD_CK(cudaMemcpyAsync(P->ws + L.sched, S.blob.data(), off, cudaMemcpyHostToDevice,
+                                   P->stream));
+  return RSVD_OK;
+}
+
+// A schedule whose partial slots do not fit is rebuilt without splits.
+void tc_build(rsvd_plan_t P, const GtcShape* sh, int count, bool ax, GtcSchedule& out,
+              int force_chunk = 0, const GtcCaps* caps = nullptr) {
+  const BatchLayout& L = *P->batch_lay;
+  gtc_schedule(sh, count, ax, P->num_sms, out, force_chunk, caps);
+  if ((size_t)out.slots * 128 * out.tmax > L.part_floats)
+    gtc_schedule(sh, count, ax, P->num_sms, out, 1 << 30, caps);
+}
+
+// Schedules of the ten shapes for the batch in the host context table.
+int tc_prepare(rsvd_plan_t P, int count) {
+  BatchTc* S = reinterpret_cast<BatchTc*>(P->batch_tc);
+  if (!S) {
+    S = new (std::nothrow) BatchTc();
+    if (!S) return RSVD_ERR_CUDA;
+    P->batch_tc = S;
+  }
+  const Ctx<float>* h = reinterpret_cast<const Ctx<float>*>(P->h_ctx);
+  std::vector<int64_t> sig;
+  sig.reserve(4 * (size_t)count + 2);
+  sig.push_back(count);
+  sig.push_back(gtc_generation());
+  for (int i = 0; i < count; ++i) {
+    sig.push_back(h[i].m);
+    sig.push_back(h[i].n);
+    sig.push_back(h[i].l);
+    sig.push_back(h[i].k);
+  }
+  if (sig == S->sig) return RSVD_OK;
+  S->sig.clear();
+  std::vector<GtcShape> sh(count);
+  for (int g = 0; g < kGeo; ++g) {
+    for (int i = 0; i < count; ++i) sh[i] = geo_shape(g, h[i].m, h[i].n, h[i].l, h[i].k);
+    tc_build(P, sh.data(), count, geo_ax(g), S->s[g]);
+  }
+  int rc = tc_upload(P, *S, 0, kGeo);
+  if (rc) return rc;
+  S->sig.swap(sig);
+  return RSVD_OK;
+}
+
+// One grouped product on the tensor engine: table, X slices, pass.
+int gtc_run(rsvd_plan_t P, const Ctx<float>* d, int count, int op, int iter,
+            const GtcSchedule& sc, size_t uoff, size_t coff, size_t foff, const GtcCaps& caps) {
+  const BatchLayout& L = *P->batch_lay;
+  GtcGemm* tab = reinterpret_cast<GtcGemm*>(P->ws + L.gtab);
+  gtc_table_kernel<<<(count + 127) / 128, 128, 0, P->stream>>>(d, count, op, iter,
+                                                              op_upper(op) ? 1 : 0, caps, tab);
+  note_launch();
+  RSVD_CK(cudaGetLastError());
+  int rc = launch_gtc_split(tab, count, (int)std::min<int64_t>(P->rows_total, 1 << 20),
+                            sc.tmax, P->stream);
+  if (rc) return rc;
+  GtcLaunch g;
+  g.ax = geo_ax(geo_of(op));
+  g.gemm = tab;
+  g.count = count;
+  g.tmax = sc.tmax;
+  g.units = reinterpret_cast<const GtcUnit*>(P->ws + L.sched + uoff);
+  g.cta_off = reinterpret_cast<const int*>(P->ws + L.sched + coff);
+  g.grid = sc.grid;
+  g.fix = reinterpret_cast<const GtcFix*>(P->ws + L.sched + foff);
+  g.nfix = (int)sc.fix.size();
+  g.part = reinterpret_cast<float*>(P->ws + L.part);
+  g.status = reinterpret_cast<int*>(P->ws + L.gflags);
+  g.wait_cycles = P->wait_cycles;
+  return launch_gtc(g, P->stream);
+}
+
+int gtc_op(rsvd_plan_t P, const Ctx<float>* d, const BatchShape& b, int op, int iter) {
+  BatchTc* S = reinterpret_cast<BatchTc*>(P->batch_tc);
+  const int g = geo_of(op);
+  GtcCaps caps;
+  gtc_caps(caps);
+  return gtc_run(P, d, b.count, op, iter, S->s[g], S->uoff[g], S->coff[g], S->foff[g], caps);
+}
+
 template <typename T, bool TRANS>
 int launch_grouped_gemm(rsvd_plan_t P, const Ctx<T>* dctx, const BatchShape& b, int op, int iter,
                         int64_t max_rows, int max_cols) {
@@ -239,6 +432,10 @@ int launch_grouped_gemm(rsvd_plan_t P, const Ctx<T>* dctx, const BatchShape& b, 
 
 template <typename T>
 int gop(rsvd_plan_t P, const Ctx<T>* d, const BatchShape& b, int op, int iter) {
+  if constexpr (sizeof(T) == 4) {
+    if (P->batch_engine == kBatchTensor)
+      return gtc_op(P, reinterpret_cast<const Ctx<float>*>(d), b, op, iter);
+  }
   const int64_t mm = b.max_m, nn = b.max_n;
   const int L = b.max_l, K = b.max_k;
   switch (op) {
@@ -357,7 +554,7 @@ int fill_ctx(rsvd_plan_t P, int count, const rsvd_problem_t* pr, BatchShape* b) 
   const BatchLayout& L = *P->batch_lay;
   Ctx<T>* h = reinterpret_cast<Ctx<T>*>(P->h_ctx);
   char* ws = P->ws;
-  int64_t moff = 0, noff = 0;
+  int64_t moff = 0, noff = 0, xoff = 0;
   b->count = count;
   b->max_m = b->max_n = 0;
   b->max_l = b->max_k = 1;
@@ -406,6 +603,11 @@ int fill_ctx(rsvd_plan_t P, int count, const rsvd_problem_t* pr, BatchShape* b) 
     c.sign = c.sig + lm;
     c.cholw = c.sign + lm;
     c.status = (DeviceStatus*)(sb + align_up(small_elems<T>(lm) * sizeof(T)));
+    c.xs = nullptr;
+    if (L.xs_ncols > 0) {
+      c.xs = ws + L.xs + (size_t)3 * 2 * L.xs_ncols * xoff;
+      xoff += std::max(q.m, q.n) + kGtcBlockK;
+    }
     moff += q.m;
     noff += q.n;
     b->max_m = std::max(b->max_m, q.m);
@@ -438,6 +640,25 @@ BatchLayout make_batch_layout(int max_count, int64_t rows_total, int64_t cols_to
   L.tmp = take((size_t)(rows_total + cols_total) * l * e);
   L.small = take((size_t)max_count * (align_up(small * e) + align_up(sizeof(DeviceStatus))));
   L.ctx = take((size_t)max_count * sizeof(Ctx<double>));
+  L.xs_ncols = 0;
+  L.sched_bytes = L.part_floats = 0;
+  L.gtab = L.xs = L.sched = L.part = L.gflags = off;
+  if (dtype == RSVD_F32) {
+    // slabs: 3 slices x (max(m, n) + 64) rows x (l rounded to 16 + 80) columns
+    // of BF16 per problem; schedules: ten shapes of at most
+    // 4 (rows + cols) / 128 + count row tiles x ceil(l / 48) column tiles each
+    L.xs_ncols = (l + 15) / 16 * 16 + kGtcMaxTile;
+    L.gtab = take((size_t)max_count * sizeof(GtcGemm));
+    L.xs = take((size_t)3 * 2 * L.xs_ncols * (size_t)(rows_total + cols_total +
+                                                      (int64_t)kGtcBlockK * max_count));
+    const size_t tiles = (size_t)4 * ((size_t)(rows_total + cols_total) / 128 + 2 * max_count) *
+                         (size_t)((l + 47) / 48);
+    L.sched_bytes = (size_t)kGeo * (tiles * (sizeof(GtcUnit) + sizeof(GtcFix)) + 4096 + 64);
+    L.sched = take(L.sched_bytes);
+    L.part_floats = (size_t)1024 * 128 * kGtcMaxTile;
+    L.part = take(L.part_floats * sizeof(float));
+    L.gflags = take(256);
+  }
   L.total = off;
   return L;
 }
@@ -470,7 +691,207 @@ int solve_batched(rsvd_plan_t P, int count, const rsvd_problem_t* pr) {
   }
   if (P->dtype == RSVD_F64)
     return solve_batched_t<double>(P, (const Ctx<double>*)dctx, b);
+  if (P->batch_engine == kBatchTensor) {
+    if ((rc = tc_prepare(P, count))) return rc;
+    RSVD_CK(cudaMemsetAsync(P->ws + P->batch_lay->gflags, 0, sizeof(int), P->stream));
+  }
   return solve_batched_t<float>(P, (const Ctx<float>*)dctx, b);
+}
+
+namespace {
+
+BatchTc* tc_state(rsvd_plan_t P) {
+  if (!P->batch_tc) P->batch_tc = new (std::nothrow) BatchTc();
+  return reinterpret_cast<BatchTc*>(P->batch_tc);
+}
+
+// Mean time of `reps` runs of one grouped product under schedule g of S.
+int time_run(rsvd_plan_t P, const Ctx<float>* d, int count, int g, BatchTc& S, const GtcCaps& caps,
+             cudaEvent_t e0, cudaEvent_t e1, float* ms) {
+  int rc;
+  if ((rc = gtc_run(P, d, count, geo_op(g), -1, S.s[g], S.uoff[g], S.coff[g], S.foff[g], caps)))
+    return rc;
+  RSVD_CK(cudaEventRecord(e0, P->stream));
+  const int reps = 3;
+  for (int r = 0; r < reps; ++r)
+    if ((rc = gtc_run(P, d, count, geo_op(g), -1, S.s[g], S.uoff[g], S.coff[g], S.foff[g], caps)))
+      return rc;
+  RSVD_CK(cudaEventRecord(e1, P->stream));
+  RSVD_CK(cudaEventSynchronize(e1));
+  RSVD_CK(cudaEventElapsedTime(ms, e0, e1));
+  *ms /= reps;
+  return RSVD_OK;
+}
+
+int autotune_body(rsvd_plan_t P, int count, const Ctx<float>* d, BatchTc& S, cudaEvent_t e0,
+                  cudaEvent_t e1) {
+  const Ctx<float>* h = reinterpret_cast<const Ctx<float>*>(P->h_ctx);
+  std::vector<GtcShape> sh(count);
+  int rc;
+  // 1. column tile limits for N above 80, on the passes over A (shapes 0, 1)
+  for (int g = 0; g < 2; ++g) {
+    std::vector<int> seen;
+    for (int i = 0; i < count; ++i) {
+      const int N = h[i].l;
+      const int B = gtc_bucket(N);
+      if (N <= kGtcMaxTile || gtc_tile_tuned(N) ||
+          std::find(seen.begin(), seen.end(), B) != seen.end())
+        continue;
+      seen.push_back(B);
+      int best = kGtcMaxTile;
+      float best_ms = 1e30f;
+      for (int cap : {48, 64, 80}) {
+        GtcCaps c2;
+        gtc_caps(c2);
+        c2.cap[B] = cap;
+        for (int j = 0; j < count; ++j) {
+          sh[j] = geo_shape(g, h[j].m, h[j].n, h[j].l, h[j].k);
+          if (gtc_bucket(sh[j].N) != B) sh[j].M = 0;
+        }
+        tc_build(P, sh.data(), count, geo_ax(g), S.s[g], 0, &c2);
+        if ((rc = tc_upload(P, S, g, g + 1))) return rc;
+        float ms = 0.f;
+        if ((rc = time_run(P, d, count, g, S, c2, e0, e1, &ms))) return rc;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = cap;
+        }
+      }
+      gtc_set_tile_cap(N, best);
+    }
+  }
+  // 2. contraction chunk per (form, K bucket) on the passes and the Grams
+  GtcCaps caps;
+  gtc_caps(caps);
+  for (int g = 0; g < 4; ++g) {
+    const bool ax = geo_ax(g);
+    std::vector<int> seen;
+    for (int i = 0; i < count; ++i) {
+      const int K = geo_shape(g, h[i].m, h[i].n, h[i].l, h[i].k).K;
+      const int B = gtc_bucket(K);
+      if (gtc_chunk_tuned(ax, K) || std::find(seen.begin(), seen.end(), B) != seen.end()) continue;
+      seen.push_back(B);
+      int kbmax = 1;
+      for (int j = 0; j < count; ++j) {
+        sh[j] = geo_shape(g, h[j].m, h[j].n, h[j].l, h[j].k);
+        if (gtc_bucket(sh[j].K) != B) sh[j].M = 0;
+        else kbmax = std::max(kbmax, (sh[j].K + kGtcBlockK - 1) / kGtcBlockK);
+      }
+      int best = kGtcDefaultChunk;
+      float best_ms = 1e30f;
+      bool whole_done = false;
+      for (int chunk : {16, 32, 64, 128, 256}) {
+        if (chunk >= kbmax) {
+          if (whole_done) continue;   // every candidate from here on splits nothing
+          whole_done = true;
+        }
+        tc_build(P, sh.data(), count, ax, S.s[g], chunk, &caps);
+        if ((rc = tc_upload(P, S, g, g + 1))) return rc;
+        float ms = 0.f;
+        if ((rc = time_run(P, d, count, g, S, caps, e0, e1, &ms))) return rc;
+        if (ms < best_ms * 0.97f) {   // a split has to win clearly
+          best_ms = ms;
+          best = chunk;
+        }
+      }
+      gtc_set_chunk(ax, K, best);
+    }
+  }
+  return RSVD_OK;
+}
+
+}  // namespace
+
+int batch_autotune(rsvd_plan_t P, int count, const rsvd_problem_t* pr) {
+  if (P->dtype != RSVD_F32 || P->batch_engine != kBatchTensor) return RSVD_ERR_UNSUPPORTED;
+  if (cudaEventSynchronize(P->ctx_event) != cudaSuccess) return RSVD_ERR_CUDA;
+  BatchShape b;
+  int rc;
+  if ((rc = fill_ctx<float>(P, count, pr, &b))) return rc;
+  void* dctx = P->ws + P->batch_lay->ctx;
+  RSVD_CK(cudaMemcpyAsync(dctx, P->h_ctx, (size_t)count * sizeof(Ctx<double>),
+                          cudaMemcpyHostToDevice, P->stream));
+  BatchTc* S = tc_state(P);
+  if (!S) return RSVD_ERR_CUDA;
+  S->sig.clear();   // the schedule region is reused by the trial runs
+  cudaEvent_t e0, e1;
+  RSVD_CK(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return RSVD_ERR_CUDA;
+  }
+  rc = autotune_body(P, count, reinterpret_cast<const Ctx<float>*>(dctx), *S, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  RSVD_CK(cudaEventRecord(P->ctx_event, P->stream));
+  S->sig.clear();
+  return rc;
+}
+
+int grouped_gemm_f32(rsvd_plan_t P, int count, const rsvd_gemm_t* gm, int trans) {
+  const BatchLayout& L = *P->batch_lay;
+  std::vector<GtcGemm> tab(count);
+  std::vector<GtcShape> sh(count);
+  const size_t xs_cap = (size_t)3 * 2 * L.xs_ncols *
+                        (size_t)(P->rows_total + P->cols_total + (int64_t)kGtcBlockK * P->max_count);
+  size_t xoff = 0;
+  for (int i = 0; i < count; ++i) {
+    const rsvd_gemm_t& q = gm[i];
+    GtcGemm& g = tab[i];
+    g.A = q.A;
+    g.X = q.X;
+    g.C = q.C;
+    g.lda = q.lda;
+    g.ldx = q.ldx;
+    g.ldc = q.ldc;
+    g.M = (int)q.M;
+    g.K = (int)q.K;
+    g.N = q.N;
+    g.x_upper = q.x_upper ? 1 : 0;
+    g.kpad = (g.K + kGtcBlockK - 1) / kGtcBlockK * kGtcBlockK;
+    const int t = gtc_tile(g.N);
+    g.ncols = (g.N + t - 1) / t * t;
+    g.t = t;
+    g.pad_ = 0;
+    const size_t bytes = (size_t)3 * 2 * g.kpad * g.ncols;
+    g.xs = reinterpret_cast<uint16_t*>(P->ws + L.xs + xoff);
+    xoff += (bytes + 255) / 256 * 256;
+    if (xoff > xs_cap) return RSVD_ERR_WORKSPACE;
+    sh[i] = {g.M, g.K, g.N};
+  }
+  BatchTc* S = tc_state(P);
+  if (!S) return RSVD_ERR_CUDA;
+  S->sig.clear();   // the schedule region is overwritten
+  const int g = trans ? 1 : 0;
+  tc_build(P, sh.data(), count, !trans, S->s[g]);
+  int rc;
+  if ((rc = tc_upload(P, *S, g, g + 1))) return rc;
+  GtcGemm* dtab = reinterpret_cast<GtcGemm*>(P->ws + L.gtab);
+  RSVD_CK(cudaMemcpyAsync(dtab, tab.data(), (size_t)count * sizeof(GtcGemm),
+                          cudaMemcpyHostToDevice, P->stream));
+  int max_kpad = 64;
+  for (const GtcGemm& t : tab) max_kpad = std::max(max_kpad, t.kpad);
+  if ((rc = launch_gtc_split(dtab, count, max_kpad, S->s[g].tmax, P->stream))) return rc;
+  GtcLaunch l;
+  l.ax = !trans;
+  l.gemm = dtab;
+  l.count = count;
+  l.tmax = S->s[g].tmax;
+  l.units = reinterpret_cast<const GtcUnit*>(P->ws + L.sched + S->uoff[g]);
+  l.cta_off = reinterpret_cast<const int*>(P->ws + L.sched + S->coff[g]);
+  l.grid = S->s[g].grid;
+  l.fix = reinterpret_cast<const GtcFix*>(P->ws + L.sched + S->foff[g]);
+  l.nfix = (int)S->s[g].fix.size();
+  l.part = reinterpret_cast<float*>(P->ws + L.part);
+  l.status = reinterpret_cast<int*>(P->ws + L.gflags);
+  l.wait_cycles = P->wait_cycles;
+  RSVD_CK(cudaMemsetAsync(P->ws + L.gflags, 0, sizeof(int), P->stream));
+  return launch_gtc(l, P->stream);
+}
+
+void batch_tc_free(rsvd_plan_t P) {
+  delete reinterpret_cast<BatchTc*>(P->batch_tc);
+  P->batch_tc = nullptr;
 }
 
 int batch_status(rsvd_plan_t P, int count, int* codes) {
@@ -482,9 +903,13 @@ int batch_status(rsvd_plan_t P, int count, int* codes) {
   // gather the first word (flags) of each problem's status into the pinned buffer
   RSVD_CK(cudaMemcpy2DAsync(P->h_ctx, sizeof(int), P->ws + P->batch_lay->small + st_off, per_small,
                             sizeof(int), count, cudaMemcpyDeviceToHost, P->stream));
+  int* f = (int*)P->h_ctx;
+  f[count] = 0;
+  if (P->batch_lay->xs_ncols > 0)   // a timeout in a tensor-engine launch concerns every problem
+    RSVD_CK(cudaMemcpyAsync(f + count, P->ws + P->batch_lay->gflags, sizeof(int),
+                            cudaMemcpyDeviceToHost, P->stream));
   RSVD_CK(cudaStreamSynchronize(P->stream));
-  const int* f = (const int*)P->h_ctx;
-  for (int i = 0; i < count; ++i) codes[i] = status_from_flags(f[i]);
+  for (int i = 0; i < count; ++i) codes[i] = status_from_flags(f[i] | f[count]);
   return RSVD_OK;
 }
 

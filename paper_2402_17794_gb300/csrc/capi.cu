@@ -95,6 +95,8 @@ int rsvd_plan_create(rsvd_plan_t* plan, int64_t m_max, int64_t n_max, int l_max,
   P->batch_lay = nullptr;
   P->h_ctx = nullptr;
   P->ctx_event = nullptr;
+  P->batch_engine = kBatchSimt;
+  P->batch_tc = nullptr;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
@@ -142,6 +144,8 @@ int rsvd_batch_plan_create(rsvd_plan_t* plan, int max_count, int64_t rows_total,
   P->h_ctx = nullptr;
   P->ctx_event = nullptr;
   P->h_status = nullptr;
+  P->batch_engine = a_dtype == RSVD_F32 ? kBatchTensor : kBatchSimt;
+  P->batch_tc = nullptr;
   P->batch_lay = new (std::nothrow) BatchLayout(
       make_batch_layout(max_count, rows_total, cols_total, l_max, a_dtype));
   int dev = 0;
@@ -149,8 +153,10 @@ int rsvd_batch_plan_create(rsvd_plan_t* plan, int max_count, int64_t rows_total,
       cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       cudaMallocHost(&P->h_ctx, batch_ctx_bytes(max_count) + 4 * sizeof(int) * max_count) !=
           cudaSuccess ||
+      cudaMallocHost((void**)&P->h_status, sizeof(int) * 8) != cudaSuccess ||
       cudaEventCreateWithFlags(&P->ctx_event, cudaEventDisableTiming) != cudaSuccess) {
     if (P->h_ctx) cudaFreeHost(P->h_ctx);
+    if (P->h_status) cudaFreeHost(P->h_status);
     delete P->batch_lay;
     delete P;
     return RSVD_ERR_CUDA;
@@ -177,6 +183,52 @@ int rsvd_solve_batched(rsvd_plan_t plan, int count, const rsvd_problem_t* proble
   }
   if (rows > plan->rows_total || cols > plan->cols_total) return RSVD_ERR_WORKSPACE;
   return solve_batched(plan, count, problems);
+}
+
+int rsvd_batch_set_engine(rsvd_plan_t plan, int engine) {
+  if (!plan || !plan->batched) return -1;
+  if (engine != RSVD_BATCH_ENGINE_SIMT && engine != RSVD_BATCH_ENGINE_TENSOR) return -2;
+  if (engine == RSVD_BATCH_ENGINE_TENSOR && plan->dtype != RSVD_F32) return RSVD_ERR_UNSUPPORTED;
+  plan->batch_engine = engine == RSVD_BATCH_ENGINE_TENSOR ? kBatchTensor : kBatchSimt;
+  return RSVD_OK;
+}
+
+int rsvd_batch_autotune(rsvd_plan_t plan, int count, const rsvd_problem_t* problems) {
+  if (!plan || !plan->batched) return -1;
+  if (count < 1 || count > plan->max_count) return -2;
+  if (!problems) return -3;
+  if (plan->dtype != RSVD_F32 || plan->batch_engine != kBatchTensor) return RSVD_ERR_UNSUPPORTED;
+  if (!plan->ws || plan->ws_bytes < plan->batch_lay->total) return RSVD_ERR_WORKSPACE;
+  int64_t rows = 0, cols = 0;
+  for (int i = 0; i < count; ++i) {
+    const rsvd_problem_t& q = problems[i];
+    const int l = q.k + q.p;
+    if (!q.A || q.m < 1 || q.n < 1 || q.lda < q.m || q.k < 1 || q.p < 0 || q.q < 0 ||
+        l > (q.m < q.n ? q.m : q.n) || !q.U || q.ldu < q.m || !q.S || !q.VT || q.ldvt < q.k)
+      return -(100 + i);
+    if (l > plan->l_max) return RSVD_ERR_WORKSPACE;
+    rows += q.m;
+    cols += q.n;
+  }
+  if (rows > plan->rows_total || cols > plan->cols_total) return RSVD_ERR_WORKSPACE;
+  return batch_autotune(plan, count, problems);
+}
+
+int rsvd_grouped_gemm_f32(rsvd_plan_t plan, int count, const rsvd_gemm_t* gemms, int trans) {
+  if (!plan || !plan->batched || plan->dtype != RSVD_F32 || plan->batch_engine != kBatchTensor)
+    return -1;
+  if (count < 1 || count > plan->max_count) return -2;
+  if (!gemms) return -3;
+  if (!plan->ws || plan->ws_bytes < plan->batch_lay->total) return RSVD_ERR_WORKSPACE;
+  for (int i = 0; i < count; ++i) {
+    const rsvd_gemm_t& g = gemms[i];
+    const bool bad = g.M < 0 || g.M > (1 << 30) || g.K < 1 || g.K > (1 << 30) || g.N < 1 ||
+                     g.N > RSVD_L_MAX ||
+                     (g.M > 0 && (!g.A || !g.X || !g.C || g.ldc < g.M || g.ldx < g.K ||
+                                  g.lda < (trans ? g.K : g.M)));
+    if (bad) return -(100 + i);
+  }
+  return grouped_gemm_f32(plan, count, gemms, trans);
 }
 
 int rsvd_batch_status(rsvd_plan_t plan, int count, int* codes) {
@@ -266,8 +318,20 @@ int rsvd_set_tile_scales(rsvd_plan_t plan, const float* scales, int64_t rows, in
 int rsvd_plan_status(rsvd_plan_t plan) {
   if (!plan) return -1;
   if (!plan->ws) return RSVD_ERR_WORKSPACE;
-  if (plan->batched)  // per-problem codes: rsvd_batch_status
-    return cudaStreamSynchronize(plan->stream) == cudaSuccess ? RSVD_OK : RSVD_ERR_CUDA;
+  if (plan->batched) {
+    // per-problem codes: rsvd_batch_status; here only the plan-wide word of
+    // the tensor engine (a timeout of a grouped launch), read and cleared
+    if (plan->batch_lay->xs_ncols == 0)
+      return cudaStreamSynchronize(plan->stream) == cudaSuccess ? RSVD_OK : RSVD_ERR_CUDA;
+    int* g = (int*)(plan->ws + plan->batch_lay->gflags);
+    if (cudaMemcpyAsync(plan->h_status, g, sizeof(int), cudaMemcpyDeviceToHost, plan->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(plan->stream) != cudaSuccess)
+      return RSVD_ERR_CUDA;
+    const int flags = plan->h_status[0];
+    if (cudaMemsetAsync(g, 0, sizeof(int), plan->stream) != cudaSuccess) return RSVD_ERR_CUDA;
+    return status_from_flags(flags);
+  }
   DeviceStatus* d = dstatus(plan);
   if (cudaMemcpyAsync(plan->h_status, &d->flags, sizeof(int), cudaMemcpyDeviceToHost,
                       plan->stream) != cudaSuccess)
@@ -296,6 +360,7 @@ int rsvd_plan_destroy(rsvd_plan_t plan) {
   if (plan->h_status) cudaFreeHost(plan->h_status);
   if (plan->h_ctx) cudaFreeHost(plan->h_ctx);
   if (plan->ctx_event) cudaEventDestroy(plan->ctx_event);
+  batch_tc_free(plan);
   delete plan->batch_lay;
   delete plan;
   return RSVD_OK;

@@ -84,6 +84,8 @@ struct rsvd_plan_s {
   rsvd::BatchLayout* batch_lay;   // owned
   void* h_ctx;                    // pinned staging for the context table
   cudaEvent_t ctx_event;          // marks the table copy of the last batched solve
+  int batch_engine;               // kBatchSimt or kBatchTensor (FP32 batch plans)
+  void* batch_tc;                 // tensor-engine host state (schedules), owned
   long long wait_cycles;          // rsvd_plan_set_wait_limit (0: the default bound)
   int f64tc;                      // RSVD_MODE_F64_TENSOR (mode holds RSVD_MODE_PLAIN)
   const void* tc_A;               // the A whose slices are current (during a call)

@@ -330,7 +330,8 @@ apass_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       int64_t t = g0 / args.kt;
       int kb = (int)(g0 - t * args.kt);
       for (int64_t g = g0; g < g1; ++g) {
-        if (!mbar_wait(&full[s], ph, abort_flag, args.wait_cycles)) break;
+        // warp-uniform outcome: the lanes meet again at __syncwarp below
+        if (!__all_sync(0xffffffffu, mbar_wait(&full[s], ph, abort_flag, args.wait_cycles))) break;
         uint8_t* a_s = tiles + (size_t)s * stage_bytes;
         const uint8_t* stg = a_s + A_BYTES + x_stage_bytes;
         // scales of the stage's MT tiles: AX walks 128-row tiles I of A at
@@ -379,7 +380,10 @@ apass_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       const int kb0 = (int)(g - t * args.kt);
       const int64_t gend = (g1 < (t + 1) * args.kt) ? g1 : (t + 1) * args.kt;
       const bool full_tile = (kb0 == 0) && (gend - t * args.kt == args.kt);
-      if (!mbar_wait(acc_full, (uint32_t)(seg & 1), abort_flag, args.wait_cycles)) break;
+      // warp-uniform outcome: tcgen05.ld below is a warp-wide instruction
+      if (!__all_sync(0xffffffffu, mbar_wait(acc_full, (uint32_t)(seg & 1), abort_flag,
+                                             args.wait_cycles)))
+        break;
       tc_fence_after();
       float* dst;
       int64_t ld;

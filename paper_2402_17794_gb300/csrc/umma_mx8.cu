@@ -306,8 +306,10 @@ apass_mx8_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                                      : 1.f);
       }
       const int e = __ldg(&args.xexp[kb]);
-      // the stage's previous MMAs have read its regions
-      if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, args.wait_cycles)) break;
+      // the stage's previous MMAs have read its regions (warp-uniform outcome:
+      // tcgen05.st below is a warp-wide instruction)
+      if (!__all_sync(0xffffffffu, mbar_wait(&empty[s], ph ^ 1u, abort_flag, args.wait_cycles)))
+        break;
       tc_fence_after();
       const uint32_t col = lane_base + (uint32_t)(s * sf_per_stage);
 #pragma unroll
@@ -334,7 +336,10 @@ apass_mx8_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
       const int kb0 = (int)(g - t * args.kt);
       const int64_t gend = (g1 < (t + 1) * args.kt) ? g1 : (t + 1) * args.kt;
       const bool full_tile = (kb0 == 0) && (gend - t * args.kt == args.kt);
-      if (!mbar_wait(acc_full, (uint32_t)(seg & 1), abort_flag, args.wait_cycles)) break;
+      // warp-uniform outcome: tcgen05.ld below is a warp-wide instruction
+      if (!__all_sync(0xffffffffu, mbar_wait(acc_full, (uint32_t)(seg & 1), abort_flag,
+                                             args.wait_cycles)))
+        break;
       tc_fence_after();
       float* dst;
       int64_t ld, row0;

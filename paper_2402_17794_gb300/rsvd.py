@@ -234,6 +234,24 @@ def rsvd_batch_status(plan, count):
     return list(codes)
 
 
+BATCH_ENGINE_SIMT, BATCH_ENGINE_TENSOR = 0, 1
+
+
+def rsvd_batch_set_engine(plan, engine) -> int:
+    return _lib.load().rsvd_batch_set_engine(plan, engine)
+
+
+def rsvd_batch_autotune(plan, problems) -> int:
+    arr = problems if isinstance(problems, ctypes.Array) else (_lib.RsvdProblem * len(problems))(*problems)
+    return _lib.load().rsvd_batch_autotune(plan, len(arr), arr)
+
+
+def rsvd_grouped_gemm_f32(plan, gemms, trans) -> int:
+    """gemms: a sequence of _lib.RsvdGemm (or an already built array)."""
+    arr = gemms if isinstance(gemms, ctypes.Array) else (_lib.RsvdGemm * len(gemms))(*gemms)
+    return _lib.load().rsvd_grouped_gemm_f32(plan, len(arr), arr, int(trans))
+
+
 def rsvd_apply_a_f64_static(A, m, n, lda, X, ldx, l, Y, ldy, stream=None) -> int:
     return _lib.load().rsvd_apply_a_f64_static(_ptr(A), m, n, lda, _ptr(X), ldx, l, _ptr(Y), ldy,
                                                _stream_handle(stream))
@@ -270,7 +288,7 @@ class BatchPlan:
                 pass
             self.handle = None
 
-    def solve(self, items, outs=None):
+    def _problems(self, items, outs):
         probs, results = [], []
         for i, (A, m, n, k, p, q, seed) in enumerate(items):
             if outs is None:
@@ -283,10 +301,31 @@ class BatchPlan:
                                           U.data_ptr(), U.shape[1], S.data_ptr(), VT.data_ptr(),
                                           VT.shape[1]))
             results.append((U, S, VT))
+        return probs, results
+
+    def solve(self, items, outs=None):
+        probs, results = self._problems(items, outs)
         _check(rsvd_solve_batched(self.handle, probs), "rsvd_solve_batched")
         self.count = len(probs)
         self._keep = (items, results)
         return results
+
+    def set_engine(self, engine):
+        _check(rsvd_batch_set_engine(self.handle, engine), "rsvd_batch_set_engine")
+
+    def autotune(self, items, outs=None):
+        """Tunes the tensor engine's schedules on these problems (FP32 plans)."""
+        probs, results = self._problems(items, outs)
+        _check(rsvd_batch_autotune(self.handle, probs), "rsvd_batch_autotune")
+
+    def grouped_gemm(self, gemms, trans):
+        """gemms: list of (A, lda, X, ldx, C, ldc, M, K, N, x_upper) with
+        device FP32 tensors; C = op(A) X on the tensor engine."""
+        arr = (_lib.RsvdGemm * len(gemms))(*[
+            _lib.RsvdGemm(_ptr(A), lda, _ptr(X), ldx, _ptr(C), ldc, M, K, N, int(xu))
+            for (A, lda, X, ldx, C, ldc, M, K, N, xu) in gemms])
+        self._keep_gemm = gemms
+        _check(rsvd_grouped_gemm_f32(self.handle, arr, trans), "rsvd_grouped_gemm_f32")
 
     def status(self):
         return rsvd_batch_status(self.handle, self.count)
