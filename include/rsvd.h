@@ -564,11 +564,37 @@ int rsvd_batch_status(rsvd_plan_t plan, int count, int* codes);
 int rsvd_batch_set_engine(rsvd_plan_t plan, int engine);
 
 /*
+ * rsvd_batch_set_graphs: on != 0 makes each rsvd_solve_batched of an FP32
+ * plan on the tensor engine one CUDA graph launch.  The graph (table copy,
+ * status resets and every grouped step of Algorithm 4) is captured on the
+ * plan's stream when the batch's launch signature -- each problem's m, n,
+ * k, p, q, the tuning table and the wait limit -- differs from the last
+ * capture, and replayed otherwise; operands and seeds may change between
+ * replays.  A capture costs about as much as a solve, so this pays for
+ * batches that repeat their shapes.  Needs a stream other than the legacy
+ * default stream.
+ * Errors: -1 not a batch plan; -2 the plan's stream is the default stream;
+ * RSVD_ERR_UNSUPPORTED unless the plan is FP32 on the tensor engine.
+ */
+int rsvd_batch_set_graphs(rsvd_plan_t plan, int on);
+
+/*
+ * rsvd_batch_set_sm_limit: the tensor engine's persistent launches of this
+ * plan use at most `sms` SMs (0: all of them), leaving the rest to work on
+ * other streams -- for instance FP64 solves of the problems an FP32 batch
+ * could not resolve.  The work split into units, and so every result, does
+ * not depend on the limit.  Errors: -1 not a batch plan; -2 sms < 0.
+ */
+int rsvd_batch_set_sm_limit(rsvd_plan_t plan, int sms);
+
+/*
  * rsvd_batch_autotune: times the tensor engine's schedule candidates on the
  * products of this batch (same arguments as rsvd_solve_batched) and keeps
  * the fastest per shape bucket in a process-wide table:
- *   - the contraction chunk (split-K: 16, 32, 64, 128 or 256 blocks of 64)
- *     for each form and contraction-length bucket (64 2^(b-1), 64 2^b];
+ *   - the contraction chunk (split-K: 4, 8, 16, 32, 64, 128 or 256 blocks
+ *     of 64) for each form, contraction-length bucket (64 2^(b-1), 64 2^b]
+ *     and output-row class (one 128-row tile, as in the Gram products, or
+ *     more);
  *   - the column-tile limit (48, 64 or 80) for each l bucket above 80.
  * The first value recorded for a bucket stays for the life of the process,
  * so every later solve gives a problem the same schedule -- and the same

@@ -83,6 +83,8 @@ SIGNATURES = {
     "rsvd_solve_batched": (c_int, [c_void_p, c_int, ctypes.POINTER(RsvdProblem)]),
     "rsvd_batch_status": (c_int, [c_void_p, c_int, ctypes.POINTER(c_int)]),
     "rsvd_batch_set_engine": (c_int, [c_void_p, c_int]),
+    "rsvd_batch_set_graphs": (c_int, [c_void_p, c_int]),
+    "rsvd_batch_set_sm_limit": (c_int, [c_void_p, c_int]),
     "rsvd_batch_autotune": (c_int, [c_void_p, c_int, ctypes.POINTER(RsvdProblem)]),
     "rsvd_grouped_gemm_f32": (c_int, [c_void_p, c_int, ctypes.POINTER(RsvdGemm), c_int]),
     "rsvd_apply_a_f64_static": (c_int, [c_void_p, c_int64, c_int64, c_int64, c_void_p, c_int64,

@@ -296,10 +296,18 @@ int geo_op(int g) {
 }
 
 struct BatchTc {
-  std::vector<int64_t> sig;   // shapes and tuning generation the schedules were built for
+  std::vector<int64_t> sig;    // shapes and tuning generation the solve's schedules were built for
+  std::vector<int64_t> gsig;   // the same for the schedule of rsvd_grouped_gemm_f32
   GtcSchedule s[kGeo];
   size_t uoff[kGeo], coff[kGeo], foff[kGeo];
   std::vector<char> blob;
+  // CUDA graph of a whole grouped solve (rsvd_batch_set_graphs), valid for
+  // the launch signature xsig
+  cudaGraphExec_t exec = nullptr;
+  std::vector<int64_t> xsig;
+  ~BatchTc() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
 };
 
 size_t align16(size_t x) { return (x + 15) / 16 * 16; }
@@ -338,9 +346,10 @@ int tc_upload(rsvd_plan_t P, BatchTc& S, int first, int last) {
 void tc_build(rsvd_plan_t P, const GtcShape* sh, int count, bool ax, GtcSchedule& out,
               int force_chunk = 0, const GtcCaps* caps = nullptr) {
   const BatchLayout& L = *P->batch_lay;
-  gtc_schedule(sh, count, ax, P->num_sms, out, force_chunk, caps);
+  const int sms = P->batch_sms > 0 ? std::min(P->batch_sms, P->num_sms) : P->num_sms;
+  gtc_schedule(sh, count, ax, sms, out, force_chunk, caps);
   if ((size_t)out.slots * 128 * out.tmax > L.part_floats)
-    gtc_schedule(sh, count, ax, P->num_sms, out, 1 << 30, caps);
+    gtc_schedule(sh, count, ax, sms, out, 1 << 30, caps);
 }
 
 // Schedules of the ten shapes for the batch in the host context table.
@@ -356,6 +365,7 @@ int tc_prepare(rsvd_plan_t P, int count) {
   sig.reserve(4 * (size_t)count + 2);
   sig.push_back(count);
   sig.push_back(gtc_generation());
+  sig.push_back(P->batch_sms);
   for (int i = 0; i < count; ++i) {
     sig.push_back(h[i].m);
     sig.push_back(h[i].n);
@@ -364,6 +374,7 @@ int tc_prepare(rsvd_plan_t P, int count) {
   }
   if (sig == S->sig) return RSVD_OK;
   S->sig.clear();
+  S->gsig.clear();   // the schedule region is rewritten below
   std::vector<GtcShape> sh(count);
   for (int g = 0; g < kGeo; ++g) {
     for (int i = 0; i < count; ++i) sh[i] = geo_shape(g, h[i].m, h[i].n, h[i].l, h[i].k);
@@ -655,7 +666,8 @@ BatchLayout make_batch_layout(int max_count, int64_t rows_total, int64_t cols_to
                          (size_t)((l + 47) / 48);
     L.sched_bytes = (size_t)kGeo * (tiles * (sizeof(GtcUnit) + sizeof(GtcFix)) + 4096 + 64);
     L.sched = take(L.sched_bytes);
-    L.part_floats = (size_t)1024 * 128 * kGtcMaxTile;
+    // partial slots of split tiles: up to eight per problem
+    L.part_floats = (size_t)std::max(1024, 8 * max_count) * 128 * kGtcMaxTile;
     L.part = take(L.part_floats * sizeof(float));
     L.gflags = take(256);
   }
@@ -664,6 +676,68 @@ BatchLayout make_batch_layout(int max_count, int64_t rows_total, int64_t cols_to
 }
 
 size_t batch_ctx_bytes(int max_count) { return (size_t)max_count * sizeof(Ctx<double>); }
+
+namespace {
+
+// Everything a grouped FP32 solve enqueues after its context table is
+// filled on the host (the part a CUDA graph captures): the table copy, the
+// status words, and the steps of Algorithm 4.
+int enqueue_f32(rsvd_plan_t P, int count, const BatchShape& b, bool capturing) {
+  const size_t bytes = (size_t)count * sizeof(Ctx<double>);
+  void* dctx = P->ws + P->batch_lay->ctx;
+  RSVD_CK(cudaMemcpyAsync(dctx, P->h_ctx, bytes, cudaMemcpyHostToDevice, P->stream));
+  // in a graph, an external record node: the event is recorded at every
+  // replay, so the next solve's host side waits for this copy
+  RSVD_CK(capturing ? cudaEventRecordWithFlags(P->ctx_event, P->stream, cudaEventRecordExternal)
+                    : cudaEventRecord(P->ctx_event, P->stream));
+  const size_t per_small = align_up(small_elems<float>(P->l_max) * sizeof(float)) +
+                           align_up(sizeof(DeviceStatus));
+  const size_t st_off = per_small - align_up(sizeof(DeviceStatus));
+  RSVD_CK(cudaMemset2DAsync(P->ws + P->batch_lay->small + st_off, per_small, 0,
+                            sizeof(DeviceStatus), count, P->stream));
+  if (P->batch_engine == kBatchTensor)
+    RSVD_CK(cudaMemsetAsync(P->ws + P->batch_lay->gflags, 0, sizeof(int), P->stream));
+  return solve_batched_t<float>(P, reinterpret_cast<const Ctx<float>*>(dctx), b);
+}
+
+// The same as one CUDA graph: captured when the launch signature (shapes,
+// power steps, tuning generation, wait limit) differs from the last capture,
+// replayed otherwise.  The graph's table copy reads the pinned staging
+// buffer at replay time, so new operands of the same shapes need no new
+// capture.
+int solve_f32_graph(rsvd_plan_t P, int count, const BatchShape& b) {
+  int rc;
+  if ((rc = tc_prepare(P, count))) return rc;   // schedule upload: outside the capture
+  BatchTc* S = reinterpret_cast<BatchTc*>(P->batch_tc);
+  const Ctx<float>* h = reinterpret_cast<const Ctx<float>*>(P->h_ctx);
+  std::vector<int64_t> sig = S->sig;
+  sig.push_back(P->wait_cycles);
+  for (int i = 0; i < count; ++i) sig.push_back(h[i].q);
+  if (!S->exec || sig != S->xsig) {
+    if (S->exec) cudaGraphExecDestroy(S->exec);
+    S->exec = nullptr;
+    S->xsig.clear();
+    RSVD_CK(cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal));
+    const int rc2 = enqueue_f32(P, count, b, true);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(P->stream, &graph);
+    if (rc2 || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc2 ? rc2 : RSVD_ERR_CUDA;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&S->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+      S->exec = nullptr;
+      return RSVD_ERR_CUDA;
+    }
+    S->xsig.swap(sig);
+  }
+  RSVD_CK(cudaGraphLaunch(S->exec, P->stream));
+  return RSVD_OK;
+}
+
+}  // namespace
 
 int solve_batched(rsvd_plan_t P, int count, const rsvd_problem_t* pr) {
   // the previous solve's table copy must have left the staging buffer
@@ -676,6 +750,8 @@ int solve_batched(rsvd_plan_t P, int count, const rsvd_problem_t* pr) {
     if ((rc = fill_ctx<double>(P, count, pr, &b))) return rc;
   } else {
     if ((rc = fill_ctx<float>(P, count, pr, &b))) return rc;
+    if (P->batch_graphs && P->batch_engine == kBatchTensor && P->stream != nullptr)
+      return solve_f32_graph(P, count, b);
   }
   RSVD_CK(cudaMemcpyAsync(dctx, P->h_ctx, bytes, cudaMemcpyHostToDevice, P->stream));
   RSVD_CK(cudaEventRecord(P->ctx_event, P->stream));
@@ -767,20 +843,22 @@ int autotune_body(rsvd_plan_t P, int count, const Ctx<float>* d, BatchTc& S, cud
     const bool ax = geo_ax(g);
     std::vector<int> seen;
     for (int i = 0; i < count; ++i) {
-      const int K = geo_shape(g, h[i].m, h[i].n, h[i].l, h[i].k).K;
-      const int B = gtc_bucket(K);
-      if (gtc_chunk_tuned(ax, K) || std::find(seen.begin(), seen.end(), B) != seen.end()) continue;
+      const GtcShape si = geo_shape(g, h[i].m, h[i].n, h[i].l, h[i].k);
+      const int K = si.K, M = si.M;
+      const int B = gtc_bucket(K) + 32 * (M <= 128 ? 1 : 0);
+      if (gtc_chunk_tuned(ax, K, M) || std::find(seen.begin(), seen.end(), B) != seen.end())
+        continue;
       seen.push_back(B);
       int kbmax = 1;
       for (int j = 0; j < count; ++j) {
         sh[j] = geo_shape(g, h[j].m, h[j].n, h[j].l, h[j].k);
-        if (gtc_bucket(sh[j].K) != B) sh[j].M = 0;
+        if (gtc_bucket(sh[j].K) + 32 * (sh[j].M <= 128 ? 1 : 0) != B) sh[j].M = 0;
         else kbmax = std::max(kbmax, (sh[j].K + kGtcBlockK - 1) / kGtcBlockK);
       }
       int best = kGtcDefaultChunk;
       float best_ms = 1e30f;
       bool whole_done = false;
-      for (int chunk : {16, 32, 64, 128, 256}) {
+      for (int chunk : {4, 8, 16, 32, 64, 128, 256}) {
         if (chunk >= kbmax) {
           if (whole_done) continue;   // every candidate from here on splits nothing
           whole_done = true;
@@ -794,7 +872,7 @@ int autotune_body(rsvd_plan_t P, int count, const Ctx<float>* d, BatchTc& S, cud
           best = chunk;
         }
       }
-      gtc_set_chunk(ax, K, best);
+      gtc_set_chunk(ax, K, M, best);
     }
   }
   return RSVD_OK;
@@ -814,6 +892,7 @@ int batch_autotune(rsvd_plan_t P, int count, const rsvd_problem_t* pr) {
   BatchTc* S = tc_state(P);
   if (!S) return RSVD_ERR_CUDA;
   S->sig.clear();   // the schedule region is reused by the trial runs
+  S->gsig.clear();
   cudaEvent_t e0, e1;
   RSVD_CK(cudaEventCreate(&e0));
   if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -861,11 +940,27 @@ int grouped_gemm_f32(rsvd_plan_t P, int count, const rsvd_gemm_t* gm, int trans)
   }
   BatchTc* S = tc_state(P);
   if (!S) return RSVD_ERR_CUDA;
-  S->sig.clear();   // the schedule region is overwritten
   const int g = trans ? 1 : 0;
-  tc_build(P, sh.data(), count, !trans, S->s[g]);
   int rc;
-  if ((rc = tc_upload(P, *S, g, g + 1))) return rc;
+  // the schedule depends only on the shapes: kept across calls with the same ones
+  std::vector<int64_t> sig;
+  sig.reserve(3 * (size_t)count + 3);
+  sig.push_back(trans);
+  sig.push_back(count);
+  sig.push_back(gtc_generation());
+  sig.push_back(P->batch_sms);
+  for (const GtcShape& x : sh) {
+    sig.push_back(x.M);
+    sig.push_back(x.K);
+    sig.push_back(x.N);
+  }
+  if (sig != S->gsig) {
+    S->sig.clear();   // the schedule region is overwritten
+    S->gsig.clear();
+    tc_build(P, sh.data(), count, !trans, S->s[g]);
+    if ((rc = tc_upload(P, *S, g, g + 1))) return rc;
+    S->gsig.swap(sig);
+  }
   GtcGemm* dtab = reinterpret_cast<GtcGemm*>(P->ws + L.gtab);
   RSVD_CK(cudaMemcpyAsync(dtab, tab.data(), (size_t)count * sizeof(GtcGemm),
                           cudaMemcpyHostToDevice, P->stream));

@@ -96,6 +96,8 @@ int rsvd_plan_create(rsvd_plan_t* plan, int64_t m_max, int64_t n_max, int l_max,
   P->h_ctx = nullptr;
   P->ctx_event = nullptr;
   P->batch_engine = kBatchSimt;
+  P->batch_graphs = 0;
+  P->batch_sms = 0;
   P->batch_tc = nullptr;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -145,6 +147,8 @@ int rsvd_batch_plan_create(rsvd_plan_t* plan, int max_count, int64_t rows_total,
   P->ctx_event = nullptr;
   P->h_status = nullptr;
   P->batch_engine = a_dtype == RSVD_F32 ? kBatchTensor : kBatchSimt;
+  P->batch_graphs = 0;
+  P->batch_sms = 0;
   P->batch_tc = nullptr;
   P->batch_lay = new (std::nothrow) BatchLayout(
       make_batch_layout(max_count, rows_total, cols_total, l_max, a_dtype));
@@ -190,6 +194,22 @@ int rsvd_batch_set_engine(rsvd_plan_t plan, int engine) {
   if (engine != RSVD_BATCH_ENGINE_SIMT && engine != RSVD_BATCH_ENGINE_TENSOR) return -2;
   if (engine == RSVD_BATCH_ENGINE_TENSOR && plan->dtype != RSVD_F32) return RSVD_ERR_UNSUPPORTED;
   plan->batch_engine = engine == RSVD_BATCH_ENGINE_TENSOR ? kBatchTensor : kBatchSimt;
+  return RSVD_OK;
+}
+
+int rsvd_batch_set_graphs(rsvd_plan_t plan, int on) {
+  if (!plan || !plan->batched) return -1;
+  if (on && (plan->dtype != RSVD_F32 || plan->batch_engine != kBatchTensor))
+    return RSVD_ERR_UNSUPPORTED;
+  if (on && plan->stream == nullptr) return -2;
+  plan->batch_graphs = on ? 1 : 0;
+  return RSVD_OK;
+}
+
+int rsvd_batch_set_sm_limit(rsvd_plan_t plan, int sms) {
+  if (!plan || !plan->batched) return -1;
+  if (sms < 0) return -2;
+  plan->batch_sms = sms;
   return RSVD_OK;
 }
 

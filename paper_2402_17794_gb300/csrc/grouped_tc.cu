@@ -626,7 +626,7 @@ __global__ void gtc_split_kernel(const GtcGemm* __restrict__ gemm) {
 }
 
 std::mutex g_tune_mu;
-int g_chunk[2][32];   // [form][K bucket] -> contraction blocks per unit (0: not tuned)
+int g_chunk[2][2][32];   // [form][one row tile][K bucket] -> blocks per unit (0: not tuned)
 int g_tile[32];       // [N bucket] -> column tile limit (0: not tuned)
 int g_generation = 0;
 
@@ -638,18 +638,18 @@ int gtc_stages(int t) {
   return std::min(4, cap / stage_bytes_of(t));
 }
 
-bool gtc_chunk_tuned(bool ax, int K) {
+bool gtc_chunk_tuned(bool ax, int K, int M) {
   std::lock_guard<std::mutex> g(g_tune_mu);
-  return g_chunk[ax ? 1 : 0][gtc_bucket(K)] != 0;
+  return g_chunk[ax ? 1 : 0][M <= BM ? 1 : 0][gtc_bucket(K)] != 0;
 }
-int gtc_chunk(bool ax, int K) {
+int gtc_chunk(bool ax, int K, int M) {
   std::lock_guard<std::mutex> g(g_tune_mu);
-  const int c = g_chunk[ax ? 1 : 0][gtc_bucket(K)];
+  const int c = g_chunk[ax ? 1 : 0][M <= BM ? 1 : 0][gtc_bucket(K)];
   return c > 0 ? c : kGtcDefaultChunk;
 }
-void gtc_set_chunk(bool ax, int K, int chunk_kb) {
+void gtc_set_chunk(bool ax, int K, int M, int chunk_kb) {
   std::lock_guard<std::mutex> g(g_tune_mu);
-  int& c = g_chunk[ax ? 1 : 0][gtc_bucket(K)];
+  int& c = g_chunk[ax ? 1 : 0][M <= BM ? 1 : 0][gtc_bucket(K)];
   if (c == 0 && chunk_kb > 0) {
     c = chunk_kb;
     ++g_generation;
@@ -698,7 +698,7 @@ void gtc_schedule(const GtcShape* shapes, int count, bool ax, int num_sms, GtcSc
     const int t = caps ? gtc_tile_rule(s.N, caps->cap[gtc_bucket(s.N)]) : gtc_tile(s.N);
     out.tmax = std::max(out.tmax, t);
     const int kbs = std::max(1, (s.K + BK - 1) / BK);
-    const int chunk = force_chunk > 0 ? force_chunk : gtc_chunk(ax, s.K);
+    const int chunk = force_chunk > 0 ? force_chunk : gtc_chunk(ax, s.K, s.M);
     const int nchunk = (kbs + chunk - 1) / chunk;
     for (int r0 = 0; r0 < s.M; r0 += BM)
       for (int c0 = 0; c0 < s.N; c0 += t) {

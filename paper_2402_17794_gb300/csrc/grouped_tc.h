@@ -122,14 +122,14 @@ int gtc_stages(int t);
 // A product's column tile: N split into ceil(N / cap) tiles of equal width
 // rounded up to 16, cap = the tuned tile limit for N's bucket (default 80).
 int gtc_tile(int N);
-// Contraction blocks per unit for a product of this form and K: the tuned
-// value for K's bucket, else kGtcDefaultChunk.
-int gtc_chunk(bool ax, int K);
+// Contraction blocks per unit for a product of this form, K and M: the tuned
+// value for (form, K's bucket, M <= 128 or not), else kGtcDefaultChunk.
+int gtc_chunk(bool ax, int K, int M);
 // Process-wide tuning table: the first value set for a bucket stays, so a
 // product's schedule (and its result) is the same in every batch of the
 // process.
-bool gtc_chunk_tuned(bool ax, int K);
-void gtc_set_chunk(bool ax, int K, int chunk_kb);
+bool gtc_chunk_tuned(bool ax, int K, int M);
+void gtc_set_chunk(bool ax, int K, int M, int chunk_kb);
 bool gtc_tile_tuned(int N);
 void gtc_set_tile_cap(int N, int cap);
 int gtc_generation();   // counts the changes of the table (schedules built before are stale)

@@ -85,6 +85,8 @@ struct rsvd_plan_s {
   void* h_ctx;                    // pinned staging for the context table
   cudaEvent_t ctx_event;          // marks the table copy of the last batched solve
   int batch_engine;               // kBatchSimt or kBatchTensor (FP32 batch plans)
+  int batch_graphs;               // rsvd_batch_set_graphs: grouped solves as CUDA graphs
+  int batch_sms;                  // rsvd_batch_set_sm_limit: SMs of a grouped tensor launch (0: all)
   void* batch_tc;                 // tensor-engine host state (schedules), owned
   long long wait_cycles;          // rsvd_plan_set_wait_limit (0: the default bound)
   int f64tc;                      // RSVD_MODE_F64_TENSOR (mode holds RSVD_MODE_PLAIN)

@@ -241,6 +241,14 @@ def rsvd_batch_set_engine(plan, engine) -> int:
     return _lib.load().rsvd_batch_set_engine(plan, engine)
 
 
+def rsvd_batch_set_graphs(plan, on) -> int:
+    return _lib.load().rsvd_batch_set_graphs(plan, int(on))
+
+
+def rsvd_batch_set_sm_limit(plan, sms) -> int:
+    return _lib.load().rsvd_batch_set_sm_limit(plan, int(sms))
+
+
 def rsvd_batch_autotune(plan, problems) -> int:
     arr = problems if isinstance(problems, ctypes.Array) else (_lib.RsvdProblem * len(problems))(*problems)
     return _lib.load().rsvd_batch_autotune(plan, len(arr), arr)
@@ -312,6 +320,14 @@ class BatchPlan:
 
     def set_engine(self, engine):
         _check(rsvd_batch_set_engine(self.handle, engine), "rsvd_batch_set_engine")
+
+    def set_sm_limit(self, sms):
+        """SMs of the tensor engine's persistent launches (0: all)."""
+        _check(rsvd_batch_set_sm_limit(self.handle, sms), "rsvd_batch_set_sm_limit")
+
+    def set_graphs(self, on=True):
+        """Grouped FP32 solves as CUDA graphs (needs a non-default stream)."""
+        _check(rsvd_batch_set_graphs(self.handle, on), "rsvd_batch_set_graphs")
 
     def autotune(self, items, outs=None):
         """Tunes the tensor engine's schedules on these problems (FP32 plans)."""

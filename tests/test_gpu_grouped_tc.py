@@ -214,3 +214,43 @@ def test_grouped_product_has_no_accumulation_bias(trans):
     e = (out - ref) / ref
     assert abs(e.mean()) <= 24 * U32, e.mean() / U32
     assert np.abs(e).max() <= 96 * U32, np.abs(e).max() / U32
+
+
+def test_graph_replays_match_direct_solves():
+    """rsvd_batch_set_graphs: the first solve captures the grouped solve as a
+    CUDA graph, later solves of the same shapes replay it with new operands
+    and seeds; every result equals the same solve launched directly."""
+    from paper_2402_17794_gb300 import synthetic as syn
+    rng = np.random.default_rng(70)
+    shapes = [(int(rng.integers(300, 3000)), int(rng.integers(300, 1500)), int(rng.integers(10, 60)))
+              for _ in range(8)]
+
+    def batch(seed0):
+        return [(R.from_numpy_f(syn.lowrank_matrix(m, n, syn.spectrum("exp", min(m, n, 300), r=25.0),
+                                                   seed=seed0 + i), dtype=torch.float32),
+                 m, n, k, 10, 1, seed0 + 7 * i) for i, (m, n, k) in enumerate(shapes)]
+
+    a, b = batch(100), batch(200)
+    rows = sum(s[0] for s in shapes)
+    cols = sum(s[1] for s in shapes)
+    stream = torch.cuda.Stream()
+    direct = R.BatchPlan(len(shapes), rows, cols, 74, R.F32, stream=stream)
+    out = direct.solve(a)
+    stream.synchronize()
+    ref_a = [tuple(t.clone() for t in o) for o in out]
+    out = direct.solve(b)
+    stream.synchronize()
+    ref_b = [tuple(t.clone() for t in o) for o in out]
+    graph = R.BatchPlan(len(shapes), rows, cols, 74, R.F32, stream=stream)
+    graph.set_graphs(True)
+    for items, ref in ((a, ref_a), (b, ref_b), (a, ref_a)):
+        out = graph.solve(items)
+        stream.synchronize()
+        assert graph.status() == [0] * len(shapes)
+        for o, r in zip(out, ref):
+            for x, y in zip(o, r):
+                assert torch.equal(x, y)
+    p64 = R.BatchPlan(2, 100, 100, 16, R.F64, stream=stream)
+    assert R.rsvd_batch_set_graphs(p64.handle, 1) == 7
+    nostream = R.BatchPlan(2, 100, 100, 16, R.F32)
+    assert R.rsvd_batch_set_graphs(nostream.handle, 1) == -2
