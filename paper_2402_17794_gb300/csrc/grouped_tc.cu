@@ -23,8 +23,8 @@
 //    once the stores (after a proxy fence) and the copy have landed;
 //  * warp 8: one lane issues tcgen05.mma (kind::f16, BF16 in, FP32 in TMEM)
 //    and tcgen05.commit: five MMAs per 16-deep step, the leading products
-//    (a1 x1, a2 x1, a3 x1) into D1, the rest into D2 | D3 (a unit of one
-//    group, a short contraction, puts all six into D1); D1 starts from
+//    (a1 x1, a2 x1, a3 x1) into D1, the rest into D2 | D3, alternating, so
+//    no MMA waits on the one before it; D1 starts from
 //    zero every group of DRAIN (2) contraction blocks, two buffers
 //    alternating, so the drain of one group overlaps the next group's MMAs;
 //  * warps 9-12 drain each group's D1 (tcgen05.ld) into per-row running sums
@@ -386,7 +386,6 @@ __global__ void __launch_bounds__(THREADS, 1) gtc_kernel(const GtcArgs args) {
           tc_fence_after();
         }
         const uint32_t d23 = tmem_base + (uint32_t)(2 * tmax + c * 2 * tmax);
-        const bool single = un.kb1 - un.kb0 <= DRAIN;
         for (int kg = un.kb0; kg < un.kb1 && ok; kg += DRAIN, ++g) {
           const int b = g & 1;
           if (g >= 2) {
@@ -416,22 +415,12 @@ __global__ void __launch_bounds__(THREADS, 1) gtc_kernel(const GtcArgs args) {
               const uint64_t a3 = a2 + (A_SLICE_BYTES >> 4);
               const uint64_t x1 = bd + kk * b_kstep;
               const uint64_t x2 = x1 + (uint64_t)((t * 128) >> 4);   // rows t .. 3t-1: x2, x3
-              if (single) {
-                // a unit of one group: all six products into D1
-                const uint64_t x3 = x2 + (uint64_t)((t * 128) >> 4);
-                umma_bf16(d1, a1, x1, id1, (kb > kg || kk > 0) ? 1u : 0u);
-                umma_bf16(d1, a1, x2, id1, 1u);
-                umma_bf16(d1, a1, x3, id1, 1u);
-                umma_bf16(d1, a2, x1, id1, 1u);
-                umma_bf16(d1, a2, x2, id1, 1u);
-                umma_bf16(d1, a3, x1, id1, 1u);
-              } else {
-                umma_bf16(d1, a1, x1, id1, (kb > kg || kk > 0) ? 1u : 0u);
-                umma_bf16(d23, a1, x2, id2, (kb > un.kb0 || kk > 0) ? 1u : 0u);
-                umma_bf16(d1, a2, x1, id1, 1u);
-                umma_bf16(d23, a2, x2, id1, 1u);   // N = t: a2 x2 into D2 only
-                umma_bf16(d1, a3, x1, id1, 1u);
-              }
+              // consecutive MMAs alternate between D1 and D2 | D3
+              umma_bf16(d1, a1, x1, id1, (kb > kg || kk > 0) ? 1u : 0u);
+              umma_bf16(d23, a1, x2, id2, (kb > un.kb0 || kk > 0) ? 1u : 0u);
+              umma_bf16(d1, a2, x1, id1, 1u);
+              umma_bf16(d23, a2, x2, id1, 1u);   // N = t: a2 x2 into D2 only
+              umma_bf16(d1, a3, x1, id1, 1u);
             }
             umma_commit(&empty[s]);       // stage reusable once these MMAs finish
             if (++s == S) {
@@ -459,8 +448,7 @@ __global__ void __launch_bounds__(THREADS, 1) gtc_kernel(const GtcArgs args) {
     // Thread r owns tile row r.  Each group's D1 goes into the row's running
     // sums (shared memory, column-major 128 x t) with round-to-nearest FP32
     // adds; after the unit's last group the result is
-    // (sums + D1) + (D2 + D3), stored to C or to the unit's partial slot.  A
-    // unit of a single group keeps every product in D1.
+    // (sums + D1) + (D2 + D3), stored to C or to the unit's partial slot.
     const int quad = warp & 3;
     const uint32_t lane_base = tmem_base + ((uint32_t)(quad * 32) << 16);
     const int r = quad * 32 + lane;
@@ -505,30 +493,6 @@ __global__ void __launch_bounds__(THREADS, 1) gtc_kernel(const GtcArgs args) {
                 sp[j * BM] = first ? __uint_as_float(v[h][j]) : sp[j * BM] + __uint_as_float(v[h][j]);
             }
           }
-        } else if (first) {
-          // a unit of one group: D1 holds all six products
-#pragma unroll
-          for (int ch = 0; ch < kGtcMaxTile / 16; ch += 2) {
-            if (ch * 16 >= t) continue;
-            const bool two = (ch + 1) * 16 < t;
-            uint32_t v[2][16];
-            tmem_ld16(d1 + (uint32_t)(ch * 16), v[0]);
-            if (two) tmem_ld16(d1 + (uint32_t)(ch * 16 + 16), v[1]);
-            tmem_wait_ld();
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              if (h == 1 && !two) continue;
-#pragma unroll
-              for (int j = 0; j < 16; ++j) {
-                const float tot = __uint_as_float(v[h][j]);
-                const int c = (ch + h) * 16 + j;
-                if (un.slot >= 0)
-                  args.part[(size_t)un.slot * BM * tmax + r + (size_t)c * BM] = tot;
-                else if (row < G.M && c < cols)
-                  G.C[row + (int64_t)(un.col0 + c) * G.ldc] = tot;
-              }
-            }
-          }
         } else {
 #pragma unroll
           for (int ch = 0; ch < kGtcMaxTile / 16; ++ch) {
@@ -541,7 +505,7 @@ __global__ void __launch_bounds__(THREADS, 1) gtc_kernel(const GtcArgs args) {
             const float* sp = sums + r + (size_t)ch * 16 * BM;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-              const float lead = sp[j * BM] + __uint_as_float(v1[j]);
+              const float lead = first ? __uint_as_float(v1[j]) : sp[j * BM] + __uint_as_float(v1[j]);
               const float tot = lead + (__uint_as_float(w2[j]) + __uint_as_float(w3[j]));
               const int c = ch * 16 + j;
               if (un.slot >= 0)
