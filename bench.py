@@ -718,7 +718,7 @@ def run_batched(args, stream):
                                    "512 problems, with its operand split)",
                          "achieved": round(pass_gbps, 1), "peak": peaks["hbm_gbs"],
                          "unit": "GB/s", "frac": round(pass_gbps / peaks["hbm_gbs"], 4),
-                         "traffic": None, "peak_source": psrc,
+                         "traffic": _traffic_from_profile("batched-f32", "ax"), "peak_source": psrc,
                          "algorithmic_bytes_per_launch": a_bytes,
                          "ms_per_launch": round(t_pass * 1e3, 3),
                          "timing": "CUDA events around 5 grouped passes on the plan's stream"},

@@ -144,14 +144,19 @@ __device__ __forceinline__ void fetch_unit(const GtcArgs& a, int u, XUnit& p) {
 }
 
 // A block is 128 tile rows x 64 contraction entries, taken as 4096 pairs of
-// neighbours in the swizzled slice layout (16 per producer thread, index q):
+// neighbours in the swizzled slice layout, PPT per producer thread (index q):
 //   AX  (MN-major: neighbours are rows i, i + 1 of one column kk):
-//       i = 2 (pt % 64), kk = pt / 64 + 4 q -- a warp covers 64 rows of a
+//       i = 2 (pt % 64), kk = pt / 64 + SK q -- a warp covers 64 rows of a
 //       column, 256 contiguous bytes of A;
 //   ATX (K-major: neighbours are kk, kk + 1 of one tile row i):
-//       kk = 2 (pt % 32), i = pt / 32 + 8 q -- a warp covers 64 entries of one
-//       of A's columns.
-// Loads walk a per-thread pointer by a fixed stride (4 lda or 8 lda).
+//       kk = 2 (pt % 32), i = pt / 32 + SI q -- a warp covers 64 entries of
+//       one of A's columns.
+// Loads walk a per-thread pointer by a fixed stride (SK lda or SI lda).
+constexpr int PPT = EPT / 2;                 // pairs per producer thread
+constexpr int SK = PROD_THREADS / 64;        // AX: contraction step between a thread's pairs
+constexpr int SI = PROD_THREADS / 32;        // ATX: row step between a thread's pairs
+static_assert(SI % 8 == 0, "ATX pairs of a thread share their swizzle phase");
+
 template <bool AX>
 __device__ __forceinline__ void load_block(const LUnit& U, int kb, int pt, float (&r)[EPT]) {
   const int k0 = kb * BK;
@@ -163,19 +168,19 @@ __device__ __forceinline__ void load_block(const LUnit& U, int kb, int pt, float
     const int row = U.row0 + 2 * (pt & 63), k = k0 + (pt >> 6);
     ok0 = row < U.M;
     ok1 = row + 1 < U.M;
-    qmax = k < U.K ? (U.K - k + 3) / 4 : 0;
+    qmax = k < U.K ? (U.K - k + SK - 1) / SK : 0;
     p = U.A + row + (int64_t)k * U.lda;
-    stride = 4 * U.lda;
+    stride = SK * U.lda;
   } else {
     const int k = k0 + 2 * (pt & 31), row = U.row0 + (pt >> 5);
     ok0 = k < U.K;
     ok1 = k + 1 < U.K;
-    qmax = row < U.M ? (U.M - row + 7) / 8 : 0;
+    qmax = row < U.M ? (U.M - row + SI - 1) / SI : 0;
     p = U.A + k + (int64_t)row * U.lda;
-    stride = 8 * U.lda;
+    stride = SI * U.lda;
   }
 #pragma unroll
-  for (int q = 0; q < EPT / 2; ++q) {
+  for (int q = 0; q < PPT; ++q) {
     const bool in = q < qmax;
     r[2 * q] = (in && ok0) ? __ldg(p) : 0.f;
     r[2 * q + 1] = (in && ok1) ? __ldg(p + 1) : 0.f;
@@ -185,29 +190,33 @@ __device__ __forceinline__ void load_block(const LUnit& U, int kb, int pt, float
 
 template <bool AX>
 __device__ __forceinline__ void store_block(uint32_t a_s, int pt, const float (&r)[EPT]) {
-  // byte offset of pair q: base + q * step, plus (AX) a swizzle term that
-  // depends on q's parity
-  uint32_t base, step, sw0 = 0, sw1 = 0;
   if (AX) {
-    const int i2 = pt & 63, k4 = pt >> 6;
+    const int i2 = pt & 63, k0t = pt >> 6;
     const int m = (2 * i2) & 63, c = m >> 3;
-    base = (uint32_t)((i2 >> 5) * 8192 + k4 * 128 + (m & 7) * 2);
-    step = 512;
-    sw0 = (uint32_t)((c ^ (k4 & 7)) << 4);
-    sw1 = (uint32_t)((c ^ ((k4 + 4) & 7)) << 4);
-  } else {
-    const int kk2 = pt & 31, i8 = pt >> 5;
-    base = (uint32_t)(i8 * 128 + (((kk2 >> 2) ^ i8) << 4) + ((2 * kk2) & 7) * 2);
-    step = 1024;
-  }
+    const uint32_t base = (uint32_t)((i2 >> 5) * 8192 + (m & 7) * 2);
 #pragma unroll
-  for (int q = 0; q < EPT / 2; ++q) {
-    uint32_t s1, s2, s3;
-    split3x2(r[2 * q], r[2 * q + 1], s1, s2, s3);
-    const uint32_t o = a_s + base + (uint32_t)q * step + (AX ? ((q & 1) ? sw1 : sw0) : 0u);
-    st_shared_u32(o, s1);
-    st_shared_u32(o + A_SLICE_BYTES, s2);
-    st_shared_u32(o + 2 * A_SLICE_BYTES, s3);
+    for (int q = 0; q < PPT; ++q) {
+      uint32_t s1, s2, s3;
+      split3x2(r[2 * q], r[2 * q + 1], s1, s2, s3);
+      const int kk = k0t + SK * q;
+      const uint32_t o = a_s + base + (uint32_t)(kk * 128 + ((c ^ (kk & 7)) << 4));
+      st_shared_u32(o, s1);
+      st_shared_u32(o + A_SLICE_BYTES, s2);
+      st_shared_u32(o + 2 * A_SLICE_BYTES, s3);
+    }
+  } else {
+    const int kk2 = pt & 31, i0t = pt >> 5;
+    const uint32_t base = (uint32_t)((i0t >> 3) * 1024 + (i0t & 7) * 128 +
+                                     (((kk2 >> 2) ^ (i0t & 7)) << 4) + ((2 * kk2) & 7) * 2);
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+      uint32_t s1, s2, s3;
+      split3x2(r[2 * q], r[2 * q + 1], s1, s2, s3);
+      const uint32_t o = a_s + base + (uint32_t)q * (SI / 8) * 1024;
+      st_shared_u32(o, s1);
+      st_shared_u32(o + A_SLICE_BYTES, s2);
+      st_shared_u32(o + 2 * A_SLICE_BYTES, s3);
+    }
   }
 }
 
@@ -475,38 +484,36 @@ __global__ void __launch_bounds__(THREADS, 1) gtc_kernel(const GtcArgs args) {
         const bool first = kg == un.kb0, last = kg + DRAIN >= un.kb1;
         const uint32_t d1 = lane_base + (uint32_t)(b * tmax);
         if (!last) {
-          // the group's D1, 32 columns per round trip, into the sums
+          // the group's D1, 16 columns per round trip, into the sums
 #pragma unroll
-          for (int ch = 0; ch < kGtcMaxTile / 16; ch += 2) {
+          for (int ch = 0; ch < kGtcMaxTile / 16; ++ch) {
             if (ch * 16 >= t) continue;
-            const bool two = (ch + 1) * 16 < t;
-            uint32_t v[2][16];
-            tmem_ld16(d1 + (uint32_t)(ch * 16), v[0]);
-            if (two) tmem_ld16(d1 + (uint32_t)(ch * 16 + 16), v[1]);
+            uint32_t v[16];
+            tmem_ld16(d1 + (uint32_t)(ch * 16), v);
             tmem_wait_ld();
+            float* sp = sums + r + (size_t)ch * 16 * BM;
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              if (h == 1 && !two) continue;
-              float* sp = sums + r + (size_t)(ch + h) * 16 * BM;
-#pragma unroll
-              for (int j = 0; j < 16; ++j)
-                sp[j * BM] = first ? __uint_as_float(v[h][j]) : sp[j * BM] + __uint_as_float(v[h][j]);
-            }
+            for (int j = 0; j < 16; ++j)
+              sp[j * BM] = first ? __uint_as_float(v[j]) : sp[j * BM] + __uint_as_float(v[j]);
           }
         } else {
 #pragma unroll
           for (int ch = 0; ch < kGtcMaxTile / 16; ++ch) {
             if (ch * 16 >= t) continue;
-            uint32_t v1[16], w2[16], w3[16];
-            tmem_ld16(d1 + (uint32_t)(ch * 16), v1);
-            tmem_ld16(d23 + (uint32_t)(ch * 16), w2);
-            tmem_ld16(d23 + (uint32_t)(t + ch * 16), w3);
+            uint32_t v[16], w[16];
+            tmem_ld16(d23 + (uint32_t)(ch * 16), v);
+            tmem_ld16(d23 + (uint32_t)(t + ch * 16), w);
+            tmem_wait_ld();
+            float tail[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) tail[j] = __uint_as_float(v[j]) + __uint_as_float(w[j]);
+            tmem_ld16(d1 + (uint32_t)(ch * 16), v);
             tmem_wait_ld();
             const float* sp = sums + r + (size_t)ch * 16 * BM;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-              const float lead = first ? __uint_as_float(v1[j]) : sp[j * BM] + __uint_as_float(v1[j]);
-              const float tot = lead + (__uint_as_float(w2[j]) + __uint_as_float(w3[j]));
+              const float lead = first ? __uint_as_float(v[j]) : sp[j * BM] + __uint_as_float(v[j]);
+              const float tot = lead + tail[j];
               const int c = ch * 16 + j;
               if (un.slot >= 0)
                 args.part[(size_t)un.slot * BM * tmax + r + (size_t)c * BM] = tot;
