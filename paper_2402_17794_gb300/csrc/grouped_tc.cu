@@ -560,39 +560,42 @@ __global__ void gtc_fix_kernel(const GtcGemm* __restrict__ gemm, const GtcFix* _
   }
 }
 
-// Every product's X as its MMA images (see GtcGemm).  Thread e writes the
-// 16-byte chunk e of the image area (8 BF16 entries, in address order): row
-// e / 8 of the area, physical chunk e % 8, which holds contraction entries
-// 8 ((e % 8) ^ (row % 8)) .. + 7 of slice j / t of X's column for row j.
+// Every product's X as its MMA images (see GtcGemm).  Thread e takes 8
+// consecutive contraction entries (logical chunk lc) of one column of one
+// image, splits each entry once and writes the chunk of all three slices:
+// row j = s t + cc of the image, physical chunk lc ^ (j % 8).
 __global__ void gtc_split_kernel(const GtcGemm* __restrict__ gemm) {
   const GtcGemm& G = gemm[blockIdx.y];
   if (G.M <= 0) return;
-  const int t3 = 3 * G.t, nkb = G.kpad / BK;
-  const int rows = (int)(3 * (int64_t)G.kpad * G.ncols / 64);   // 128-byte rows of the area
-  const int chunks = rows * 8;
+  const int t = G.t, nkb = G.kpad / BK;
+  const int nimg = (G.ncols / t) * nkb;
+  const int tasks = nimg * t * 8;
   uint4* out = reinterpret_cast<uint4*>(G.xs);
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < chunks; e += gridDim.x * blockDim.x) {
-    const int row = e >> 3, pchunk = e & 7;
-    const int img = row / t3, j = row - img * t3;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < tasks; e += gridDim.x * blockDim.x) {
+    const int lc = e & 7, rest = e >> 3;
+    const int img = rest / t, cc = rest - img * t;
     const int ct = img / nkb, kb = img - ct * nkb;
-    const int sl = j / G.t, c = ct * G.t + (j - sl * G.t);
-    const int k0 = kb * BK + ((pchunk ^ (j & 7)) << 3);
-    uint32_t w[4];
+    const int c = ct * t + cc, k0 = kb * BK + lc * 8;
+    uint32_t w[3][4];
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
-      uint16_t o[2];
+      uint16_t sl[2][3];
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         const int k = k0 + 2 * h + q;
         float v = 0.f;
         if (k < G.K && c < G.N && (!G.x_upper || k <= c)) v = G.X[k + (int64_t)c * G.ldx];
-        uint16_t s1, s2, s3;
-        split3(v, s1, s2, s3);
-        o[q] = sl == 0 ? s1 : (sl == 1 ? s2 : s3);
+        split3(v, sl[q][0], sl[q][1], sl[q][2]);
       }
-      w[h] = (uint32_t)o[0] | ((uint32_t)o[1] << 16);
+#pragma unroll
+      for (int z = 0; z < 3; ++z) w[z][h] = (uint32_t)sl[0][z] | ((uint32_t)sl[1][z] << 16);
     }
-    out[e] = make_uint4(w[0], w[1], w[2], w[3]);
+#pragma unroll
+    for (int z = 0; z < 3; ++z) {
+      const int j = z * t + cc;
+      const int64_t row = (int64_t)img * 3 * t + j;
+      out[row * 8 + (lc ^ (j & 7))] = make_uint4(w[z][0], w[z][1], w[z][2], w[z][3]);
+    }
   }
 }
 
