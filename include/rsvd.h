@@ -634,6 +634,26 @@ typedef struct rsvd_gemm_s {
 } rsvd_gemm_t;
 int rsvd_grouped_gemm_f32(rsvd_plan_t plan, int count, const rsvd_gemm_t* gemms, int trans);
 
+/*
+ * rsvd_grouped_schedule: the tensor engine's work schedule for `count`
+ * products of shapes shapes[3i .. 3i+2] = (M, K, N) (M = 0: skipped) in the
+ * given form (trans as in rsvd_grouped_gemm_f32) on `num_sms` SMs, with the
+ * process's current tuning table.  Host computation only (no device work):
+ * a planning query, also usable without a GPU.
+ *   units: NULL, or room for max_units entries of 7 ints each:
+ *     (product, row0, col0, kb0, kb1, slot, t) -- output rows row0 ..
+ *     row0 + 127 and columns col0 .. col0 + t - 1 over contraction blocks
+ *     kb0 .. kb1 - 1 of 64; slot >= 0 marks a split tile's partial slot.
+ *   cta_off: NULL, or room for num_sms + 1 ints: CTA c takes units
+ *     cta_off[c] .. cta_off[c+1] - 1 (in the order listed).
+ *   info: 4 ints: unit count, grid (CTAs), partial slots, largest t.
+ * Errors: -1 count < 1; -2 shapes or info NULL; -3 num_sms < 1;
+ * -(100 + i) shape i invalid; RSVD_ERR_WORKSPACE when units or cta_off
+ * are too small (info is still written).
+ */
+int rsvd_grouped_schedule(int count, const int64_t* shapes, int trans, int num_sms,
+                          int* units, int max_units, int* cta_off, int* info);
+
 /* ---------------------------------------------------------------------- */
 /* Allocation-free entry point                                             */
 /* ---------------------------------------------------------------------- */

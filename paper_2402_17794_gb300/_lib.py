@@ -87,6 +87,9 @@ SIGNATURES = {
     "rsvd_batch_set_sm_limit": (c_int, [c_void_p, c_int]),
     "rsvd_batch_autotune": (c_int, [c_void_p, c_int, ctypes.POINTER(RsvdProblem)]),
     "rsvd_grouped_gemm_f32": (c_int, [c_void_p, c_int, ctypes.POINTER(RsvdGemm), c_int]),
+    "rsvd_grouped_schedule": (c_int, [c_int, ctypes.POINTER(c_int64), c_int, c_int,
+                                      ctypes.POINTER(c_int), c_int, ctypes.POINTER(c_int),
+                                      ctypes.POINTER(c_int)]),
     "rsvd_apply_a_f64_static": (c_int, [c_void_p, c_int64, c_int64, c_int64, c_void_p, c_int64,
                                         c_int, c_void_p, c_int64, c_void_p]),
 }

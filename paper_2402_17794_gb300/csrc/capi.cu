@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "batched.h"
+#include "grouped_tc.h"
 #include "pipeline.h"
 #include "umma.h"
 
@@ -249,6 +250,39 @@ int rsvd_grouped_gemm_f32(rsvd_plan_t plan, int count, const rsvd_gemm_t* gemms,
     if (bad) return -(100 + i);
   }
   return grouped_gemm_f32(plan, count, gemms, trans);
+}
+
+int rsvd_grouped_schedule(int count, const int64_t* shapes, int trans, int num_sms, int* units,
+                          int max_units, int* cta_off, int* info) {
+  if (count < 1) return -1;
+  if (!shapes || !info) return -2;
+  if (num_sms < 1) return -3;
+  std::vector<GtcShape> sh(count);
+  for (int i = 0; i < count; ++i) {
+    const int64_t M = shapes[3 * i], K = shapes[3 * i + 1], N = shapes[3 * i + 2];
+    if (M < 0 || M > (1 << 30) || K < 1 || K > (1 << 30) || N < 1 || N > RSVD_L_MAX)
+      return -(100 + i);
+    sh[i] = {(int)M, (int)K, (int)N};
+  }
+  GtcSchedule sc;
+  gtc_schedule(sh.data(), count, !trans, num_sms, sc);
+  info[0] = (int)sc.units.size();
+  info[1] = sc.grid;
+  info[2] = sc.slots;
+  info[3] = sc.tmax;
+  if ((units && max_units < (int)sc.units.size())) return RSVD_ERR_WORKSPACE;
+  if (units)
+    for (size_t u = 0; u < sc.units.size(); ++u) {
+      const GtcUnit& x = sc.units[u];
+      const int v[7] = {x.prob, x.row0, x.col0, x.kb0, x.kb1, x.slot, x.t};
+      for (int j = 0; j < 7; ++j) units[7 * u + j] = v[j];
+    }
+  if (cta_off) {
+    if (num_sms < sc.grid) return RSVD_ERR_WORKSPACE;
+    for (int c = 0; c <= sc.grid; ++c) cta_off[c] = sc.cta_off[c];
+    for (int c = sc.grid + 1; c <= num_sms; ++c) cta_off[c] = sc.cta_off[sc.grid];
+  }
+  return RSVD_OK;
 }
 
 int rsvd_batch_status(rsvd_plan_t plan, int count, int* codes) {

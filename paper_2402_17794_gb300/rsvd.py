@@ -260,6 +260,23 @@ def rsvd_grouped_gemm_f32(plan, gemms, trans) -> int:
     return _lib.load().rsvd_grouped_gemm_f32(plan, len(arr), arr, int(trans))
 
 
+def rsvd_grouped_schedule(shapes, trans, num_sms):
+    """The tensor engine's work schedule for product shapes [(M, K, N)]:
+    (units as a list of (product, row0, col0, kb0, kb1, slot, t), cta_off,
+    info (units, grid, slots, largest t)).  Host computation only."""
+    lib = _lib.load()
+    flat = (ctypes.c_int64 * (3 * len(shapes)))(*[v for s in shapes for v in s])
+    info = (ctypes.c_int * 4)()
+    _check(lib.rsvd_grouped_schedule(len(shapes), flat, int(trans), num_sms, None, 0, None, info),
+           "rsvd_grouped_schedule")
+    units = (ctypes.c_int * (7 * max(1, info[0])))()
+    cta = (ctypes.c_int * (num_sms + 1))()
+    _check(lib.rsvd_grouped_schedule(len(shapes), flat, int(trans), num_sms, units, info[0], cta,
+                                     info), "rsvd_grouped_schedule")
+    u = [tuple(units[7 * i: 7 * i + 7]) for i in range(info[0])]
+    return u, list(cta)[: info[1] + 1], tuple(info)
+
+
 def rsvd_apply_a_f64_static(A, m, n, lda, X, ldx, l, Y, ldy, stream=None) -> int:
     return _lib.load().rsvd_apply_a_f64_static(_ptr(A), m, n, lda, _ptr(X), ldx, l, _ptr(Y), ldy,
                                                _stream_handle(stream))
