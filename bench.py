@@ -1225,7 +1225,18 @@ def run_srft(args, world, dA, w, gaussian_pass_ms):
     st = plan.status()
     if st != 0:
         raise RuntimeError(f"SRFT range finder failed: {R.rsvd_status_string(st)}")
-    del plan
+    # the whole SRFT solve: the range above, then Stage B on the complex
+    # basis (B = Q^H A, its SVD through the realified 2l x 2l Jacobi, the lift)
+    U = torch.empty(2 * k, m, dtype=torch.float64, device="cuda")
+    S = torch.empty(k, dtype=torch.float64, device="cuda")
+    VT = torch.empty(2 * n, k, dtype=torch.float64, device="cuda")
+    solve_ms = timed(lambda: R._check(R.rsvd_solve_srft(plan.handle, dA, m, n, m, k, p, seed, U, m,
+                                                        S, VT, k), "rsvd_solve_srft"),
+                     max(3, steps // 2))
+    st = plan.status()
+    if st != 0:
+        raise RuntimeError(f"SRFT solve failed: {R.rsvd_status_string(st)}")
+    del plan, U, S, VT
     # arithmetic of the FFT form per element of A: the phase (2), the 8 x 8
     # length-64 DFT (16 eight-point DFTs of 56 flops + 64 twiddles of 6,
     # per 64 elements: 20) and one complex multiply-add per sample per 64
@@ -1237,6 +1248,10 @@ def run_srft(args, world, dA, w, gaussian_pass_ms):
                         "on " + w["desc"].split(";")[0] + f"; l={l}",
             "value": round(steps * world / (rng_ms * steps / 1e3), 4), "unit": "ranges/s",
             "ms_per_range": round(rng_ms, 4), "ms_sketch": round(sk_ms, 4),
+            "solve": {"ms_per_solve": round(solve_ms, 4),
+                      "value": round(world * 1e3 / solve_ms, 4), "unit": "solves/s",
+                      "what": "rsvd_solve_srft: the range, then B = Q^H A, the SVD of the "
+                              "realified 2l x 2l factor and the lift (rank k)"},
             "ms_gaussian_sketch_same_l": round(gaussian_pass_ms, 4),
             "sketch_roofline": {"bound": "alu", "achieved": round(flops / (sk_ms / 1e3) / 1e12, 4),
                                 "peak": round(fp64_peak, 4), "unit": "TFLOP/s (FP64)",
