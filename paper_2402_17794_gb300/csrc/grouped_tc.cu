@@ -23,10 +23,10 @@
 //    once the stores (after a proxy fence) and the copy have landed;
 //  * warp 8: one lane issues tcgen05.mma (kind::f16, BF16 in, FP32 in TMEM)
 //    and tcgen05.commit: five MMAs per 16-deep step, the leading products
-//    (a1 x1, a2 x1, a3 x1) into D1, the rest into D2 | D3, alternating, so
-//    no MMA waits on the one before it; D1 starts from
-//    zero every group of DRAIN (2) contraction blocks, two buffers
-//    alternating, so the drain of one group overlaps the next group's MMAs;
+//    (a1 x1, a2 x1, a3 x1) into D1 and the rest into D2 | D3, issued
+//    alternately; D1 starts from zero every group of DRAIN (2) contraction
+//    blocks, two buffers alternating, so the drain of one group overlaps the
+//    next group's MMAs;
 //  * warps 9-12 drain each group's D1 (tcgen05.ld) into per-row running sums
 //    with round-to-nearest FP32 adds (the tensor cores' internal
 //    accumulation rounds toward zero; over a long contraction that would
