@@ -2,10 +2,11 @@
 // Algorithm 4, Section 3.3: every problem's passes over A, its Gram products
 // and its products with R^-1 and the small SVD's factors).
 //
-// FP32 accuracy from BF16 tensor cores.  Every FP32 value v splits exactly
-// into three BF16 values v = v1 + v2 + v3 (v1 = bf16(v), v2 = bf16(v - v1),
+// FP32 accuracy from BF16 tensor cores.  An FP32 value v splits into three
+// BF16 values v = v1 + v2 + v3 (v1 = bf16(v), v2 = bf16(v - v1),
 // v3 = v - v1 - v2; each remainder is exact in FP32 and the last one fits
-// eight bits).  A product a x is then the sum of the nine slice products, of
+// eight bits), exactly for |v| >= 2^-110 and to within 2^-134 below that
+// (BF16's subnormal step).  A product a x is then the sum of the nine slice products, of
 // which the six with i + j <= 4 are kept:
 //   a x ~ a1 (x1 + x2 + x3) + a2 (x1 + x2) + a3 x1,
 // dropping terms of relative size 2^-24 and below, with FP32 accumulation --
@@ -80,7 +81,8 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
-// v -> three BF16 slices (bits), v = f(s1) + f(s2) + f(s3) exactly.
+// v -> three BF16 slices (bits), v = f(s1) + f(s2) + f(s3) (exact for
+// |v| >= 2^-110).
 __device__ __forceinline__ void split3(float v, uint16_t& s1, uint16_t& s2, uint16_t& s3) {
   uint16_t b;
   asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(b) : "f"(v));
@@ -94,7 +96,7 @@ __device__ __forceinline__ void split3(float v, uint16_t& s1, uint16_t& s2, uint
 }
 
 // v0, v1 -> three packed BF16 slice pairs (v0 in the low half), each value
-// the exact sum of its three slices.
+// the sum of its three slices (exact for |v| >= 2^-110).
 __device__ __forceinline__ void split3x2(float v0, float v1, uint32_t& s1, uint32_t& s2,
                                          uint32_t& s3) {
   asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(s1) : "f"(v1), "f"(v0));

@@ -13,7 +13,8 @@ namespace rsvd {
 //   C (M x N, ldc) = op(A) X,  op(A) = A (M x K, lda) in the AX form or
 //   A^T (A stored K x M, lda) in the ATX form;  X K x N (ldx).
 // M == 0 marks a product that is skipped (a problem outside this step).
-// X enters the MMAs as three BF16 slices (x = x1 + x2 + x3 exactly), written
+// X enters the MMAs as three BF16 slices (x = x1 + x2 + x3, exact for
+// |x| >= 2^-110), written
 // by the split kernel to `xs` as the shared-memory images the MMAs read: for
 // column tile ct (columns ct t .. ct t + t - 1) and contraction block kb,
 // image (ct * kpad / 64 + kb) holds 3t rows of 128 bytes -- row j is slice
